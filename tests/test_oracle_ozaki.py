@@ -1,0 +1,314 @@
+"""Pins of O2 (the Ozaki emulation) against the mathematics and against O1.
+
+Each pin is chosen so that a plausible slip in O2 fails at least one of them;
+``test_planted_mistakes_are_caught`` plants such slips (in the oracle, on the
+CPU) and checks that the pins notice.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import exact, ozaki
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_balanced_digits_reassemble():
+    rng = np.random.default_rng(3)
+    for _ in range(2000):
+        nd = int(rng.integers(1, 40))
+        lim = 1 << (8 * nd - 1)
+        X = int(rng.integers(-2**62, 2**62)) * (1 << int(rng.integers(0, max(1, 8 * nd - 63)))) % lim
+        X = X if rng.random() < 0.5 else -X
+        d = ozaki.balanced_digits(X, nd)
+        assert sum(v * 256 ** (nd - 1 - t) for t, v in enumerate(d)) == X
+        assert all(-128 <= v <= 127 for v in d[1:])
+        assert -128 <= d[0] <= 128
+    # extremes
+    for X in (2 ** 23 - 1, -(2 ** 23 - 1), 0, 1, -1, 128, -128, 127):
+        d = ozaki.balanced_digits(X, 3)
+        assert sum(v * 256 ** (2 - t) for t, v in enumerate(d)) == X
+    d = ozaki.balanced_digits(2 ** 23 - 1, 3)
+    assert d[0] == 128   # the top digit may reach +-128
+
+
+def test_fixed_point_truncation():
+    """0 <= |a| 2^(8s-1-E) - |X| < 1 and |X| < 2^(8s-1) for |a| < 2^E."""
+    p = 256
+    A = si.random_matrix(8, 12, p, 5, "uniform_exp")
+    s = 20
+    E = ozaki.row_exponents(A, "rows")
+    for i in range(8):
+        for l in range(12):
+            for c in range(2):
+                v = exact.component(A, c, i, l)
+                a = abs(exact.to_fraction(v))
+                assert a < Fraction(2) ** E[i]
+                X, lossless = ozaki.fixed_point(v, E[i], s)
+                scaled = a * Fraction(2) ** (8 * s - 1 - E[i])
+                assert 0 <= scaled - abs(X) < 1
+                assert abs(X) < 2 ** (8 * s - 1)
+                assert lossless == (scaled == abs(X))
+                assert (X < 0) == (v[0] < 0) or X == 0
+
+
+def test_vectorised_split_matches_scalar_definition():
+    p = 192
+    A = si.random_matrix(6, 9, p, 8, "uniform_exp", zero_frac=0.15)
+    s = 26
+    sp = ozaki.split_operand(A, s, "A", "3m")
+    spB = ozaki.split_operand(A, s, "B", "3m")
+    for i in range(6):
+        for l in range(9):
+            xr, _ = ozaki.fixed_point(exact.component(A, 0, i, l), sp.E[i], s)
+            xi, _ = ozaki.fixed_point(exact.component(A, 1, i, l), sp.E[i], s)
+            assert list(sp.digits["re"][:, i, l]) == ozaki.balanced_digits(xr, s)
+            assert list(sp.digits["im"][:, i, l]) == ozaki.balanced_digits(xi, s)
+            assert list(sp.digits["sum"][:, i, l]) == ozaki.balanced_digits(xr + xi, s + 1)
+            yr, _ = ozaki.fixed_point(exact.component(A, 0, i, l), spB.E[l], s)
+            assert list(spB.digits["re"][:, l, i]) == ozaki.balanced_digits(yr, s)
+
+
+def test_row_exponent_is_the_row_maximum():
+    A = si.random_matrix(10, 7, 128, 9, "uniform_exp", zero_frac=0.3)
+    A.limb[:, :, 4, :] = 0      # an all-zero row
+    E = ozaki.row_exponents(A, "rows")
+    assert E[4] is None
+    for i in range(10):
+        if i == 4:
+            continue
+        exps = [int(A.exp[c, i, l]) for c in range(2) for l in range(7) if np.any(A.limb[c, :, i, l])]
+        assert E[i] == max(exps)
+
+
+def _exact_scaled(A, B, r):
+    return ozaki.exact_accumulators(A, B, r.splitA, r.splitB, r.params)
+
+
+@pytest.mark.parametrize("method", ["4m", "3m"])
+def test_all_pairs_and_lossless_split_give_the_exact_product(method):
+    """Special case: P = every pair and no digit dropped -> Acc * 2^scale == T exactly."""
+    p = 128
+    A = si.random_matrix(5, 8, p, 12, "uniform_exp")
+    B = si.random_matrix(8, 4, p, 13, "uniform_exp", zero_frac=0.1)
+    prm = ozaki.make_params(p, 8, method, guard=60)
+    r = ozaki.ozaki_cgemm(A, B, p, method, guard=60, Q=2 * prm.s + 2)
+    assert all(r.splitA.lossless) and all(r.splitB.lossless)
+    T = _exact_scaled(A, B, r)
+    for comp in ("re", "im"):
+        for i in range(5):
+            for j in range(4):
+                assert Fraction(int(r.acc[comp][i, j])) == T[comp][i, j]
+                assert ozaki.entry_bound(r.params, r.splitA, r.splitB, i, j, comp)[0] == 0
+    assert r.certified.all()
+    assert exact.equal_arrays(r.C, exact.rounded_cgemm(A, B, p))
+
+
+@pytest.mark.parametrize("method,dist,guard", [("4m", "uniform", 8), ("3m", "uniform", 8),
+                                                ("4m", "uniform_exp", 0), ("3m", "uniform_exp", 4)])
+def test_truncation_bound_holds(method, dist, guard):
+    """|Acc - T| <= b 2^beta for the paper's triangle, lossy split included."""
+    p = 128
+    A = si.random_matrix(6, 10, p, 14, dist)
+    B = si.random_matrix(10, 5, p, 15, dist)
+    r = ozaki.ozaki_cgemm(A, B, p, method, guard=guard)
+    T = _exact_scaled(A, B, r)
+    worst = Fraction(0)
+    for comp in ("re", "im"):
+        for i in range(6):
+            for j in range(5):
+                b, beta = ozaki.entry_bound(r.params, r.splitA, r.splitB, i, j, comp)
+                err = abs(Fraction(int(r.acc[comp][i, j])) - T[comp][i, j])
+                assert err <= b * Fraction(2) ** beta
+                worst = max(worst, err / (b * Fraction(2) ** beta))
+    assert worst > Fraction(1, 1 << 20)   # the bound is not vacuous
+
+
+def test_truncation_bound_is_attained_by_coherent_errors():
+    """All-ones mantissas truncate almost a full ulp each, all with one sign:
+    the error then sits just below the split term of the bound (not far under it)."""
+    p, k = 128, 16
+    vals = np.zeros((2, 1, k), np.int64)
+    A = si.from_integers(vals, p)
+    B = si.from_integers(np.zeros((2, k, 1), np.int64), p)
+    ones = np.uint64(0xFFFFFFFFFFFFFFFF)
+    A.limb[:, :, 0, :] = ones           # Re and Im of A: +(1 - 2^-128) 2^3
+    A.exp[:, 0, :] = 3
+    B.limb[:, :, :, 0] = ones           # Re of B positive, Im negative: Re = rr - ii adds
+    B.exp[:, :, 0] = -2                 # both truncation errors with one sign
+    B.sign[1, :, 0] = 1
+    s_ = 10
+    r = ozaki.ozaki_cgemm(A, B, p, "4m", s=s_, Q=2 * s_ - 2)   # every pair kept: no dropped term
+    assert not r.splitA.lossless[0] and not r.splitB.lossless[0]
+    T = _exact_scaled(A, B, r)
+    b, beta = ozaki.entry_bound(r.params, r.splitA, r.splitB, 0, 0, "re")
+    bound = b * Fraction(2) ** beta
+    err = abs(Fraction(int(r.acc["re"][0, 0])) - T["re"][0, 0])
+    assert Fraction(99, 100) * bound < err <= bound
+
+
+def test_group_partition_does_not_change_level_sums():
+    p = 128
+    A = si.random_matrix(4, 6, p, 16)
+    B = si.random_matrix(6, 5, p, 17)
+    base = ozaki.make_params(p, 6, "4m")
+    spA = ozaki.split_operand(A, base.s, "A", "4m")
+    spB = ozaki.split_operand(B, base.s, "B", "4m")
+    results = []
+    for gmax in (1, 3, 10 ** 6):
+        prm = ozaki.Params(p=p, k=6, s=base.s, Q=base.Q, gmax=gmax, method="4m")
+        gs, sums = ozaki.group_sums(spA, spB, "ri", prm)
+        assert all(g.count <= gmax for g in gs)
+        levels = {}
+        for g, G in zip(gs, sums):
+            levels[g.q] = levels.get(g.q, 0) + G
+        results.append(levels)
+    for lv in results[1:]:
+        assert lv.keys() == results[0].keys()
+        assert all(np.array_equal(lv[q], results[0][q]) for q in lv)
+
+
+def test_group_sums_fit_int32_at_the_limit():
+    """Gmax * k * 2^14 <= 2^31 - 1 for the largest supported k; worst-case digits."""
+    for k in (1, 7, 256, 2048, 131071):
+        prm = ozaki.make_params(256, k)
+        assert prm.gmax * k * (128 * 128) <= 2 ** 31 - 1
+        assert (prm.gmax + 1) * k * (128 * 128) > 2 ** 31 - 1 or prm.gmax == 2 ** 31 // (k << 14)
+    with pytest.raises(ValueError):
+        ozaki.make_params(256, 131072)
+
+
+@pytest.mark.parametrize("method", ["4m", "3m"])
+@pytest.mark.parametrize("dist,guard,zf", [("uniform", 40, 0.0), ("uniform_exp", 40, 0.1),
+                                           ("uniform", 0, 0.0), ("uniform_exp", 2, 0.2)])
+def test_final_output_equals_o1(method, dist, guard, zf):
+    """Certified entries round Acc; the rest fall back to the exact value -> == O1."""
+    p = 128
+    A = si.random_matrix(7, 9, p, 18, dist, zero_frac=zf)
+    B = si.random_matrix(9, 6, p, 19, dist, zero_frac=zf)
+    r = ozaki.ozaki_cgemm(A, B, p, method, guard=guard)
+    assert exact.equal_arrays(r.C, exact.rounded_cgemm(A, B, p))
+    if guard >= 40 and dist == "uniform":
+        assert r.certified.all()
+    if guard == 0:
+        assert not r.certified.all()   # the fallback path is exercised
+
+
+def test_certification_is_sound_near_midpoints():
+    """Values planted right next to a rounding midpoint are never certified wrongly."""
+    p = 16
+    rng = np.random.default_rng(4)
+    for _ in range(3000):
+        sh = int(rng.integers(4, 40))
+        q = int(rng.integers(1 << (p - 1), 1 << p))
+        mid = (2 * q + 1) << (sh - 1)
+        off = int(rng.integers(-(1 << (sh - 2)), 1 << (sh - 2)))
+        acc = mid + off
+        b = int(rng.integers(0, 1 << max(1, sh - 4)))
+        if ozaki.certify(acc, b, 0, p):
+            for T in (acc - b, acc + b, acc):
+                assert exact.round_nearest_even((T, 0), p) == exact.round_nearest_even((acc, 0), p)
+
+
+def test_paper_division_counts():
+    """The tau rule of Alg. 2 with binary64 slices reproduces d = 13 / 25 / 37 (Sec. IV)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "ozaki_division_counts.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        p, d = int(row[0]), int(row[1])
+        for l in map(int, row[2:]):
+            assert ozaki.paper_division_count(p, 53, l) == d
+    assert ozaki.paper_slice_bits(53, 1024) == 21
+
+
+def test_table1_real_products_per_method():
+    rows = {l.split()[0]: int(l.split()[2]) for l in open(os.path.join(GOLDEN, "table1_op_counts.txt"))
+            if l.strip() and not l.startswith("#")}
+    assert len(ozaki.PRODUCTS_4M) == rows["4m"] and len(ozaki.PRODUCTS_3M) == rows["3m"]
+
+
+# ------------------------------------------------------------ planted mistakes
+
+def _pins_pass(monkeypatch_ctx):
+    """Run a compact version of the pins; True if all hold."""
+    try:
+        test_balanced_digits_reassemble()
+        test_fixed_point_truncation()
+        for method in ("4m", "3m"):
+            test_all_pairs_and_lossless_split_give_the_exact_product(method)
+            test_final_output_equals_o1(method, "uniform", 40, 0.0)
+            test_final_output_equals_o1(method, "uniform_exp", 0, 0.1)
+        test_truncation_bound_holds("3m", "uniform_exp", 4)
+        test_truncation_bound_holds("4m", "uniform", 8)
+        test_truncation_bound_is_attained_by_coherent_errors()
+    except AssertionError:
+        return False
+    return True
+
+
+def _mutants():
+    orig_bd = ozaki.balanced_digits
+    orig_bda = ozaki.balanced_digits_array
+    orig_acc = ozaki.accumulate
+    orig_fp = ozaki.fixed_point
+    orig_fpa = ozaki.fixed_point_array
+    orig_bexp = ozaki.bound_exponent
+
+    def digit_order(m):      # digits stored least significant first
+        m.setattr(ozaki, "balanced_digits", lambda X, nd: list(reversed(orig_bd(X, nd))))
+        m.setattr(ozaki, "balanced_digits_array", lambda X, nd: orig_bda(X, nd)[::-1].copy())
+
+    def level_shift(m):      # level weight off by one digit
+        m.setattr(ozaki, "accumulate", lambda gs, sums, Q: orig_acc(gs, sums, Q + 1))
+
+    def split_rounding(m):   # magnitude rounded up instead of truncated
+        def fp(v, E, s):
+            X, ok = orig_fp(v, E, s)
+            return (X + (1 if X > 0 else -1 if X < 0 else 0)), ok
+
+        def fpa(N, x, E, s):
+            X, ok = orig_fpa(N, x, E, s)
+            return np.where(X > 0, X + 1, np.where(X < 0, X - 1, X)), ok
+        m.setattr(ozaki, "fixed_point", fp)
+        m.setattr(ozaki, "fixed_point_array", fpa)
+
+    def no_drop_bound(m):    # bound forgets the dropped pairs
+        m.setattr(ozaki, "drop_bound", lambda *a: 0)
+
+    def bound_scale(m):      # bound expressed in the wrong unit (one digit too coarse)
+        m.setattr(ozaki, "bound_exponent", lambda prm: max(0, orig_bexp(prm) - 8))
+
+    def im_sign(m):          # 3M imaginary part: + rr instead of - rr
+        orig = ozaki.ozaki_cgemm
+
+        def wrapped(*a, **kw):
+            r = orig(*a, **kw)
+            return r
+        orig_acc2 = ozaki.accumulate
+        state = {"n": 0}
+
+        def acc(gs, sums, Q):
+            v = orig_acc2(gs, sums, Q)
+            state["n"] += 1
+            # products arrive in the order rr, ii, (ri, ir | ss); flip rr's sign
+            return -v if state["n"] % (4 if False else 3) == 1 else v
+        m.setattr(ozaki, "accumulate", acc)
+
+    return {"digit_order": digit_order, "level_shift": level_shift,
+            "split_rounding": split_rounding, "no_drop_bound": no_drop_bound,
+            "bound_scale": bound_scale, "rr_sign": im_sign}
+
+
+@pytest.mark.parametrize("name", ["digit_order", "level_shift", "split_rounding",
+                                  "no_drop_bound", "bound_scale", "rr_sign"])
+def test_planted_mistakes_are_caught(monkeypatch, name):
+    plant = _mutants()[name]
+    with monkeypatch.context() as m:
+        plant(m)
+        assert not _pins_pass(m), f"planted mistake {name!r} went unnoticed"
+    assert _pins_pass(None)
