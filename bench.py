@@ -1,0 +1,372 @@
+"""Benchmark: complex multiple-precision GEMM rate (8 m n k per second) on GB300.
+
+One step = one C := RN_p(A B) through the library's C ABI, the whole hot
+path: split (row/column exponents + digits), slice products on the tensor
+cores, exact accumulation + certified rounding, exact fallback.
+
+Default workload: m = n = k = 2048, p = 1024 bits, Ozaki 3M, entries
+u * 2^e (u uniform on the p-bit grid of [-1, 1), e uniform in [-20, 20]),
+seeded.  Ozaki 4M and the plain multi-limb GEMM are timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (the product shards by independent problems: no
+collective on the data path); rank 0 prints one JSON line with the
+whole-job rate (all ranks' units over the max-over-ranks time).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic_inputs as si  # noqa: E402
+
+METRIC = "complex MP GEMM 8mnk/s at p=256/512/1024 bits: Ozaki-INT8 vs plain, 1 GB300"
+UNIT = "8mnk/s"
+WORKLOADS = {
+    # name: (m, n, k, p, dist, seed index)
+    "c2_2048_p1024": (2048, 2048, 2048, 1024, "uniform_exp", 2),
+    "c2_2048_p512": (2048, 2048, 2048, 512, "uniform_exp", 2),
+    "c2_1024_p512": (1024, 1024, 1024, 512, "uniform_exp", 2),
+    "c2_1024_p1024": (1024, 1024, 1024, 1024, "uniform_exp", 2),
+    "c1_256_p256": (256, 256, 256, 256, "uniform", 1),
+}
+PROFILE = os.path.join(ROOT, "profiles", "oz_slicegemm_c2_2048_p1024.md")
+SLICEGEMM_SRC = os.path.join(ROOT, "paper_2307_06072_gb300", "csrc", "slicegemm_tc.cu")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_inputs(workload: str, rank: int):
+    m, n, k, p, dist, idx = WORKLOADS[workload]
+    A = si.random_matrix(m, k, p, si.SEED_BASE + idx + 7919 * rank, dist)
+    B = si.random_matrix(k, n, p, si.SEED_BASE + idx + 1000 + 7919 * rank, dist)
+    return A, B, p
+
+
+def pair_count(s: int, Q: int, method: str) -> int:
+    """Kept slice pairs over all real products (Alg. 2's triangle t + u <= Q)."""
+    def tri(a0, na, b0, nb):
+        return sum(1 for t in range(a0, a0 + na) for u in range(b0, b0 + nb) if t + u <= Q)
+    if method == "4m":
+        return 4 * tri(0, s, 0, s)
+    return 2 * tri(0, s, 0, s) + tri(-1, s + 1, -1, s + 1)
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read only; never sets clocks)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = [l.split(",") for l in open(self.path) if l.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        busy = [v for v in sm if mx and v > 0.3 * mx] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def committed_traffic(kernel_hash: str):
+    """DRAM bytes per launch of the slice-GEMM kernel from the committed ncu summary,
+    or None if the summary is missing or was taken on a different kernel source."""
+    if not os.path.exists(PROFILE):
+        return None
+    txt = open(PROFILE).read()
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not h or not t or h.group(1) != kernel_hash:
+        return None
+    return float(t.group(1))
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as tdist
+    ws_, rank, local = dist_env()
+    if ws_ > 1:
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws_ > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2307_06072_gb300 import build
+    if rank == 0 or ws_ == 1:
+        build.build()
+    if ws_ > 1:
+        tdist.barrier()
+    import paper_2307_06072_gb300 as mp
+
+    m, n, k, p, dist, _ = WORKLOADS[args.workload]
+    t0 = time.time()
+    A, B, p = make_inputs(args.workload, rank)
+    log(f"[rank {rank}] inputs {m}x{k}x{n} p={p} generated in {time.time() - t0:.1f}s")
+    dA, dB = mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(B, dev)
+    dC = mp.DeviceMatrix.empty(m, n, p, dev)
+    stream = torch.cuda.current_stream(dev)
+    method = args.method
+    pl = mp.plan(m, n, k, p, method, "ozaki")
+    ws = mp.Workspace(dev)
+    ws.get(pl["ws_bytes"])
+
+    def timed(method_, algo_, steps, warmup, with_events=False):
+        evs = []
+        for _ in range(warmup):
+            mp.mpcgemm(dA, dB, dC, p, method_, algo_, workspace=ws, stream=stream)
+        torch.cuda.synchronize(dev)
+        if ws_ > 1:
+            tdist.barrier()
+        torch.cuda.synchronize(dev)
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if with_events else None
+            mp.mpcgemm(dA, dB, dC, p, method_, algo_, workspace=ws, stream=stream, events=ev)
+            if ev:
+                evs.append(ev)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        if ws_ > 1:
+            tdist.barrier()
+        ms = start.elapsed_time(end)
+        stages = None
+        if evs:
+            stages = [float(np.mean([e[x].elapsed_time(e[x + 1]) for e in evs])) for x in range(4)]
+        return ms, stages
+
+    def max_over_ranks(v: float) -> float:
+        if ws_ == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    units = 8.0 * m * n * k
+    with ClockSampler(dev.index or 0) as clocks:
+        ms_main, stages = timed(method, "ozaki", args.steps, args.warmup, with_events=True)
+    ms_main = max_over_ranks(ms_main)
+    st = mp.read_status(ws, stream)
+    value = units * args.steps * ws_ / (ms_main / 1e3)
+    extras = {}
+    if not args.quick:
+        other = "4m" if method == "3m" else "3m"
+        ms_o, st_o = timed(other, "ozaki", max(1, args.steps // 2), 1, with_events=True)
+        extras[f"ozaki_{other}"] = {"value": units * max(1, args.steps // 2) * ws_ / (max_over_ranks(ms_o) / 1e3),
+                                    "ms_per_step": ms_o / max(1, args.steps // 2),
+                                    "stage_ms": st_o}
+        ms_pl, st_pl = timed("4m", "plain", 1, 1, with_events=True)
+        extras["plain_4m"] = {"value": units * ws_ / (max_over_ranks(ms_pl) / 1e3), "ms_per_step": ms_pl,
+                              "stage_ms": st_pl}
+        extras["ozaki_speedup_vs_plain"] = value / extras["plain_4m"]["value"]
+
+    # roofline of the dominant kernel (the slice GEMM): algorithmic MMA flops / its event time
+    pairs = pair_count(pl["s"], pl["Q"], method)
+    flops = pairs * 2.0 * m * n * k
+    gemm_ms = stages[1]
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    achieved = flops / (gemm_ms / 1e3) / 1e12
+    khash = hashlib.sha256(open(SLICEGEMM_SRC, "rb").read()).hexdigest()[:16] if os.path.exists(SLICEGEMM_SRC) else ""
+    roofline = {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": committed_traffic(khash),
+                "kernel": "oz_slicegemm", "peak_source": f"bf16_tflops_sustained ({peak_src})",
+                "algorithmic_flops_per_launch": flops, "kernel_ms": round(gemm_ms, 3)}
+
+    # e2e through the public API with host buffers: H2D of A, B and D2H of C inside the region
+    e2e = None
+    if not args.no_e2e:
+        hA = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (A.sign, A.exp, A.limb.view(np.int64))]
+        hB = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (B.sign, B.exp, B.limb.view(np.int64))]
+        hC = [torch.empty_like(dC.sign, device="cpu").pin_memory(), torch.empty_like(dC.exp, device="cpu").pin_memory(),
+              torch.empty_like(dC.limb, device="cpu").pin_memory()]
+        h2d = sum(t.numel() * t.element_size() for t in hA + hB)
+        d2h = sum(t.numel() * t.element_size() for t in hC)
+
+        def e2e_step():
+            for dst, src in zip((dA.sign, dA.exp, dA.limb, dB.sign, dB.exp, dB.limb), hA + hB):
+                dst.copy_(src, non_blocking=True)
+            mp.mpcgemm(dA, dB, dC, p, method, "ozaki", workspace=ws, stream=stream)
+            for dst, src in zip(hC, (dC.sign, dC.exp, dC.limb)):
+                dst.copy_(src, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        es = max(1, args.steps // 2)
+        for _ in range(es):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        e2e_s = max_over_ranks(time.perf_counter() - t1)
+        e2e = {"value": units * es * ws_ / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and ws_ == 1 and not args.no_cpu:
+        cpu = cpu_baseline(A, B, p, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_main / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 slices (exact int), u64 limbs",
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"{args.workload}: ozaki {method}, m=n=k={m}, p={p} bits, entries u*2^e, "
+                                   "e in [-20,20]", "method": method, "algo": "ozaki", "m": m, "n": n, "k": k,
+                       "p_bits": p, "slices": pl["s"], "cut_level_Q": pl["Q"], "pairs": pairs,
+                       "l2": "inputs (A, B: %.2f GB) larger than L2 (126 MB)" % ((A.nbytes() + B.nbytes()) / 1e9),
+                       "parallelism": f"replicas x{ws_}"},
+            "stage_ms": {"split": stages[0], "slice_gemm": stages[1], "accumulate_round": stages[2],
+                         "fallback": stages[3]},
+            "device_status": st,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": pl["launches"] * args.steps,
+            "clocks": clocks.summary(), "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    if ws_ > 1:
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+def cpu_baseline(A, B, p, seconds: float, entries_hint: int = 0):
+    """Time the oracle (C, exact, all host threads) on a bounded sample of output entries."""
+    from oracle import c_oracle
+    m, k, n = A.rows, A.cols, B.cols
+    threads = c_oracle.max_threads()
+    rng = np.random.default_rng(12345)
+
+    def sample(cnt):
+        return np.stack([rng.integers(0, m, cnt), rng.integers(0, n, cnt)], axis=1)
+    probe = max(threads, 16)
+    t0 = time.perf_counter()
+    c_oracle.rounded_cgemm(A, B, p, sample(probe))
+    dt = time.perf_counter() - t0
+    cnt = entries_hint or int(max(probe, min(200000, probe * seconds / max(dt, 1e-6))))
+    ent = sample(cnt)
+    t0 = time.perf_counter()
+    c_oracle.rounded_cgemm(A, B, p, ent)
+    dt = time.perf_counter() - t0
+    return {"value": 8.0 * k * cnt / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{cnt} random output entries (both components) of the same {m}x{k}x{n} p={p} product, "
+                      f"exact C oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws_, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import c_oracle
+    c_oracle.build()
+    m, n, k, p, dist, _ = WORKLOADS[args.workload]
+    A, B, p = make_inputs(args.workload, 0)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(A, B, p, min(per_step, 5.0))
+    vals = []
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(A, B, p, per_step)
+        vals.append(cb["value"])
+    value = float(np.mean(vals))
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 8.0 * m * n * k / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "exact integer (u64 limbs)", "data": "synthetic (seeded)",
+            "config": {"workload": f"{args.workload}: exact oracle, m=n=k={m}, p={p} bits, entries u*2^e",
+                       "m": m, "n": n, "k": k, "p_bits": p},
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2_2048_p1024")
+    ap.add_argument("--method", choices=["3m", "4m"], default="3m")
+    ap.add_argument("--quick", action="store_true", help="skip the 4M / plain side measurements")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        log("note: warm-up raised to the minimum of 3 steps")
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * mpcgemm.h -- arbitrary-precision complex matrix multiplication on one
+ * NVIDIA GB300 (sm_103a), by the Ozaki scheme under the 4M and 3M complex
+ * formulations, or by a plain multi-limb GEMM.
+ *
+ * The operation (Kouya, "Acceleration of complex matrix multiplication
+ * using arbitrary precision floating-point arithmetic", Sec. III-A,
+ * Eq. (cmatmul)):  C := A B,  A in C^{m x k}, B in C^{k x n}, every real and
+ * imaginary part a p-bit binary floating-point number.  C is the product
+ * rounded once, to nearest with ties to even, to p bits per component:
+ * the result is the correctly rounded exact product, whatever the algorithm.
+ *
+ * ------------------------------------------------------------------------
+ * Number format (one real component; Sec. II's F_bM, one fixed width):
+ *
+ *     value = (-1)^sign * M * 2^(exp - 64 L),   L = ceil(p / 64),
+ *     M = sum_{j < L} limb_j 2^(64 j)          (limb 0 least significant).
+ *
+ * A component is ZERO iff its top limb (limb L-1) is 0; sign and exp are then
+ * ignored.  A nonzero input is used as given (normalised inputs have bit 63 of
+ * limb L-1 set; the kernels only need |value| < 2^exp, which every M with a
+ * nonzero top limb satisfies).  Outputs are normalised, have at most p
+ * significant bits (the 64L-p low bits of M are 0), and zero is written as
+ * sign 0, exp INT32_MIN, M 0.  Exponents are int32; a result whose exponent
+ * does not fit makes the call report MPC_ERANGE.
+ *
+ * Matrix layout (struct mpc_mat): separate real and imaginary planes, each a
+ * row-major rows x cols array with leading dimension ld >= cols, element
+ * (r, c) at index idx = r*ld + c:
+ *     sign[ri][idx]                  uint8   (0 = +, 1 = -)
+ *     exp[ri][idx]                   int32
+ *     limb[ri][j * rows * ld + idx]  uint64  limb j
+ * with ri = 0 for the real and 1 for the imaginary plane.  All pointers
+ * are DEVICE pointers owned by the caller; the library never frees or
+ * retains them past the call's stream work.
+ *
+ * ------------------------------------------------------------------------
+ * Conventions for every entry point:
+ *   * Asynchronous on `stream` (a cudaStream_t passed as void*; NULL = the
+ *     legacy default stream).  Returns MPC_OK once the work is enqueued.
+ *   * Argument errors are detected on the host before any launch and return
+ *     a negative code with nothing enqueued.
+ *   * Errors that only the device can see (exponent overflow, a fallback
+ *     list overflow) are written to a status block inside the workspace;
+ *     read it with mpcgemm_read_status() (which synchronises the stream).
+ *   * The library allocates no device memory and no pinned host memory:
+ *     all scratch space lives in the caller's `workspace` of `ws_bytes`
+ *     bytes (device memory, 256-byte aligned), sized by
+ *     mpcgemm_workspace_size().  C must not alias A, B or the workspace.
+ *   * k == 0 gives C = 0; m == 0 or n == 0 is a no-op.
+ */
+#ifndef MPCGEMM_H
+#define MPCGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define MPC_OK 0
+#define MPC_EINVAL (-22)    /* bad size, precision, pointer, method or parameter */
+#define MPC_ENOSPC (-28)    /* workspace too small */
+#define MPC_ERANGE (-34)    /* a result exponent does not fit int32 (device-detected) */
+#define MPC_ENOTSUP (-95)   /* unsupported on this device (needs sm_103a) */
+#define MPC_ECUDA (-1000)   /* a CUDA runtime error e occurred: returns MPC_ECUDA - e */
+
+/* ---- algorithm selection --------------------------------------------- */
+enum { MPC_4M = 0, MPC_3M = 1 };          /* Eq. (4m_way) / Eq. (3m_way) */
+enum { MPC_PLAIN = 0, MPC_OZAKI = 1 };    /* Eq. (simple_triple_loop) / Alg. 2 */
+enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2 };
+
+/* Largest supported precision and inner size. */
+#define MPC_MAX_P_BITS 1024
+#define MPC_MAX_K 131071
+
+typedef struct mpc_mat {
+    int64_t rows, cols, ld;
+    uint8_t *sign[2];
+    int32_t *exp[2];
+    uint64_t *limb[2];
+} mpc_mat;
+
+/*
+ * Optional tuning of the Ozaki path (Alg. 2's number of divisions d and pair
+ * triangle).  Zero-initialise and set what you need; a zeroed struct (or a
+ * NULL pointer) means the defaults.
+ *   guard_bits  extra fixed-point bits: s = ceil((p + ceil(log2 k) + guard)/8)
+ *               slices (0 -> 40).  More guard bits make exact fallbacks rarer.
+ *   slices      s itself (0 -> the rule above); 1 <= s <= 160.
+ *   cut_level   Q + 1, where pairs (t, u) with t + u <= Q are multiplied
+ *               (0 -> Q = s - 1, the paper's triangle alpha + beta <= d + 1).
+ *   kernel      MPC_KERNEL_*: which slice-GEMM kernel (auto = tcgen05).
+ */
+typedef struct mpc_oz_params {
+    int32_t guard_bits;
+    int32_t slices;
+    int32_t cut_level;
+    int32_t kernel;
+} mpc_oz_params;
+
+/*
+ * The plan of one call: chosen parameters and the workspace layout (byte
+ * offsets into the workspace).  Filled by mpcgemm_plan(); useful to inspect
+ * intermediate stages (digit planes, group sums) after a call.
+ */
+typedef struct mpc_plan {
+    int32_t algo, method, p_bits, limbs;
+    int32_t s, Q;                 /* slices per operand, highest kept level */
+    int32_t kpad;                 /* k rounded up to 64 (digit-plane row length) */
+    int32_t gmax;                 /* max pairs per group (int32-exact group sums) */
+    int32_t n_products;           /* 4 (4M) or 3 (3M) real products */
+    int32_t n_groups_total;       /* group planes over all products */
+    int32_t n_groups[4];          /* per product: rr, ii, ri|ss, ir */
+    int32_t planes_A, planes_B;   /* digit planes per operand */
+    int32_t acc_slots;            /* 32-bit slots of the exact accumulator */
+    int32_t bound_shift;          /* beta: bounds are b * 2^beta */
+    uint64_t bound_drop[2];       /* ceil(dropped-pair bound / 2^beta), Re / Im */
+    uint64_t bound_lossy_a[2];    /* per unit of k: added when the row of A is lossy */
+    uint64_t bound_lossy_b[2];    /* per unit of k: added when the column of B is lossy */
+    uint64_t off_status, off_rowexp, off_colexp, off_rowlossy, off_collossy;
+    uint64_t off_digits_a, off_digits_b, off_groups, off_group_table;
+    uint64_t off_fallback, fallback_capacity, off_fb_scratch, fb_scratch_limbs, fb_threads;
+    uint64_t off_fix_a, off_fix_b;  /* plain path: fixed-point operands */
+    uint64_t ws_bytes;
+    int32_t launches;             /* kernel launches one call makes */
+    int32_t reserved;
+} mpc_plan;
+
+/*
+ * Optional stage timing: cudaEvent_t handles (passed as void*) created by the
+ * caller with timing enabled.  When a handle is non-NULL the library records it
+ * on `stream` at that stage boundary:
+ *   ev[0] call start, ev[1] after the split (row/column exponents, digits or
+ *   fixed-point operands), ev[2] after the slice products (Ozaki) or the plain
+ *   GEMM, ev[3] after the accumulation and rounding (Ozaki; = ev[2] for plain),
+ *   ev[4] after the exact fallback.  ev[5..7] unused.
+ */
+typedef struct mpc_stage_events {
+    void *ev[8];
+} mpc_stage_events;
+
+/* Device-side outcome of a call (read back by mpcgemm_read_status). */
+typedef struct mpc_status {
+    int32_t erange;           /* nonzero: some result exponent did not fit int32 */
+    int32_t fallback_entries; /* components recomputed exactly (certification failed) */
+    int32_t fallback_overflow;/* nonzero: more failures than the list holds */
+    int32_t uncertified;      /* components whose exact window was too wide (rounded
+                                 from a truncated sum; see mpcgemm_read_status) */
+} mpc_status;
+
+/*
+ * C := RN_p(A B) for m x k A and k x n B, 1 <= p_bits <= MPC_MAX_P_BITS,
+ * k <= MPC_MAX_K.  method: MPC_4M or MPC_3M (Eqs. 4m_way / 3m_way; with
+ * exact arithmetic both give the same C).  algo: MPC_OZAKI (Alg. 2 on the
+ * tensor cores: balanced 8-bit integer slices, exact slice products, exact
+ * accumulation, certified rounding with exact fallback) or MPC_PLAIN (the
+ * triple loop of Eq. simple_triple_loop as an exact fixed-point multi-limb
+ * GEMM on the CUDA cores; method must be MPC_4M).  Sizes use A->rows == m,
+ * A->cols == k, B->rows == k, B->cols == n, C->rows == m, C->cols == n.
+ * Returns MPC_OK, MPC_EINVAL, MPC_ENOSPC, MPC_ENOTSUP or MPC_ECUDA - e.
+ */
+int mpcgemm(int64_t m, int64_t n, int64_t k, int32_t p_bits,
+            const mpc_mat *A, const mpc_mat *B, mpc_mat *C,
+            int method, int algo, void *workspace, size_t ws_bytes, void *stream);
+
+/* As mpcgemm(), with Ozaki tuning (params may be NULL). */
+int mpcgemm_ex(int64_t m, int64_t n, int64_t k, int32_t p_bits,
+               const mpc_mat *A, const mpc_mat *B, mpc_mat *C,
+               int method, int algo, const mpc_oz_params *params,
+               void *workspace, size_t ws_bytes, void *stream);
+
+/* As mpcgemm_ex(), recording the caller's events at stage boundaries
+ * (events may be NULL: then identical to mpcgemm_ex). */
+int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits,
+                     const mpc_mat *A, const mpc_mat *B, mpc_mat *C,
+                     int method, int algo, const mpc_oz_params *params,
+                     const mpc_stage_events *events,
+                     void *workspace, size_t ws_bytes, void *stream);
+
+/* Bytes of workspace a call with these arguments needs (0 on bad arguments). */
+size_t mpcgemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t p_bits,
+                              int method, int algo);
+
+/* The plan (parameters + workspace layout) of a call; params may be NULL. */
+int mpcgemm_plan(int64_t m, int64_t n, int64_t k, int32_t p_bits, int method, int algo,
+                 const mpc_oz_params *params, mpc_plan *out);
+
+/* Synchronise `stream` and read the device status of the last call that used
+ * this workspace.  Returns MPC_OK, or MPC_ERANGE if status->erange is set. */
+int mpcgemm_read_status(const void *workspace, size_t ws_bytes, mpc_status *status, void *stream);
+
+/* Human-readable text of a status code (static storage). */
+const char *mpcgemm_strerror(int code);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int mpcgemm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPCGEMM_H */

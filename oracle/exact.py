@@ -38,10 +38,13 @@ class ExponentRangeError(ArithmeticError):
 def component(mat, c: int, r: int, col: int):
     """Exact value of component c (0 = Re, 1 = Im) of element (r, col).
 
-    Format: value = (-1)**sign * M * 2**(exp - 64L), M = sum limb_j 2**(64 j).
+    Format: value = (-1)**sign * M * 2**(exp - 64L), M = sum limb_j 2**(64 j);
+    the component is zero iff its top limb is 0.
     Returns (N, x) with value = N * 2**x; zero is (0, 0).
     """
     L = mat.limb.shape[1]
+    if int(mat.limb[c, L - 1, r, col]) == 0:
+        return (0, 0)
     M = 0
     for j in range(L - 1, -1, -1):
         M = (M << 64) | int(mat.limb[c, j, r, col])

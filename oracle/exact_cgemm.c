@@ -12,7 +12,7 @@
  * ties to even, on a p-bit significand.
  *
  * Number format (per real component): value = (-1)^sign * M * 2^(exp-64L),
- * M = sum_j limb[j] 2^(64j), zero iff M == 0.  Arrays are dense planes:
+ * M = sum_j limb[j] 2^(64j), zero iff the top limb limb[L-1] == 0.  Arrays are dense planes:
  *   sign[c*R*C + idx], exp[c*R*C + idx], limb[(c*L + j)*R*C + idx],
  *   idx = r*C + col, c = 0 real, 1 imaginary.
  */
@@ -37,11 +37,10 @@ typedef struct {
     int L;
 } omat;
 
+/* zero iff the top limb is 0 (format definition) */
 static int is_zero(const omat *a, int c, int64_t idx) {
     int64_t plane = a->R * a->C;
-    for (int j = 0; j < a->L; j++)
-        if (a->limb[((int64_t)c * a->L + j) * plane + idx]) return 0;
-    return 1;
+    return a->limb[((int64_t)c * a->L + a->L - 1) * plane + idx] == 0;
 }
 
 static void load_mant(const omat *a, int c, int64_t idx, uint64_t *out) {

@@ -37,6 +37,7 @@ Algorithm 2 of the paper (Kouya, Sec. III-C) in this library's reading:
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass, field
 
@@ -96,11 +97,15 @@ def make_params(p: int, k: int, method: str = "4m", guard: int = DEFAULT_GUARD,
 # ------------------------------------------------------------- step 1
 
 def mantissas(mat, c: int):
-    """Object array of the signed integers N with component value N * 2**(exp - 64L)."""
+    """Object array of the signed integers N with component value N * 2**(exp - 64L).
+
+    A component whose top limb is 0 is zero (format definition).
+    """
     L = mat.limb.shape[1]
     M = np.zeros((mat.rows, mat.cols), dtype=object)
     for j in range(L - 1, -1, -1):
         M = (M * (1 << 64)) + mat.limb[c, j].astype(object)
+    M = np.where(mat.limb[c, L - 1] == 0, 0, M)
     return np.where(mat.sign[c] != 0, -M, M)
 
 
@@ -280,6 +285,7 @@ def accumulate(gs, sums, Q: int):
 
 # ------------------------------------------------------------- step 6 (bound)
 
+@functools.lru_cache(maxsize=None)
 def drop_bound(tA: tuple, tB: tuple, Q: int, k: int) -> int:
     """Integer bound on the dropped pairs of one product, in Acc units.
 

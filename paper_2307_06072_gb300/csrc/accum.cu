@@ -1,0 +1,309 @@
+// oz_accum + cplx_assemble + rounding (Alg. 2's final L-bit accumulation and
+// Eqs. (4m_way) / (3m_way)), and the exact fallback.
+//
+// k_oz_accum: one thread per output element (i, j).  The group sums of every
+// real product are shifted by 8 (Q - q) and added, with the sign the complex
+// formula gives them, into two exact accumulators (Re, Im):
+//     4M: Re = rr - ii,        Im = ri + ir
+//     3M: Re = rr - ii,        Im = ss - rr - ii
+// The accumulators are "lazy" radix-2^32 integers (int64 slots in shared
+// memory) normalised once at the end.  Value = Acc * 2^(E_i + F_j - 14 - 8Q).
+// The result is RN_p(Acc) when no rounding midpoint lies within the error
+// bound b * 2^beta of Acc (then it equals RN_p of the exact product);
+// otherwise the component is queued for k_exact_fallback.
+//
+// k_exact_fallback: one thread per queued component; the exact dot product
+// of Eq. (simple_triple_loop) with Eq. (4m_way_base), in a fixed-point window
+// wide enough for every product, then RN_p.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mpc {
+
+namespace {
+
+struct SlotAcc {   // 32-bit words stored in int64 shared-memory slots (stride T)
+  const int64_t *base;
+  int stride;
+  __device__ __forceinline__ uint32_t operator()(int i) const { return (uint32_t)base[(int64_t)i * stride]; }
+};
+
+struct LimbAcc {   // 32-bit words of a little-endian uint64 array
+  const uint64_t *base;
+  __device__ __forceinline__ uint32_t operator()(int i) const {
+    return (uint32_t)(base[i >> 1] >> (32 * (i & 1)));
+  }
+};
+
+// sign with which product `prod` enters component c
+__device__ __forceinline__ int product_sign(int method, int c, int prod) {
+  if (method == MPC_4M) {
+    if (c == 0) return prod == 0 ? 1 : (prod == 1 ? -1 : 0);
+    return (prod == 2 || prod == 3) ? 1 : 0;
+  }
+  if (c == 0) return prod == 0 ? 1 : (prod == 1 ? -1 : 0);
+  return prod == 2 ? 1 : -1;
+}
+
+// normalise lazy slots into 32-bit two's-complement words; return sign, leave magnitude
+__device__ __forceinline__ bool normalise_slots(int64_t *my, int nslot, int T) {
+  int64_t carry = 0;
+  for (int s = 0; s < nslot; ++s) {
+    int64_t t = my[(int64_t)s * T] + carry;
+    my[(int64_t)s * T] = t & 0xFFFFFFFFll;
+    carry = t >> 32;
+  }
+  bool neg = carry < 0;
+  if (neg) {
+    int64_t c = 1;
+    for (int s = 0; s < nslot; ++s) {
+      int64_t w = ((~my[(int64_t)s * T]) & 0xFFFFFFFFll) + c;
+      my[(int64_t)s * T] = w & 0xFFFFFFFFll;
+      c = w >> 32;
+    }
+  }
+  return neg;
+}
+
+}  // namespace
+
+__global__ void k_group_table(ProductDesc p0, ProductDesc p1, ProductDesc p2, ProductDesc p3, int n_products,
+                              int Q, int gmax, GroupEntry *table) {
+  if (blockIdx.x != 0 || threadIdx.x >= (unsigned)n_products) return;
+  ProductDesc pd = threadIdx.x == 0 ? p0 : threadIdx.x == 1 ? p1 : threadIdx.x == 2 ? p2 : p3;
+  build_groups((int)threadIdx.x, pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, Q, gmax, table + pd.group0,
+               pd.n_groups);
+}
+
+__global__ void k_oz_accum(AccumArgs a, OutView C) {
+  extern __shared__ int64_t slots[];   // [2][nslot][T]
+  const int T = blockDim.x;
+  const int64_t j = (int64_t)blockIdx.x * T + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j >= a.n || i >= a.m) return;    // no block-level sync below
+  int64_t *acc[2] = {slots + threadIdx.x, slots + (int64_t)a.nslot * T + threadIdx.x};
+  for (int c = 0; c < 2; ++c)
+    for (int s = 0; s < a.nslot; ++s) acc[c][(int64_t)s * T] = 0;
+  const int32_t Ei = a.E[i], Fj = a.F[j];
+  const bool zero = (Ei == INT32_MIN) || (Fj == INT32_MIN);
+  const int64_t mn = a.m * a.n, ij = i * a.n + j;
+  if (!zero) {
+    for (int e = 0; e < a.n_entries; ++e) {
+      const GroupEntry g = a.groups[e];
+      const int s0 = product_sign(a.method, 0, g.prod), s1 = product_sign(a.method, 1, g.prod);
+      const int64_t v = (int64_t)a.planes[(int64_t)e * mn + ij];
+      const int shift = 8 * (a.Q - g.q);
+      const int w = shift >> 5, r = shift & 31;
+      if (s0) {
+        const int64_t x = (s0 > 0 ? v : -v) * ((int64_t)1 << r);
+        acc[0][(int64_t)w * T] += x & 0xFFFFFFFFll;
+        acc[0][(int64_t)(w + 1) * T] += x >> 32;
+      }
+      if (s1) {
+        const int64_t x = (s1 > 0 ? v : -v) * ((int64_t)1 << r);
+        acc[1][(int64_t)w * T] += x & 0xFFFFFFFFll;
+        acc[1][(int64_t)(w + 1) * T] += x >> 32;
+      }
+    }
+  }
+  for (int c = 0; c < 2; ++c) {
+    const int64_t o = i * C.ld + j;
+    if (zero) {
+      store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+      continue;
+    }
+    const bool neg = normalise_slots(acc[c], a.nslot, T);
+    SlotAcc mag{acc[c], T};
+    const int N = bitlen(mag, a.nslot);
+    const uint64_t b = a.bound_drop[c] + (uint64_t)a.k * ((a.lossyA[i] ? a.bound_lossy_a[c] : 0ull) +
+                                                          (a.lossyB[j] ? a.bound_lossy_b[c] : 0ull));
+    if (N == 0 && b == 0) {
+      store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+    } else if (N > 0 && certified(mag, a.nslot, N, a.p, b, a.bound_shift)) {
+      const int64_t scale = (int64_t)Ei + (int64_t)Fj - kProdLog2 - 8 * (int64_t)a.Q;
+      if (!round_store(mag, a.nslot, N, neg, scale, a.p, a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o,
+                       C.plane)) {
+        status_set(a.status, kStErange, 1);
+        store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+      }
+    } else {
+      const int slot = atomicAdd(reinterpret_cast<int *>(a.status) + kStFallbackCount, 1);
+      if (slot < a.fallback_cap) a.fallback[slot] = ij * 2 + c;
+      else status_set(a.status, kStFallbackOverflow, 1);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ fallback
+
+namespace {
+
+// window (nw limbs, two's complement) += / -= (P << shift), P = 2L limbs; shift may be < 0
+__device__ void window_add(uint64_t *win, int nw, const uint64_t *P, int np, int64_t shift, bool sub) {
+  int64_t w0 = shift >= 0 ? (shift >> 6) : 0;
+  int64_t wtop = (shift + 64 * (int64_t)np) / 64 + 1;   // last limb the operand can touch
+  uint64_t carry = 0;
+  for (int64_t w = w0; w < nw; ++w) {
+    uint64_t v = 0;
+    if (w <= wtop) {
+      const int64_t b = 64 * w - shift;                  // operand bit at window bit 64w
+      if (b < 64 * (int64_t)np && b > -64) {
+        const int64_t q = b >= 0 ? (b >> 6) : -1;
+        const int off = (int)(b - 64 * q);
+        const uint64_t lo = (q >= 0 && q < np) ? P[q] : 0ull;
+        const uint64_t hi = (q + 1 >= 0 && q + 1 < np) ? P[q + 1] : 0ull;
+        v = off ? ((lo >> off) | (hi << (64 - off))) : lo;
+      }
+    } else if (carry == 0) {
+      break;
+    }
+    if (!sub) {
+      uint64_t s = win[w] + v;
+      uint64_t c1 = s < v;
+      s += carry;
+      c1 |= (s < carry);
+      win[w] = s;
+      carry = c1;
+    } else {
+      uint64_t d = win[w] - v;
+      uint64_t b1 = win[w] < v;
+      uint64_t d2 = d - carry;
+      b1 |= (d < carry);
+      win[w] = d2;
+      carry = b1;
+    }
+  }
+}
+
+}  // namespace
+
+__global__ void k_exact_fallback(FallbackArgs f, MatView A, MatView B, OutView C) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  int64_t count = f.status[kStFallbackCount];
+  if (count > f.cap) count = f.cap;
+  uint64_t *win = f.scratch + tid * f.scratch_limbs;
+  const int L = f.L;
+  for (int64_t q = tid; q < count; q += nthreads) {
+    const int64_t code = f.list[q];
+    const int c = (int)(code & 1);
+    const int64_t ij = code >> 1, i = ij / f.n, j = ij % f.n;
+    // terms of Eq. (4m_way_base): (component of A, component of B, subtract)
+    const int ta[2] = {0, 1}, tb[2] = {c == 0 ? 0 : 1, c == 0 ? 1 : 0};
+    const bool tsub[2] = {false, c == 0};
+    int64_t xmin = INT64_MAX, top = INT64_MIN;
+    for (int64_t l = 0; l < f.k; ++l) {
+      const int64_t ia = i * A.ld + l, ib = l * B.ld + j;
+      for (int t = 0; t < 2; ++t) {
+        if (!A.limb[ta[t]][(int64_t)(L - 1) * A.plane + ia] || !B.limb[tb[t]][(int64_t)(L - 1) * B.plane + ib])
+          continue;
+        const int64_t es = (int64_t)A.exp[ta[t]][ia] + (int64_t)B.exp[tb[t]][ib];
+        xmin = min(xmin, es - 128 * (int64_t)L);
+        top = max(top, es);
+      }
+    }
+    const int64_t o = i * C.ld + j;
+    if (top == INT64_MIN) {
+      store_zero(L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+      continue;
+    }
+    int growth = 2;
+    while (((int64_t)1 << growth) < 4 * f.k) ++growth;
+    int64_t width = top - xmin + growth + 2;
+    int nw = (int)(width / 64 + 2);
+    bool truncated = false;
+    if (nw > f.scratch_limbs) {
+      nw = f.scratch_limbs;
+      xmin = top + growth + 2 - 64 * (int64_t)(nw - 1);
+      truncated = true;
+    }
+    for (int w = 0; w < nw; ++w) win[w] = 0;
+    uint64_t Ma[kMaxLimbs], Mb[kMaxLimbs], P[2 * kMaxLimbs];
+    for (int64_t l = 0; l < f.k; ++l) {
+      const int64_t ia = i * A.ld + l, ib = l * B.ld + j;
+      for (int t = 0; t < 2; ++t) {
+        if (!A.limb[ta[t]][(int64_t)(L - 1) * A.plane + ia] || !B.limb[tb[t]][(int64_t)(L - 1) * B.plane + ib])
+          continue;
+        for (int u = 0; u < L; ++u) {
+          Ma[u] = A.limb[ta[t]][(int64_t)u * A.plane + ia];
+          Mb[u] = B.limb[tb[t]][(int64_t)u * B.plane + ib];
+        }
+        for (int u = 0; u < 2 * L; ++u) P[u] = 0;
+        for (int x = 0; x < L; ++x) {
+          uint64_t carry = 0;
+          for (int y = 0; y < L; ++y) {
+            const uint64_t lo = Ma[x] * Mb[y];
+            uint64_t hi = __umul64hi(Ma[x], Mb[y]);
+            uint64_t s = P[x + y] + lo;
+            hi += (s < lo);
+            s += carry;
+            hi += (s < carry);
+            P[x + y] = s;
+            carry = hi;
+          }
+          P[x + L] = carry;
+        }
+        const int64_t es = (int64_t)A.exp[ta[t]][ia] + (int64_t)B.exp[tb[t]][ib];
+        const bool neg = (A.sign[ta[t]][ia] ^ B.sign[tb[t]][ib]) ^ (tsub[t] ? 1 : 0);
+        window_add(win, nw, P, 2 * L, es - 128 * (int64_t)L - xmin, neg);
+      }
+    }
+    const bool neg = (win[nw - 1] >> 63) != 0;
+    if (neg) {
+      uint64_t cc = 1;
+      for (int w = 0; w < nw; ++w) {
+        const uint64_t v = ~win[w] + cc;
+        cc = (cc && v == 0) ? 1ull : 0ull;
+        win[w] = v;
+      }
+    }
+    LimbAcc mag{win};
+    const int N = bitlen(mag, 2 * nw);
+    if (truncated) atomicAdd(reinterpret_cast<int *>(f.status) + kStUncertified, 1);
+    if (N == 0) {
+      store_zero(L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+    } else if (!round_store(mag, 2 * nw, N, neg, xmin, f.p, L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o,
+                            C.plane)) {
+      status_set(f.status, kStErange, 1);
+      store_zero(L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+    }
+  }
+}
+
+__global__ void k_zero_output(OutView C, int64_t m, int64_t n, int L) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * n) return;
+  const int64_t o = (t / n) * C.ld + (t % n);
+  for (int c = 0; c < 2; ++c) store_zero(L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+}
+
+// ---------------------------------------------------------------- launchers
+
+void launch_group_table(const ProductDesc *prods, int n_products, int Q, int gmax, GroupEntry *table,
+                        cudaStream_t st) {
+  ProductDesc z{};
+  k_group_table<<<1, 32, 0, st>>>(prods[0], prods[1], n_products > 2 ? prods[2] : z,
+                                  n_products > 3 ? prods[3] : z, n_products, Q, gmax, table);
+}
+
+void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st) {
+  int T = 128;
+  while (T > 32 && (size_t)2 * a.nslot * T * sizeof(int64_t) > 200 * 1024) T >>= 1;
+  const size_t smem = (size_t)2 * a.nslot * T * sizeof(int64_t);
+  cudaFuncSetAttribute(k_oz_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 g((unsigned)((a.n + T - 1) / T), (unsigned)a.m);
+  k_oz_accum<<<g, T, smem, st>>>(a, C);
+}
+
+void launch_fallback(const FallbackArgs &f, const MatView &A, const MatView &B, const OutView &C, int blocks,
+                     int threads, cudaStream_t st) {
+  k_exact_fallback<<<blocks, threads, 0, st>>>(f, A, B, C);
+}
+
+void launch_zero_output(const OutView &C, int64_t m, int64_t n, int L, cudaStream_t st) {
+  const int64_t tot = m * n;
+  if (tot <= 0) return;
+  k_zero_output<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(C, m, n, L);
+}
+
+}  // namespace mpc

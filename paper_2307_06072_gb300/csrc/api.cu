@@ -1,0 +1,406 @@
+// C ABI of the mpcgemm library: argument checks, the plan (Alg. 2's
+// parameters and the workspace layout) and the launch sequence on the
+// caller's stream.  See include/mpcgemm.h for the contract.
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mpc {
+namespace {
+
+constexpr int kFallbackThreads = 128;
+constexpr int kFallbackBlocks = 64;
+constexpr int kFallbackLimbs = 192;     // exact window of the fallback: 12288 bits
+
+inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+inline int ceil_log2(int64_t k) {
+  int r = 0;
+  while (((int64_t)1 << r) < k) ++r;
+  return r;
+}
+
+struct Plan {
+  mpc_plan pub;
+  ProductDesc prod[4];
+  int kernel;
+};
+
+// Integer bound on the pairs a product drops, in Acc units (dropped level
+// Q + j contributes <= n_{Q+j} k 2^14 2^(-8 j)): k (64 n_{Q+1} + ceil(max_{j>=2} n / 3)).
+uint64_t drop_bound(const ProductDesc &pd, int Q, int64_t k) {
+  const int qmax = pd.a_pos0 + pd.a_npos - 1 + pd.b_pos0 + pd.b_npos - 1;
+  if (Q + 1 > qmax) return 0;
+  const uint64_t n1 = (uint64_t)level_pairs(pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, Q + 1);
+  uint64_t nmax = 0;
+  for (int q = Q + 2; q <= qmax; ++q) {
+    const uint64_t v = (uint64_t)level_pairs(pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, q);
+    if (v > nmax) nmax = v;
+  }
+  return (uint64_t)k * (64 * n1 + (nmax + 2) / 3);
+}
+
+uint64_t ceil_shift(uint64_t v, int beta) {
+  if (beta == 0) return v;
+  if (beta >= 64) return v ? 1 : 0;
+  return (v >> beta) + ((v & ((1ull << beta) - 1)) ? 1 : 0);
+}
+
+int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, const mpc_oz_params *prm,
+              Plan *out) {
+  std::memset(out, 0, sizeof(*out));
+  mpc_plan &P = out->pub;
+  if (m < 0 || n < 0 || k < 0 || p < 1 || p > MPC_MAX_P_BITS || k > MPC_MAX_K) return MPC_EINVAL;
+  if (method != MPC_4M && method != MPC_3M) return MPC_EINVAL;
+  if (algo != MPC_PLAIN && algo != MPC_OZAKI) return MPC_EINVAL;
+  const int L = (p + 63) / 64;
+  P.algo = algo;
+  P.method = method;
+  P.p_bits = p;
+  P.limbs = L;
+  out->kernel = prm ? prm->kernel : MPC_KERNEL_AUTO;
+  if (out->kernel < MPC_KERNEL_AUTO || out->kernel > MPC_KERNEL_MMA_SYNC) return MPC_EINVAL;
+  uint64_t off = 0;
+  P.off_status = off;
+  off = align256(off + kStatusWords * 4);
+  P.off_rowexp = off;
+  off = align256(off + (uint64_t)m * 4);
+  P.off_colexp = off;
+  off = align256(off + (uint64_t)n * 4);
+  P.off_rowlossy = off;
+  off = align256(off + (uint64_t)m * 4);
+  P.off_collossy = off;
+  off = align256(off + (uint64_t)n * 4);
+  P.fallback_capacity = (uint64_t)2 * m * n;
+  P.off_fallback = off;
+  off = align256(off + P.fallback_capacity * 8);
+  P.fb_threads = (uint64_t)kFallbackThreads * kFallbackBlocks;
+  P.fb_scratch_limbs = kFallbackLimbs;
+  P.off_fb_scratch = off;
+  off = align256(off + P.fb_threads * P.fb_scratch_limbs * 8);
+  if (algo == MPC_PLAIN) {
+    const int Lp = L + 1;
+    P.off_fix_a = off;
+    off = align256(off + (uint64_t)2 * Lp * m * k * 8);
+    P.off_fix_b = off;
+    off = align256(off + (uint64_t)2 * Lp * n * k * 8);
+    P.off_digits_a = off;   // fixed-point signs of A, then of B
+    off = align256(off + (uint64_t)2 * m * k);
+    P.off_digits_b = off;
+    off = align256(off + (uint64_t)2 * n * k);
+    P.ws_bytes = off;
+    P.launches = 8;   // init, row max, column max, 2 x fix, plain GEMM, fallback (+1 zero fill when k == 0)
+    return MPC_OK;
+  }
+  // ---- Ozaki: Alg. 2's number of slices and the kept triangle
+  const int guard = (prm && prm->guard_bits > 0) ? prm->guard_bits : kDefaultGuard;
+  int s = (prm && prm->slices > 0) ? prm->slices : (int)((p + ceil_log2(k) + guard + 7) / 8);
+  if (s < 1 || s > kMaxSlices) return MPC_EINVAL;
+  const int Q = (prm && prm->cut_level > 0) ? prm->cut_level - 1 : s - 1;
+  if (Q > 2 * s) return MPC_EINVAL;
+  const int64_t kk = k > 0 ? k : 1;
+  const int gmax = (int)(((int64_t)INT32_MAX) / (kk << kProdLog2));
+  if (gmax < 1) return MPC_EINVAL;
+  P.s = s;
+  P.Q = Q;
+  P.gmax = gmax;
+  P.kpad = (int32_t)(((k + kKBlock - 1) / kKBlock) * kKBlock);
+  P.n_products = method == MPC_4M ? 4 : 3;
+  P.planes_A = P.planes_B = 2 * s + (method == MPC_3M ? s + 1 : 0);
+  // digit sets: re planes [0, s), im [s, 2s), sums [2s, 3s+1) at positions -1 .. s-1
+  const int re0 = 0, im0 = s, sum0 = 2 * s;
+  int total = 0, qmin = 0;
+  for (int pr = 0; pr < P.n_products; ++pr) {
+    ProductDesc &d = out->prod[pr];
+    int a0, b0;
+    if (method == MPC_4M) {
+      a0 = (pr == 0 || pr == 2) ? re0 : im0;       // rr, ii, ri, ir
+      b0 = (pr == 0 || pr == 3) ? re0 : im0;
+      d.a_pos0 = d.b_pos0 = 0;
+      d.a_npos = d.b_npos = s;
+    } else if (pr < 2) {
+      a0 = b0 = pr == 0 ? re0 : im0;               // rr, ii
+      d.a_pos0 = d.b_pos0 = 0;
+      d.a_npos = d.b_npos = s;
+    } else {
+      a0 = b0 = sum0;                               // ss
+      d.a_pos0 = d.b_pos0 = -1;
+      d.a_npos = d.b_npos = s + 1;
+    }
+    d.a_plane0 = a0;
+    d.b_plane0 = b0;
+    d.group0 = total;
+    d.n_groups = build_groups(pr, d.a_pos0, d.a_npos, d.b_pos0, d.b_npos, Q, gmax, nullptr, 0);
+    P.n_groups[pr] = d.n_groups;
+    total += d.n_groups;
+    if (d.a_pos0 + d.b_pos0 < qmin) qmin = d.a_pos0 + d.b_pos0;
+  }
+  P.n_groups_total = total;
+  P.acc_slots = (8 * (Q - qmin) + 64) / 32 + 3;
+  // bounds: b = bound_drop[c] + k (lossyA * bound_lossy_a[c] + lossyB * bound_lossy_b[c]), times 2^beta
+  const int beta = 15 + 8 * (Q - s) > 0 ? 15 + 8 * (Q - s) : 0;
+  P.bound_shift = beta;
+  for (int c = 0; c < 2; ++c) {
+    int prods[3], np = 0;
+    if (c == 0) { prods[np++] = 0; prods[np++] = 1; }
+    else if (method == MPC_4M) { prods[np++] = 2; prods[np++] = 3; }
+    else { prods[np++] = 2; prods[np++] = 0; prods[np++] = 1; }
+    uint64_t bd = 0, la = 0, lb = 0;
+    for (int x = 0; x < np; ++x) {
+      const ProductDesc &d = out->prod[prods[x]];
+      bd += ceil_shift(drop_bound(d, Q, k), beta);
+      const uint64_t cf = (d.a_pos0 < 0) ? 2 : 1;   // sums: 2 ulps truncation, |.| < 2^(E+1)
+      la += cf * cf;
+      lb += cf * cf;
+    }
+    P.bound_drop[c] = bd;
+    P.bound_lossy_a[c] = la;
+    P.bound_lossy_b[c] = lb;
+  }
+  P.off_digits_a = off;
+  off = align256(off + (uint64_t)P.planes_A * m * P.kpad * 2);
+  P.off_digits_b = off;
+  off = align256(off + (uint64_t)P.planes_B * n * P.kpad * 2);
+  P.off_groups = off;
+  off = align256(off + (uint64_t)total * m * n * 4);
+  P.off_group_table = off;
+  off = align256(off + (uint64_t)total * sizeof(GroupEntry));
+  P.ws_bytes = off;
+  P.launches = 9;     // init, row max, column max, group table, 2 x digits, slice GEMM, accumulate, fallback
+  return MPC_OK;
+}
+
+int cuda_code(cudaError_t e) { return e == cudaSuccess ? MPC_OK : MPC_ECUDA - (int)e; }
+
+bool mat_ok(const mpc_mat *X, int64_t rows, int64_t cols) {
+  if (!X || X->rows != rows || X->cols != cols || X->ld < cols || X->ld < 1) return false;
+  if (rows * cols == 0) return true;
+  for (int c = 0; c < 2; ++c)
+    if (!X->sign[c] || !X->exp[c] || !X->limb[c]) return false;
+  return true;
+}
+
+MatView view_of(const mpc_mat *X) {
+  MatView v;
+  for (int c = 0; c < 2; ++c) {
+    v.sign[c] = X->sign[c];
+    v.exp[c] = X->exp[c];
+    v.limb[c] = X->limb[c];
+  }
+  v.rows = X->rows;
+  v.cols = X->cols;
+  v.ld = X->ld;
+  v.plane = X->rows * X->ld;
+  return v;
+}
+
+OutView out_of(mpc_mat *X) {
+  OutView v;
+  for (int c = 0; c < 2; ++c) {
+    v.sign[c] = X->sign[c];
+    v.exp[c] = X->exp[c];
+    v.limb[c] = X->limb[c];
+  }
+  v.rows = X->rows;
+  v.cols = X->cols;
+  v.ld = X->ld;
+  v.plane = X->rows * X->ld;
+  return v;
+}
+
+}  // namespace
+}  // namespace mpc
+
+using namespace mpc;
+
+extern "C" {
+
+int mpcgemm_plan(int64_t m, int64_t n, int64_t k, int32_t p_bits, int method, int algo,
+                 const mpc_oz_params *params, mpc_plan *out) {
+  if (!out) return MPC_EINVAL;
+  Plan pl;
+  const int rc = make_plan(m, n, k, p_bits, method, algo, params, &pl);
+  if (rc == MPC_OK) *out = pl.pub;
+  return rc;
+}
+
+size_t mpcgemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t p_bits, int method, int algo) {
+  Plan pl;
+  if (make_plan(m, n, k, p_bits, method, algo, nullptr, &pl) != MPC_OK) return 0;
+  return (size_t)pl.pub.ws_bytes;
+}
+
+int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_mat *A, const mpc_mat *B,
+                     mpc_mat *C, int method, int algo, const mpc_oz_params *params, const mpc_stage_events *events,
+                     void *workspace, size_t ws_bytes, void *stream) {
+  Plan pl;
+  int rc = make_plan(m, n, k, p_bits, method, algo, params, &pl);
+  if (rc != MPC_OK) return rc;
+  if (!mat_ok(A, m, k) || !mat_ok(B, k, n) || !mat_ok(C, m, n)) return MPC_EINVAL;
+  if (m == 0 || n == 0) return MPC_OK;
+  if (!workspace || ((uintptr_t)workspace & 255)) return MPC_EINVAL;
+  if (ws_bytes < pl.pub.ws_bytes) return MPC_ENOSPC;
+  cudaStream_t st = (cudaStream_t)stream;
+  const mpc_plan &P = pl.pub;
+  const int L = P.limbs;
+  char *ws = (char *)workspace;
+  int32_t *status = (int32_t *)(ws + P.off_status);
+  int32_t *E = (int32_t *)(ws + P.off_rowexp), *F = (int32_t *)(ws + P.off_colexp);
+  int32_t *lossyA = (int32_t *)(ws + P.off_rowlossy), *lossyB = (int32_t *)(ws + P.off_collossy);
+  int64_t *fallback = (int64_t *)(ws + P.off_fallback);
+  OutView Cv = out_of(C);
+  cudaGetLastError();   // clear a stale error of an earlier, unrelated call
+  auto mark = [&](int x) {
+    if (events && events->ev[x]) cudaEventRecord((cudaEvent_t)events->ev[x], st);
+  };
+  mark(0);
+  launch_init(status, E, m, F, n, lossyA, lossyB, st);
+  if (k == 0) {
+    launch_zero_output(Cv, m, n, L, st);
+    for (int x = 1; x <= 4; ++x) mark(x);
+    return cuda_code(cudaGetLastError());
+  }
+  MatView Av = view_of(A), Bv = view_of(B);
+  launch_line_max(Av, Bv, m, n, k, L, E, F, st);
+  FallbackArgs fa{};
+  fa.m = m;
+  fa.n = n;
+  fa.k = k;
+  fa.p = p_bits;
+  fa.L = L;
+  fa.list = fallback;
+  fa.cap = (int64_t)P.fallback_capacity;
+  fa.scratch = (uint64_t *)(ws + P.off_fb_scratch);
+  fa.scratch_limbs = (int)P.fb_scratch_limbs;
+  fa.status = status;
+  if (algo == MPC_PLAIN) {
+    const int Lp = L + 1;
+    uint64_t *fixA = (uint64_t *)(ws + P.off_fix_a), *fixB = (uint64_t *)(ws + P.off_fix_b);
+    uint8_t *sgA = (uint8_t *)(ws + P.off_digits_a), *sgB = (uint8_t *)(ws + P.off_digits_b);
+    launch_plain_fix(Av, 0, m, k, L, Lp, E, lossyA, fixA, sgA, st);
+    launch_plain_fix(Bv, 1, n, k, L, Lp, F, lossyB, fixB, sgB, st);
+    mark(1);
+    PlainArgs pa{};
+    pa.fixA = fixA;
+    pa.fixB = fixB;
+    pa.sgnA = sgA;
+    pa.sgnB = sgB;
+    pa.m = m;
+    pa.n = n;
+    pa.k = k;
+    pa.p = p_bits;
+    pa.L = L;
+    pa.Lp = Lp;
+    pa.E = E;
+    pa.F = F;
+    pa.lossyA = lossyA;
+    pa.lossyB = lossyB;
+    pa.fallback = fallback;
+    pa.fallback_cap = (int64_t)P.fallback_capacity;
+    pa.status = status;
+    launch_plain_gemm(pa, Cv, st);
+    mark(2);
+    mark(3);
+  } else {
+    __nv_bfloat16 *dA = (__nv_bfloat16 *)(ws + P.off_digits_a), *dB = (__nv_bfloat16 *)(ws + P.off_digits_b);
+    GroupEntry *table = (GroupEntry *)(ws + P.off_group_table);
+    int32_t *planes = (int32_t *)(ws + P.off_groups);
+    const int want_sum = method == MPC_3M;
+    launch_group_table(pl.prod, P.n_products, P.Q, P.gmax, table, st);
+    launch_oz_digits(Av, 0, m, k, P.kpad, L, P.s, want_sum, E, lossyA, dA, st);
+    launch_oz_digits(Bv, 1, n, k, P.kpad, L, P.s, want_sum, F, lossyB, dB, st);
+    mark(1);
+    SliceGemmArgs sa{};
+    sa.dA = dA;
+    sa.dB = dB;
+    sa.m = m;
+    sa.n = n;
+    sa.kpad = P.kpad;
+    sa.groups = table;
+    sa.n_entries = P.n_groups_total;
+    for (int x = 0; x < 4; ++x) sa.prod[x] = pl.prod[x];
+    sa.out = planes;
+    sa.status = status;
+    if (pl.kernel == MPC_KERNEL_MMA_SYNC) {
+      launch_slicegemm_mma(sa, st);
+    } else {
+      const cudaError_t e = launch_slicegemm_tc(sa, st);
+      if (e == cudaErrorNotSupported && pl.kernel == MPC_KERNEL_AUTO) launch_slicegemm_mma(sa, st);
+      else if (e != cudaSuccess) return cuda_code(e);
+    }
+    mark(2);
+    AccumArgs aa{};
+    aa.planes = planes;
+    aa.groups = table;
+    aa.n_entries = P.n_groups_total;
+    aa.m = m;
+    aa.n = n;
+    aa.k = k;
+    aa.p = p_bits;
+    aa.L = L;
+    aa.Q = P.Q;
+    aa.nslot = P.acc_slots;
+    aa.method = method;
+    aa.E = E;
+    aa.F = F;
+    aa.lossyA = lossyA;
+    aa.lossyB = lossyB;
+    aa.bound_shift = P.bound_shift;
+    for (int c = 0; c < 2; ++c) {
+      aa.bound_drop[c] = P.bound_drop[c];
+      aa.bound_lossy_a[c] = P.bound_lossy_a[c];
+      aa.bound_lossy_b[c] = P.bound_lossy_b[c];
+    }
+    aa.fallback = fallback;
+    aa.fallback_cap = (int64_t)P.fallback_capacity;
+    aa.status = status;
+    launch_oz_accum(aa, Cv, st);
+    mark(3);
+  }
+  launch_fallback(fa, Av, Bv, Cv, kFallbackBlocks, kFallbackThreads, st);
+  mark(4);
+  return cuda_code(cudaGetLastError());
+}
+
+int mpcgemm_ex(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_mat *A, const mpc_mat *B, mpc_mat *C,
+               int method, int algo, const mpc_oz_params *params, void *workspace, size_t ws_bytes,
+               void *stream) {
+  return mpcgemm_profiled(m, n, k, p_bits, A, B, C, method, algo, params, nullptr, workspace, ws_bytes, stream);
+}
+
+int mpcgemm(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_mat *A, const mpc_mat *B, mpc_mat *C,
+            int method, int algo, void *workspace, size_t ws_bytes, void *stream) {
+  return mpcgemm_ex(m, n, k, p_bits, A, B, C, method, algo, nullptr, workspace, ws_bytes, stream);
+}
+
+int mpcgemm_read_status(const void *workspace, size_t ws_bytes, mpc_status *status, void *stream) {
+  if (!workspace || !status || ws_bytes < kStatusWords * 4) return MPC_EINVAL;
+  int32_t words[kStatusWords];
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemcpy(words, workspace, sizeof(words), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_code(e);
+  status->erange = words[kStErange];
+  status->fallback_entries = words[kStFallbackCount];
+  status->fallback_overflow = words[kStFallbackOverflow];
+  status->uncertified = words[kStUncertified];
+  return status->erange ? MPC_ERANGE : MPC_OK;
+}
+
+const char *mpcgemm_strerror(int code) {
+  switch (code) {
+    case MPC_OK: return "success";
+    case MPC_EINVAL: return "invalid argument (size, precision, pointer, method or parameter)";
+    case MPC_ENOSPC: return "workspace too small";
+    case MPC_ERANGE: return "result exponent outside int32";
+    case MPC_ENOTSUP: return "not supported on this device";
+    default: break;
+  }
+  if (code <= MPC_ECUDA) return cudaGetErrorString((cudaError_t)(MPC_ECUDA - code));
+  return "unknown error";
+}
+
+int mpcgemm_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,247 @@
+// oz_split: the first half of Alg. 2 (Kouya, Sec. III-C) on the GPU.
+//
+//  * k_rowmax / k_colmax: mu_A / mu_B of Alg. 2 as exponents -- E_i, the
+//    largest exponent of row i of A over the real AND imaginary planes (one
+//    split for both parts, last paragraph of Sec. III-C), F_j likewise for
+//    column j of B.  Every |a_il| < 2^E_i.
+//  * k_oz_digits: the split itself.  Alg. 2 cuts A on a grid set by tau into
+//    short floats whose products are exact.  Here the grid is fixed per row:
+//    X = sign * floor(|a| 2^(8s-1-E)) and X is written in s balanced base-256
+//    digits (|d| <= 128, exact in bf16, products exact), most significant
+//    first; digit t stands for slice A_{t+1}.  For the 3M form (Eq. 3m_way)
+//    the digits of X_re + X_im are produced as well (s+1 digits).  B is split
+//    by columns and stored transposed (K-major), as the tensor cores read it.
+//  * k_plain_fix: the plain path's fixed-point operands (L+1 limbs).
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mpc {
+
+__device__ __forceinline__ bool comp_nonzero(const MatView &X, int c, int64_t idx, int L) {
+  return X.limb[c][(int64_t)(L - 1) * X.plane + idx] != 0;
+}
+
+// E for each row of A (m x k): block per row, threads stride the row.
+__global__ void k_rowmax(MatView A, int64_t m, int64_t k, int L, int32_t *E) {
+  int64_t i = blockIdx.x;
+  if (i >= m) return;
+  int best = INT32_MIN;
+  for (int64_t l = threadIdx.x; l < k; l += blockDim.x) {
+    int64_t idx = i * A.ld + l;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      if (comp_nonzero(A, c, idx, L)) best = max(best, A.exp[c][idx]);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  __shared__ int red[32];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[w] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int r = INT32_MIN;
+    for (int v = 0; v < (int)(blockDim.x >> 5); ++v) r = max(r, red[v]);
+    E[i] = r;
+  }
+}
+
+// F for each column of B (k x n): threads over columns, blocks over row chunks.
+__global__ void k_colmax(MatView B, int64_t k, int64_t n, int L, int rows_per_block, int32_t *F) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int64_t l0 = (int64_t)blockIdx.y * rows_per_block;
+  int64_t l1 = min(k, l0 + rows_per_block);
+  int best = INT32_MIN;
+  for (int64_t l = l0; l < l1; ++l) {
+    int64_t idx = l * B.ld + j;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      if (comp_nonzero(B, c, idx, L)) best = max(best, B.exp[c][idx]);
+  }
+  if (best != INT32_MIN) atomicMax(F + j, best);
+}
+
+__global__ void k_init(int32_t *status, int32_t *E, int64_t m, int32_t *F, int64_t n, int32_t *lossyA,
+                       int32_t *lossyB) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < kStatusWords) status[t] = 0;
+  if (t < m) { E[t] = INT32_MIN; lossyA[t] = 0; }
+  if (t < n) { F[t] = INT32_MIN; lossyB[t] = 0; }
+}
+
+// 8 bits of the L-limb integer M starting at bit b (zero outside [0, 64L)).
+__device__ __forceinline__ uint32_t byte_at(const uint64_t *M, int L, int64_t b) {
+  if (b >= 64 * (int64_t)L || b <= -8) return 0;
+  int64_t w = b >> 6;                 // floor division (b may be negative)
+  int off = (int)(b & 63);
+  uint64_t lo = (w >= 0 && w < L) ? M[w] : 0ull;
+  uint64_t hi = (w + 1 >= 0 && w + 1 < L) ? M[w + 1] : 0ull;
+  uint64_t v = off ? ((lo >> off) | (hi << (64 - off))) : lo;
+  return (uint32_t)(v & 0xFFu);
+}
+
+// true iff every bit of M below bit `nb` is zero
+__device__ __forceinline__ bool low_bits_zero(const uint64_t *M, int L, int64_t nb) {
+  if (nb <= 0) return true;
+  for (int j = 0; j < L; ++j) {
+    int64_t lo = 64 * (int64_t)j;
+    if (lo >= nb) break;
+    int64_t take = nb - lo;
+    uint64_t mask = take >= 64 ? ~0ull : ((1ull << take) - 1ull);
+    if (M[j] & mask) return false;
+  }
+  return true;
+}
+
+// One thread per (line, l): digits of element (line, l) of the operand.
+// Side A: line = row i, element (i, l).  Side B: line = column j, element (l, j).
+// Output planes: digits[(plane * lines + line) * kpad + l], plane = t (real),
+// s + t (imaginary), 2s + 1 + t (sums, t = -1 .. s-1).
+__global__ void k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
+                            int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits) {
+  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t line = blockIdx.y;
+  if (l >= kpad || line >= lines) return;
+  const int64_t pstride = lines * kpad;
+  __nv_bfloat16 *out = digits + line * kpad + l;
+  const int nplanes = 2 * s + (want_sum ? s + 1 : 0);
+  int32_t e_line = E[line];
+  if (l >= k || e_line == INT32_MIN) {
+    for (int pl = 0; pl < nplanes; ++pl) out[pl * pstride] = __float2bfloat16_rn(0.0f);
+    return;
+  }
+  int64_t idx = side == 0 ? line * X.ld + l : l * X.ld + line;
+  uint64_t M[2][kMaxLimbs];
+  int64_t sh[2];
+  int neg[2];
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    bool nz = comp_nonzero(X, c, idx, L);
+    for (int j = 0; j < L; ++j) M[c][j] = nz ? X.limb[c][(int64_t)j * X.plane + idx] : 0ull;
+    // |X| bit b  <->  M bit b + sh:  X = |v| 2^(8s-1-E), |v| = M 2^(exp-64L)
+    sh[c] = nz ? (64 * (int64_t)L + (int64_t)e_line - (int64_t)X.exp[c][idx] - (8 * (int64_t)s - 1)) : 0;
+    neg[c] = nz ? X.sign[c][idx] : 0;
+    if (nz) {
+      if (sh[c] >= 64 * (int64_t)L) ok = false;            // every bit dropped (M != 0)
+      else if (!low_bits_zero(M[c], L, sh[c])) ok = false;  // some low bits dropped
+    }
+  }
+  if (!ok) atomicOr(lossy + line, 1);
+  // walk the bytes of the two's-complement integers from the bottom
+  int cneg[2] = {1, 1}, cbal[2] = {0, 0};
+  int csum = 0, cbal_s = 0;
+  for (int pos = 0; pos <= s; ++pos) {
+    int bt[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      uint32_t b = (pos < s) ? byte_at(M[c], L, 8 * (int64_t)pos + sh[c]) : 0u;
+      if (neg[c]) {
+        uint32_t v = ((~b) & 0xFFu) + (uint32_t)cneg[c];
+        cneg[c] = (int)(v >> 8);
+        b = v & 0xFFu;
+      }
+      bt[c] = (int)b;
+      if (pos < s) {
+        int d;
+        if (pos == s - 1) {
+          d = (int)(int8_t)(uint8_t)b + cbal[c];            // top digit: signed byte + carry
+        } else {
+          d = (int)b + cbal[c];
+          cbal[c] = d >= 128;
+          if (d >= 128) d -= 256;
+        }
+        int plane = c * s + (s - 1 - pos);
+        out[plane * pstride] = __float2bfloat16_rn((float)d);
+      }
+    }
+    if (want_sum) {
+      int S = bt[0] + bt[1] + csum;
+      csum = S >> 8;
+      S &= 0xFF;
+      int d;
+      if (pos == s) {
+        d = (int)(int8_t)(uint8_t)S + cbal_s;
+      } else {
+        d = S + cbal_s;
+        cbal_s = d >= 128;
+        if (d >= 128) d -= 256;
+      }
+      int plane = 2 * s + (s - pos);   // position t = s-1-pos -> plane 2s + 1 + t
+      out[plane * pstride] = __float2bfloat16_rn((float)d);
+    }
+  }
+}
+
+// Plain path: X = floor(|a| 2^(64 Lp - E)) as Lp limbs (Lp = L + 1), sign kept apart.
+// Layout: fix[(c * Lp + j) * lines * k + line * k + l], fsign[c * lines * k + line * k + l].
+__global__ void k_plain_fix(MatView X, int side, int64_t lines, int64_t k, int L, int Lp, const int32_t *E,
+                            int32_t *lossy, uint64_t *fix, uint8_t *fsign) {
+  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t line = blockIdx.y;
+  if (l >= k || line >= lines) return;
+  const int64_t plane = lines * k;
+  const int64_t o = line * k + l;
+  int32_t e_line = E[line];
+  int64_t idx = side == 0 ? line * X.ld + l : l * X.ld + line;
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    bool nz = (e_line != INT32_MIN) && comp_nonzero(X, c, idx, L);
+    uint64_t M[kMaxLimbs];
+    for (int j = 0; j < L; ++j) M[j] = nz ? X.limb[c][(int64_t)j * X.plane + idx] : 0ull;
+    // |X| bit b <-> M bit b - sl, sl = 64(Lp - L) - (E - exp)
+    int64_t sl = nz ? (64 * (int64_t)(Lp - L) - ((int64_t)e_line - (int64_t)X.exp[c][idx])) : 0;
+    if (nz && sl < 0) {
+      if (-sl >= 64 * (int64_t)L || !low_bits_zero(M, L, -sl)) ok = false;
+    }
+    for (int j = 0; j < Lp; ++j) {
+      uint64_t v = 0;
+      if (nz) {
+        int64_t b = 64 * (int64_t)j - sl;   // M bit of X bit 64j
+        if (b < 64 * (int64_t)L && b > -64) {
+          int64_t w = b >> 6;
+          int off = (int)(b & 63);
+          uint64_t lo = (w >= 0 && w < L) ? M[w] : 0ull;
+          uint64_t hi = (w + 1 >= 0 && w + 1 < L) ? M[w + 1] : 0ull;
+          v = off ? ((lo >> off) | (hi << (64 - off))) : lo;
+        }
+      }
+      fix[((int64_t)c * Lp + j) * plane + o] = v;
+    }
+    fsign[(int64_t)c * plane + o] = nz ? X.sign[c][idx] : 0;
+  }
+  if (!ok) atomicOr(lossy + line, 1);
+}
+
+// ---------------------------------------------------------------- launchers
+
+void launch_init(int32_t *status, int32_t *E, int64_t m, int32_t *F, int64_t n, int32_t *lossyA, int32_t *lossyB,
+                 cudaStream_t st) {
+  int64_t tot = m > n ? m : n;
+  if (tot < kStatusWords) tot = kStatusWords;
+  k_init<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(status, E, m, F, n, lossyA, lossyB);
+}
+
+void launch_line_max(const MatView &A, const MatView &B, int64_t m, int64_t n, int64_t k, int L, int32_t *E,
+                     int32_t *F, cudaStream_t st) {
+  k_rowmax<<<(unsigned)m, 256, 0, st>>>(A, m, k, L, E);
+  const int rpb = 64;
+  dim3 g((unsigned)((n + 127) / 128), (unsigned)((k + rpb - 1) / rpb));
+  k_colmax<<<g, 128, 0, st>>>(B, k, n, L, rpb, F);
+}
+
+void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
+                      int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, cudaStream_t st) {
+  dim3 g((unsigned)((kpad + 127) / 128), (unsigned)lines);
+  k_oz_digits<<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits);
+}
+
+void launch_plain_fix(const MatView &X, int side, int64_t lines, int64_t k, int L, int Lp, const int32_t *E,
+                      int32_t *lossy, uint64_t *fix, uint8_t *fsign, cudaStream_t st) {
+  dim3 g((unsigned)((k + 127) / 128), (unsigned)lines);
+  k_plain_fix<<<g, 128, 0, st>>>(X, side, lines, k, L, Lp, E, lossy, fix, fsign);
+}
+
+}  // namespace mpc

@@ -1,0 +1,123 @@
+"""C-ABI library: builds, loads without a GPU, exports every declared symbol,
+rejects bad arguments on the host, and plans like the oracle (no GPU compute)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import ozaki
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mpcgemm.h")
+
+
+@pytest.fixture(scope="module")
+def mp():
+    from paper_2307_06072_gb300 import build
+    build.build()
+    import paper_2307_06072_gb300 as mp
+    return mp
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpcgemm\w*)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(mp):
+    names = declared_functions()
+    assert "mpcgemm" in names and "mpcgemm_plan" in names and len(names) >= 8
+    lib = ctypes.CDLL(mp._native.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(mp._native.EXPORTED)
+
+
+def test_version_and_strerror(mp):
+    assert mp.version() >= 100
+    assert "workspace" in mp.strerror(-28)
+    assert "exponent" in mp.strerror(-34)
+
+
+def _dummy_mat(rows, cols, ld=None):
+    m = mp_native().MpcMat()
+    m.rows, m.cols, m.ld = rows, cols, cols if ld is None else ld
+    for c in range(2):
+        m.sign[c] = m.exp[c] = m.limb[c] = 0x1000 * (c + 1)   # never dereferenced
+    return m
+
+
+def mp_native():
+    import paper_2307_06072_gb300._native as n
+    return n
+
+
+@pytest.mark.parametrize("m,n,k,p,method,algo,code", [
+    (4, 4, 4, 0, 0, 1, -22), (4, 4, 4, 1025, 0, 1, -22), (4, 4, 131072, 128, 0, 1, -22),
+    (4, 4, 4, 128, 2, 1, -22), (4, 4, 4, 128, 0, 2, -22), (-1, 4, 4, 128, 0, 1, -22)])
+def test_bad_arguments_rejected_on_host(mp, m, n, k, p, method, algo, code):
+    A, B, C = _dummy_mat(max(m, 0), max(k, 0)), _dummy_mat(max(k, 0), n), _dummy_mat(max(m, 0), n)
+    rc = mp.lib().mpcgemm(m, n, k, p, ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), method, algo,
+                          ctypes.c_void_p(0x100000), 1 << 40, None)
+    assert rc == code
+
+
+def test_shape_mismatch_and_workspace_checks(mp):
+    A, B, C = _dummy_mat(8, 5), _dummy_mat(6, 7), _dummy_mat(8, 7)
+    lib = mp.lib()
+    assert lib.mpcgemm(8, 7, 5, 128, ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), 0, 1,
+                       ctypes.c_void_p(0x100000), 1 << 40, None) == -22
+    B = _dummy_mat(5, 7)
+    Cbad = _dummy_mat(8, 7, ld=3)
+    assert lib.mpcgemm(8, 7, 5, 128, ctypes.byref(A), ctypes.byref(B), ctypes.byref(Cbad), 0, 1,
+                       ctypes.c_void_p(0x100000), 1 << 40, None) == -22
+    need = lib.mpcgemm_workspace_size(8, 7, 5, 128, 0, 1)
+    assert need > 0
+    assert lib.mpcgemm(8, 7, 5, 128, ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), 0, 1,
+                       ctypes.c_void_p(0x100000), need - 1, None) == -28
+    assert lib.mpcgemm(8, 7, 5, 128, ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), 0, 1,
+                       ctypes.c_void_p(0x100001), need, None) == -22   # misaligned workspace
+    # m == 0: a no-op that succeeds without touching anything
+    Z = _dummy_mat(0, 5)
+    Cz = _dummy_mat(0, 7)
+    assert lib.mpcgemm(0, 7, 5, 128, ctypes.byref(Z), ctypes.byref(B), ctypes.byref(Cz), 0, 1,
+                       ctypes.c_void_p(0x100000), need, None) == 0
+
+
+@pytest.mark.parametrize("p,k,method,guard,s,Q", [
+    (128, 32, "4m", None, None, None), (256, 256, "4m", None, None, None), (256, 256, "3m", None, None, None),
+    (1024, 2048, "3m", None, None, None), (512, 1024, "4m", 8, None, None), (128, 9, "3m", 0, None, 3),
+    (128, 8, "4m", None, 10, 18), (192, 2048, "3m", None, 30, 33)])
+def test_plan_matches_the_oracle_parameters(mp, p, k, method, guard, s, Q):
+    """s, Q, group counts and bound constants of the C plan equal O2's."""
+    prm = ozaki.make_params(p, k, method, guard if guard is not None else ozaki.DEFAULT_GUARD, s, Q)
+    params = dict(guard_bits=guard or 0, slices=s or 0, cut_level=(Q + 1) if Q is not None else 0)
+    if guard == 0:
+        params["guard_bits"] = 0
+        prm = ozaki.make_params(p, k, method, ozaki.DEFAULT_GUARD, s, Q)   # 0 means default in the ABI
+    pl = mp.plan(64, 48, k, p, method, "ozaki", params)
+    assert (pl["s"], pl["Q"], pl["gmax"]) == (prm.s, prm.Q, prm.gmax)
+    first = {"re": 0, "im": 0, "sum": -1}
+    npos = {"re": prm.s, "im": prm.s, "sum": prm.s + 1}
+    for idx, pr in enumerate(prm.products):
+        wa, wb = ozaki.PRODUCT_OPERANDS[pr]
+        gs = ozaki.groups_for((first[wa], first[wa] + npos[wa] - 1), (first[wb], first[wb] + npos[wb] - 1),
+                              prm.Q, prm.gmax)
+        assert pl["n_groups"][idx] == len(gs)
+    # the bound constants: compare with entry_bound on synthetic split summaries
+    class FakeSplit:
+        def __init__(self, lossless):
+            self.E = [0]
+            self.lossless = [lossless]
+            self.first_pos = first
+            self.digits = {w: np.zeros((npos[w], 1, 1)) for w in ("re", "im", "sum")}
+    for la in (True, False):
+        for lb in (True, False):
+            for c, comp in enumerate(("re", "im")):
+                b, beta = ozaki.entry_bound(prm, FakeSplit(la), FakeSplit(lb), 0, 0, comp)
+                want = pl["bound_drop"][c] + k * ((0 if la else pl["bound_lossy_a"][c]) +
+                                                  (0 if lb else pl["bound_lossy_b"][c]))
+                assert (b, beta) == (want, pl["bound_shift"])

@@ -1,0 +1,198 @@
+"""CUDA path vs the oracle, through the C ABI.
+
+Integer stages (digits, group sums) must equal O2 bit for bit; every output
+must equal O1 = RN_p(exact product) bit for bit (certified rounding plus exact
+fallback make the result the correctly rounded product).  Each case also
+reports the error in units of 2^-p, which is 0 or <= 1/2 ulp by construction.
+"""
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import c_oracle, exact, ozaki
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_against_o1(C, A, B, p):
+    ref = c_oracle.rounded_cgemm_matrix(A, B, p)
+    bad = gu.mismatches(C, ref)
+    assert len(bad) == 0, f"{len(bad)} mismatching components, first {bad[:5].tolist()}"
+
+
+def test_plain_config0_bit_exact():
+    A, B, p = si.make_config("c0_plain_32_p128")
+    C, ws, st = gu.run(A, B, p, "4m", "plain")
+    assert gu.same(C, exact.rounded_cgemm(A, B, p))
+    assert st["erange"] == 0
+
+
+@pytest.mark.parametrize("method", ["4m", "3m"])
+@pytest.mark.parametrize("dist,zf", [("uniform", 0.0), ("uniform_exp", 0.1)])
+def test_ozaki_ragged_tiles_bit_exact(method, dist, zf):
+    """Several 128 x 128 tiles with ragged edges and a k tail (k = 150 -> kpad 192)."""
+    p = 128
+    A = si.random_matrix(200, 150, p, 301, dist, zero_frac=zf)
+    B = si.random_matrix(150, 300, p, 302, dist, zero_frac=zf)
+    C, ws, st = gu.run(A, B, p, method, "ozaki")
+    _check_against_o1(C, A, B, p)
+    assert st["fallback_overflow"] == 0 and st["uncertified"] == 0
+
+
+def test_plain_ragged_bit_exact():
+    p = 192
+    A = si.random_matrix(37, 70, p, 311, "uniform_exp", zero_frac=0.1)
+    B = si.random_matrix(70, 29, p, 312, "uniform_exp")
+    C, ws, st = gu.run(A, B, p, "4m", "plain")
+    _check_against_o1(C, A, B, p)
+
+
+@pytest.mark.parametrize("method", ["4m", "3m"])
+def test_config1_stage_parity(method):
+    """256^3, p = 256: digits and every group sum equal O2; output equals O1."""
+    A, B, p = si.make_config("c1_ozaki_256_p256")
+    C, ws, st = gu.run(A, B, p, method, "ozaki")
+    pl = gu.plan(A, B, p, method)
+    r = ozaki.ozaki_cgemm(A, B, p, method, fallback=lambda i, j: ((0, 0), (0, 0)))
+    s, kp, k = r.params.s, pl["kpad"], A.cols
+    dA = gu.ws_digits(ws, pl, "A", A.rows)
+    dB = gu.ws_digits(ws, pl, "B", B.cols)
+    assert np.array_equal(dA[:s, :, :k], r.splitA.digits["re"])
+    assert np.array_equal(dA[s:2 * s, :, :k], r.splitA.digits["im"])
+    assert np.array_equal(dB[:s, :, :k], r.splitB.digits["re"])
+    assert np.array_equal(dB[s:2 * s, :, :k], r.splitB.digits["im"])
+    if method == "3m":
+        assert np.array_equal(dA[2 * s:, :, :k], r.splitA.digits["sum"])
+        assert np.array_equal(dB[2 * s:, :, :k], r.splitB.digits["sum"])
+    assert not np.any(dA[:, :, k:]) and not np.any(dB[:, :, k:])
+    G = gu.ws_groups(ws, pl, A.rows, B.cols)
+    e = 0
+    for pr in r.params.products:
+        for Gref in r.group_sums[pr]:
+            assert np.array_equal(G[e], Gref), (pr, e)
+            e += 1
+    assert e == G.shape[0]
+    assert st["fallback_entries"] == int((~r.certified).sum())
+    _check_against_o1(C, A, B, p)
+
+
+@pytest.mark.parametrize("method", ["4m", "3m"])
+def test_forced_fallbacks_stay_exact(method):
+    """Two guard bits: many components fail certification and are recomputed exactly."""
+    p = 128
+    A = si.random_matrix(40, 33, p, 321, "uniform_exp")
+    B = si.random_matrix(33, 50, p, 322, "uniform_exp")
+    C, ws, st = gu.run(A, B, p, method, "ozaki", params=dict(guard_bits=1))
+    r = ozaki.ozaki_cgemm(A, B, p, method, guard=1, fallback=lambda i, j: ((0, 0), (0, 0)))
+    assert st["fallback_entries"] == int((~r.certified).sum()) > 0
+    _check_against_o1(C, A, B, p)
+
+
+def test_full_pair_set_lossless_is_exact_without_fallback():
+    p = 128
+    A = si.random_matrix(64, 40, p, 331)
+    B = si.random_matrix(40, 64, p, 332)
+    prm = ozaki.make_params(p, 40, "4m", guard=70)
+    C, ws, st = gu.run(A, B, p, "4m", "ozaki", params=dict(guard_bits=70, cut_level=2 * prm.s))
+    assert st["fallback_entries"] == 0
+    _check_against_o1(C, A, B, p)
+
+
+def test_methods_and_algorithms_agree_bitwise():
+    p = 320
+    A = si.random_matrix(150, 140, p, 341, "uniform_exp")
+    B = si.random_matrix(140, 130, p, 342, "uniform_exp")
+    outs = [gu.run(A, B, p, m_, a_)[0] for m_, a_ in (("4m", "ozaki"), ("3m", "ozaki"), ("4m", "plain"))]
+    assert gu.same(outs[0], outs[1]) and gu.same(outs[0], outs[2])
+    _check_against_o1(outs[0], A, B, p)
+
+
+# ------------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("algo", ["ozaki", "plain"])
+def test_k_zero_gives_zero(algo):
+    p = 128
+    A = si.random_matrix(5, 0, p, 1)
+    B = si.random_matrix(0, 7, p, 2)
+    C, ws, st = gu.run(A, B, p, "4m", algo)
+    assert not C.limb.any() and not C.sign.any() and np.all(C.exp == si.INT32_MIN)
+
+
+@pytest.mark.parametrize("algo,method", [("ozaki", "4m"), ("ozaki", "3m"), ("plain", "4m")])
+def test_zero_rows_columns_identity_and_padded_ld(algo, method):
+    p = 256
+    A = si.random_matrix(20, 20, p, 351, "uniform_exp")
+    A.limb[:, :, 3, :] = 0          # zero row
+    A.limb[0, :, 7, :] = 0          # row with a zero real part
+    B = si.identity_matrix(20, p)
+    C, ws, st = gu.run(A, B, p, method, algo, ld_pad=5)
+    Aref = exact.rounded_cgemm(A, si.identity_matrix(20, p), p)
+    assert gu.same(C, Aref)
+    B2 = si.random_matrix(20, 9, p, 352)
+    B2.limb[:, :, :, 4] = 0          # zero column
+    C2, _, _ = gu.run(A, B2, p, method, algo)
+    _check_against_o1(C2, A, B2, p)
+
+
+@pytest.mark.parametrize("algo,method", [("ozaki", "4m"), ("ozaki", "3m"), ("plain", "4m")])
+def test_tiny_and_one_by_one(algo, method):
+    for (m, k, n, p) in ((1, 1, 1, 64), (1, 3, 2, 1), (3, 1, 2, 1000), (2, 2, 2, 65)):
+        A = si.random_matrix(m, k, p, 360 + m, "uniform_exp")
+        B = si.random_matrix(k, n, p, 370 + n, "uniform_exp")
+        C, _, _ = gu.run(A, B, p, method, algo)
+        assert gu.same(C, exact.rounded_cgemm(A, B, p)), (m, k, n, p)
+
+
+@pytest.mark.parametrize("algo,method", [("ozaki", "4m"), ("ozaki", "3m"), ("plain", "4m")])
+def test_huge_exponent_spread(algo, method):
+    """Exponents over +-3000: lossy splits, uncertified entries, exact fallbacks."""
+    p = 128
+    A = si.random_matrix(24, 16, p, 381, "uniform_exp", emin=-3000, emax=3000)
+    B = si.random_matrix(16, 20, p, 382, "uniform_exp", emin=-3000, emax=3000)
+    C, ws, st = gu.run(A, B, p, method, algo)
+    _check_against_o1(C, A, B, p)
+
+
+@pytest.mark.parametrize("algo", ["ozaki", "plain"])
+def test_exponent_overflow_sets_status(algo):
+    p = 128
+    A = si.random_matrix(3, 4, p, 391)
+    B = si.random_matrix(4, 3, p, 392)
+    A.exp[:] = 2 ** 30 + 7
+    B.exp[:] = 2 ** 30 + 7
+    C, ws, st = gu.run(A, B, p, "4m", algo)
+    assert st["erange"] == 1
+
+
+# ------------------------------------------------------------------ full sizes, sampled
+
+def _sampled(C, A, B, p, n_samples, seed):
+    rng = np.random.default_rng(seed)
+    ent = np.stack([rng.integers(0, A.rows, n_samples), rng.integers(0, B.cols, n_samples)], axis=1)
+    ent[0] = (0, 0)
+    ent[1] = (A.rows - 1, B.cols - 1)
+    sg, ex, li = c_oracle.rounded_cgemm(A, B, p, ent)
+    gs, ge, gl = gu.take_entries(C, ent)
+    assert np.array_equal(gs, sg) and np.array_equal(ge, ex) and np.array_equal(gl, li)
+
+
+@pytest.mark.parametrize("method", ["4m", "3m"])
+def test_config2_1024_p512_sampled(method):
+    A, B, p = si.make_config("c2_1024_p512")
+    C, ws, st = gu.run(A, B, p, method, "ozaki")
+    assert st["uncertified"] == 0 and st["fallback_overflow"] == 0
+    _sampled(C, A, B, p, 192, 7)
+
+
+def test_config2_2048_p1024_3m_sampled():
+    A, B, p = si.make_config("c2_2048_p1024")
+    C, ws, st = gu.run(A, B, p, "3m", "ozaki")
+    assert st["uncertified"] == 0
+    _sampled(C, A, B, p, 96, 8)
+
+
+def test_plain_1024_p512_sampled():
+    A, B, p = si.make_config("c2_1024_p512")
+    C, ws, st = gu.run(A, B, p, "4m", "plain")
+    _sampled(C, A, B, p, 96, 9)
