@@ -92,7 +92,8 @@ typedef struct mpc_mat {
  *   slices      s itself (0 -> the rule above); 1 <= s <= 160.
  *   cut_level   Q + 1, where pairs (t, u) with t + u <= Q are multiplied
  *               (0 -> Q = s - 1, the paper's triangle alpha + beta <= d + 1).
- *   kernel      MPC_KERNEL_*: which slice-GEMM kernel (auto = tcgen05).
+ *   kernel      MPC_KERNEL_*: which slice-GEMM kernel (auto = tcgen05; the mma.sync
+ *               kernel is a second, independent implementation of the same sums).
  */
 typedef struct mpc_oz_params {
     int32_t guard_bits;
@@ -149,6 +150,7 @@ typedef struct mpc_status {
     int32_t fallback_overflow;/* nonzero: more failures than the list holds */
     int32_t uncertified;      /* components whose exact window was too wide (rounded
                                  from a truncated sum; see mpcgemm_read_status) */
+    int32_t device_timeout;   /* nonzero: a kernel's bounded wait gave up (results invalid) */
 } mpc_status;
 
 /*

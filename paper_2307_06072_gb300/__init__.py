@@ -157,7 +157,10 @@ def mpcgemm(A: DeviceMatrix, B: DeviceMatrix, C: DeviceMatrix, p: int, method: s
     ev = None
     if events is not None:
         ev = _native.StageEvents()
+        torch = _torch()
         for x, e in enumerate(events[:8]):
+            if e is not None and not int(e.cuda_event):
+                e.record(stream if stream is not None else torch.cuda.current_stream())  # creates the event
             ev.ev[x] = int(e.cuda_event) if e is not None else None
     code = lib().mpcgemm_profiled(m, n, k, p, ctypes.byref(sa), ctypes.byref(sb), ctypes.byref(sc),
                                   _native.METHODS[method], _native.ALGOS[algo],
@@ -178,7 +181,8 @@ def read_status(workspace: Workspace, stream=None) -> dict:
     if code not in (_native.MPC_OK, _native.MPC_ERANGE):
         check(code)
     return {"erange": st.erange, "fallback_entries": st.fallback_entries,
-            "fallback_overflow": st.fallback_overflow, "uncertified": st.uncertified}
+            "fallback_overflow": st.fallback_overflow, "uncertified": st.uncertified,
+            "device_timeout": st.device_timeout}
 
 
 def version() -> int:

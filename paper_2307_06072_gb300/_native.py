@@ -65,7 +65,8 @@ class StageEvents(ctypes.Structure):
 
 class Status(ctypes.Structure):
     _fields_ = [("erange", ctypes.c_int32), ("fallback_entries", ctypes.c_int32),
-                ("fallback_overflow", ctypes.c_int32), ("uncertified", ctypes.c_int32)]
+                ("fallback_overflow", ctypes.c_int32), ("uncertified", ctypes.c_int32),
+                ("device_timeout", ctypes.c_int32)]
 
 
 _lib = None

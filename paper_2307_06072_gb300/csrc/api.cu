@@ -175,8 +175,9 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
 int cuda_code(cudaError_t e) { return e == cudaSuccess ? MPC_OK : MPC_ECUDA - (int)e; }
 
 bool mat_ok(const mpc_mat *X, int64_t rows, int64_t cols) {
-  if (!X || X->rows != rows || X->cols != cols || X->ld < cols || X->ld < 1) return false;
-  if (rows * cols == 0) return true;
+  if (!X || X->rows != rows || X->cols != cols || X->ld < cols) return false;
+  if (rows * cols == 0) return true;      // empty operand: nothing is read
+  if (X->ld < 1) return false;
   for (int c = 0; c < 2; ++c)
     if (!X->sign[c] || !X->exp[c] || !X->limb[c]) return false;
   return true;
@@ -325,10 +326,10 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_
     sa.status = status;
     if (pl.kernel == MPC_KERNEL_MMA_SYNC) {
       launch_slicegemm_mma(sa, st);
-    } else {
+    } else {   // auto: the tcgen05 kernel
       const cudaError_t e = launch_slicegemm_tc(sa, st);
       if (e == cudaErrorNotSupported && pl.kernel == MPC_KERNEL_AUTO) launch_slicegemm_mma(sa, st);
-      else if (e != cudaSuccess) return cuda_code(e);
+      else if (e != cudaSuccess) return e == cudaErrorNotSupported ? MPC_ENOTSUP : cuda_code(e);
     }
     mark(2);
     AccumArgs aa{};
@@ -385,6 +386,7 @@ int mpcgemm_read_status(const void *workspace, size_t ws_bytes, mpc_status *stat
   status->fallback_entries = words[kStFallbackCount];
   status->fallback_overflow = words[kStFallbackOverflow];
   status->uncertified = words[kStUncertified];
+  status->device_timeout = words[kStTimeout];
   return status->erange ? MPC_ERANGE : MPC_OK;
 }
 

@@ -22,7 +22,7 @@ constexpr int kStatusWords = 16;
 constexpr int kDefaultGuard = 40;
 
 // status block (int32 words at the start of the workspace)
-enum StatusWord { kStErange = 0, kStFallbackCount = 1, kStFallbackOverflow = 2, kStUncertified = 3 };
+enum StatusWord { kStErange = 0, kStFallbackCount = 1, kStFallbackOverflow = 2, kStUncertified = 3, kStTimeout = 4 };
 
 // Digit sets of one operand: planes [0, s) real part, [s, 2s) imaginary part,
 // [2s, 3s+1) the 3M sums (positions -1 .. s-1).

@@ -1,10 +1,416 @@
-// oz_slicegemm on the 5th-generation tensor cores (tcgen05): placeholder
-// until the kernel lands; the mma.sync kernel serves meanwhile.
+// oz_slicegemm on the 5th-generation tensor cores (tcgen05, sm_103a):
+// the slice products C_ab := A_a B_b of Alg. 2 (Kouya, Sec. III-C), summed
+// over the pairs of one group, exactly.
+//
+// Work unit = (group g, 128 x 256 output tile).  Its GEMM runs over the
+// concatenated inner dimension K' = count * kpad: for pair (t, q - t) the
+// digit planes D^A_t (rows of A) and D^B_{q-t} (columns of B, K-major).
+//
+// Persistent CTA per SM, warp-specialised, 320 threads:
+//   warp 0      TMA producer: 64-element k-blocks of A (128 rows) and B (256
+//               rows) into a 4-stage shared-memory ring (128-byte swizzle).
+//   warp 1      TMEM owner (alloc 512 columns) and, on one lane, the MMA
+//               issuer: tcgen05.mma.cta_group::1.kind::f16, bf16 x bf16 ->
+//               fp32 into one of two 128 x 256 TMEM accumulators.
+//   warps 2..9  epilogue: every kChunk = 960 inner elements (15 k-blocks) the
+//               accumulator holds an exact integer < 2^24 (digits |d| <= 128,
+//               |d_a d_b| <= 2^14, 960 * 2^14 < 2^24); it is read with
+//               tcgen05.ld, converted exactly to int32 and added to int32
+//               registers (the group bound keeps every sum below 2^31).
+//               The two TMEM buffers let the MMA fill one while the other
+//               drains.  At the end of a unit the int32 tile is stored.
+// Every mbarrier wait is bounded: on a timeout the kernel records it in the
+// status block, lets in-flight copies and MMAs land, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace mpc {
 
-cudaError_t launch_slicegemm_tc(const SliceGemmArgs &, cudaStream_t) { return cudaErrorNotSupported; }
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int KB_PER_CHUNK = kChunk / BK;       // 15
+constexpr int NUM_THREADS = 320, EPI_WARPS = 8;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr long long kTimeoutCycles = 4000000000ll;   // ~2 s at 2 GHz
+static_assert(kChunk % BK == 0, "chunk must be whole k-blocks");
+constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
+
+struct TcParams {
+  int64_t m, n;
+  int kbpp;            // k-blocks per pair (kpad / 64)
+  int n_entries, tiles_m, tiles_n;
+  int64_t units;
+  const GroupEntry *groups;
+  ProductDesc prod[4];
+  int32_t *out;
+  int32_t *status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; false on abort (another role gave up) or timeout (sets abort + status)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, int32_t *status) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kTimeoutCycles) {
+      *abort = 1;
+      atomicOr(reinterpret_cast<int *>(status) + kStTimeout, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+// short bounded wait used only while shutting down after an abort
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity) && clock64() - t0 < 2000000ll) {
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(const void *p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3FFFull;            // start address
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused with 128B swizzle), 16 B
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                  // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                  // swizzle mode: 128 B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D fp32, A = B = bf16, both K-major, M = 128, N = 256.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct Unit {
+  GroupEntry g;
+  ProductDesc pd;
+  int tm, tn, nkb;
+  int e;
+};
+
+__device__ __forceinline__ Unit decode(const TcParams &P, int64_t u) {
+  Unit x;
+  const int tiles = P.tiles_m * P.tiles_n;
+  x.e = (int)(u / tiles);
+  const int t = (int)(u % tiles);
+  x.tm = t / P.tiles_n;
+  x.tn = t % P.tiles_n;
+  x.g = P.groups[x.e];
+  x.pd = P.prod[x.g.prod];
+  x.nkb = x.g.count * P.kbpp;
+  return x;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_slicegemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + STAGES * A_BYTES;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+  uint64_t *empty = full + STAGES;
+  uint64_t *tfull = empty + STAGES;
+  uint64_t *tempty = tfull + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+  volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], EPI_WARPS);
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+        const Unit x = decode(P, u);
+        for (int kb = 0; kb < x.nkb; ++kb) {
+          const int pi = kb / P.kbpp;
+          const int k0 = (kb - pi * P.kbpp) * BK;
+          const int t = x.g.t0 + pi, uu = x.g.q - t;
+          const int planeA = x.pd.a_plane0 + t - x.pd.a_pos0;
+          const int planeB = x.pd.b_plane0 + uu - x.pd.b_pos0;
+          if (!mbar_wait(&empty[stage], phase ^ 1, abort, P.status)) { ok = false; break; }
+          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          tma_load_3d(sA + stage * A_BYTES, &tmA, k0, x.tm * BM, planeA, &full[stage]);
+          tma_load_3d(sB + stage * B_BYTES, &tmB, k0, x.tn * BN, planeB, &full[stage]);
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+      if (!ok) {   // let copies still in flight land before the CTA exits
+        for (int s = 0; s < STAGES; ++s) {
+          mbar_drain(&full[s], 0);
+          mbar_drain(&full[s], 1);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int stage = 0, buf = 0;
+      uint32_t phase = 0, tphase = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+        const Unit x = decode(P, u);
+        for (int c0 = 0; c0 < x.nkb && ok; c0 += KB_PER_CHUNK) {
+          const int cend = min(x.nkb, c0 + KB_PER_CHUNK);
+          if (!mbar_wait(&tempty[buf], tphase ^ 1, abort, P.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+          for (int kb = c0; kb < cend; ++kb) {
+            if (!mbar_wait(&full[stage], phase, abort, P.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t ad = smem_desc(sA + stage * A_BYTES);
+            const uint64_t bd = smem_desc(sB + stage * B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)   // K = 16 per instruction: +32 B in the swizzled row
+              mma_f16(d_tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb > c0 || kk > 0) ? 1u : 0u);
+            mma_commit(&empty[stage]);
+            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          mma_commit(&tfull[buf]);
+          buf ^= 1;
+          if (buf == 0) tphase ^= 1;
+        }
+      }
+      if (!ok) {   // wait for the MMAs already issued before TMEM is freed
+        mma_commit(&tfull[buf]);
+        mbar_drain(&tfull[buf], tphase);
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..9
+    const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31 (hardware rule: warp id % 4)
+    const int half = (warp - 2) >> 2;          // columns half*128 .. +127
+    const int row_in_tile = quad * 32 + lane;
+    int buf = 0;
+    uint32_t tphase = 0;
+    bool ok = true;
+    int32_t acc[128];
+#pragma unroll
+    for (int x = 0; x < 128; ++x) acc[x] = 0;
+    for (int64_t u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+      const Unit x = decode(P, u);
+      for (int c0 = 0; c0 < x.nkb; c0 += KB_PER_CHUNK) {
+        if (!mbar_wait(&tfull[buf], tphase, abort, P.status)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + half * 128);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          uint32_t r[32];
+          tmem_ld32(taddr + (uint32_t)(j * 32), r);
+#pragma unroll
+          for (int y = 0; y < 32; ++y) acc[j * 32 + y] += __float2int_rn(__uint_as_float(r[y]));
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        buf ^= 1;
+        if (buf == 0) tphase ^= 1;
+      }
+      if (!ok) break;
+      // store the int32 tile rows of this thread
+      const int64_t row = (int64_t)x.tm * BM + row_in_tile;
+      const int64_t col0 = (int64_t)x.tn * BN + half * 128;
+      if (row < P.m) {
+        int32_t *dst = P.out + (int64_t)x.e * P.m * P.n + row * P.n + col0;
+        if (col0 + 128 <= P.n && ((P.n & 3) == 0)) {
+#pragma unroll
+          for (int v = 0; v < 32; ++v)
+            reinterpret_cast<int4 *>(dst)[v] = make_int4(acc[4 * v], acc[4 * v + 1], acc[4 * v + 2], acc[4 * v + 3]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 128; ++v)
+            if (col0 + v < P.n) dst[v] = acc[v];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 128; ++v) acc[v] = 0;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t kpad, int64_t planes, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)rows * kpad * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+}  // namespace
+
+cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st) {
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3) return cudaErrorNotSupported;   // built for sm_103a only
+  int planes_a = 0, planes_b = 0;
+  for (int x = 0; x < 4; ++x) {
+    if (a.prod[x].a_plane0 + a.prod[x].a_npos > planes_a) planes_a = a.prod[x].a_plane0 + a.prod[x].a_npos;
+    if (a.prod[x].b_plane0 + a.prod[x].b_npos > planes_b) planes_b = a.prod[x].b_plane0 + a.prod[x].b_npos;
+  }
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a.dA, a.m, a.kpad, planes_a, BM) || !make_map(&mb, a.dB, a.n, a.kpad, planes_b, BN))
+    return cudaErrorNotSupported;
+  TcParams P{};
+  P.m = a.m;
+  P.n = a.n;
+  P.kbpp = (int)(a.kpad / BK);
+  P.n_entries = a.n_entries;
+  P.tiles_m = (int)((a.m + BM - 1) / BM);
+  P.tiles_n = (int)((a.n + BN - 1) / BN);
+  P.units = (int64_t)a.n_entries * P.tiles_m * P.tiles_n;
+  P.groups = a.groups;
+  for (int x = 0; x < 4; ++x) P.prod[x] = a.prod[x];
+  P.out = a.out;
+  P.status = a.status;
+  if (P.units == 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_slicegemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int grid = (int)(P.units < num_sms() ? P.units : num_sms());
+  k_slicegemm_tc<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ma, mb, P);
+  return cudaGetLastError();
+}
 
 }  // namespace mpc

@@ -1,0 +1,45 @@
+"""The tcgen05 slice-GEMM kernel against the mma.sync kernel and the oracle.
+
+Both kernels compute the same exact int32 group sums; every group plane must
+agree bit for bit, the outputs must equal O1, and no bounded wait may time out.
+Shapes cover single and many tiles, ragged M / N / K edges, 3M sum digits,
+units of one pair and of 63 pairs (many 960-element chunks, both TMEM buffers),
+and more units than SMs (persistent loop).
+"""
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import c_oracle
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # m, k, n, p, method, dist
+    (128, 64, 256, 128, "4m", "uniform"),        # exactly one tile, one k-block per pair
+    (200, 150, 300, 128, "4m", "uniform_exp"),   # ragged tiles and k tail
+    (37, 70, 29, 192, "3m", "uniform_exp"),      # smaller than one tile
+    (260, 2048, 520, 128, "3m", "uniform"),      # 63-pair groups: 135 chunks per unit
+    (512, 320, 768, 256, "4m", "uniform"),       # many units per CTA
+]
+
+
+def _planes(A, B, p, method, kernel):
+    C, ws, st = gu.run(A, B, p, method, "ozaki", params=dict(kernel=kernel))
+    pl = gu.plan(A, B, p, method, params=dict(kernel=kernel))
+    return C, gu.ws_groups(ws, pl, A.rows, B.cols), st
+
+
+@pytest.mark.parametrize("m,k,n,p,method,dist", CASES)
+def test_tcgen05_matches_mma_sync_and_oracle(m, k, n, p, method, dist):
+    A = si.random_matrix(m, k, p, 500 + m, dist)
+    B = si.random_matrix(k, n, p, 600 + n, dist)
+    Ct, Gt, st_t = _planes(A, B, p, method, "tcgen05")
+    Cm, Gm, st_m = _planes(A, B, p, method, "mma_sync")
+    assert st_t["device_timeout"] == 0
+    bad = np.argwhere(Gt != Gm)
+    assert len(bad) == 0, f"{len(bad)} group-sum mismatches, first {bad[:4].tolist()}"
+    assert gu.same(Ct, Cm)
+    ref = c_oracle.rounded_cgemm_matrix(A, B, p)
+    assert gu.same(Ct, ref)
