@@ -194,6 +194,32 @@ int mpcgemm_plan(int64_t m, int64_t n, int64_t k, int32_t p_bits, int method, in
  * this workspace.  Returns MPC_OK, or MPC_ERANGE if status->erange is set. */
 int mpcgemm_read_status(const void *workspace, size_t ws_bytes, mpc_status *status, void *stream);
 
+/*
+ * Allocation-free variant of mpcgemm(), for callers that cannot allocate device
+ * memory themselves -- for example a plug-in or callback that its host
+ * application hands only the input and output buffers, or a latency-bound loop
+ * that must not allocate once it is running.  The paper has no counterpart: this
+ * is an interface convenience of the library.
+ *
+ * Instead of a caller workspace it uses one static device array of
+ * MPC_NOALLOC_SCRATCH_BYTES (64 MiB) inside the library; a device that has run
+ * this entry point keeps that array until the process exits.  A problem whose
+ * mpcgemm_workspace_size() exceeds it is rejected with MPC_ENOSPC before
+ * anything is enqueued (for example m = n = k = 192 fits at p = 256 and 128 at
+ * p = 1024 for Ozaki 4M/3M, 256 at p = 1024 for plain; 256 at p = 256 for Ozaki
+ * does not).  The first call on a device looks
+ * up the array's device address (it allocates nothing); make that first call
+ * outside any stream capture.  Every call uses the same array and finds the
+ * previous call's contents there (each call re-initialises what it reads), so
+ * calls whose GPU work overlaps -- on different streams or from different host
+ * threads -- race and produce wrong results: serialise them.  Arguments, results
+ * and errors are those of mpcgemm(), with no workspace arguments.
+ */
+#define MPC_NOALLOC_SCRATCH_BYTES (64u << 20)
+int mpcgemm_noalloc(int64_t m, int64_t n, int64_t k, int32_t p_bits,
+                    const mpc_mat *A, const mpc_mat *B, mpc_mat *C,
+                    int method, int algo, void *stream);
+
 /* Human-readable text of a status code (static storage). */
 const char *mpcgemm_strerror(int code);
 

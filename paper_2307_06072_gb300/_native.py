@@ -20,8 +20,9 @@ METHODS = {"4m": 0, "3m": 1}
 ALGOS = {"plain": 0, "ozaki": 1}
 KERNELS = {"auto": 0, "tcgen05": 1, "mma_sync": 2}
 
-EXPORTED = ("mpcgemm", "mpcgemm_ex", "mpcgemm_profiled", "mpcgemm_workspace_size", "mpcgemm_plan", "mpcgemm_read_status",
-            "mpcgemm_strerror", "mpcgemm_version")
+EXPORTED = ("mpcgemm", "mpcgemm_ex", "mpcgemm_profiled", "mpcgemm_workspace_size", "mpcgemm_plan",
+            "mpcgemm_read_status", "mpcgemm_noalloc", "mpcgemm_strerror", "mpcgemm_version")
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class MpcMat(ctypes.Structure):
@@ -95,6 +96,8 @@ def lib():
         L.mpcgemm_plan.restype = ctypes.c_int
         L.mpcgemm_read_status.argtypes = [P, ctypes.c_size_t, P, P]
         L.mpcgemm_read_status.restype = ctypes.c_int
+        L.mpcgemm_noalloc.argtypes = [I64, I64, I64, I32, P, P, P, ctypes.c_int, ctypes.c_int, P]
+        L.mpcgemm_noalloc.restype = ctypes.c_int
         L.mpcgemm_strerror.argtypes = [ctypes.c_int]
         L.mpcgemm_strerror.restype = ctypes.c_char_p
         L.mpcgemm_version.argtypes = []
