@@ -128,6 +128,7 @@ typedef struct mpc_plan {
     uint64_t ws_bytes;
     int32_t launches;             /* kernel launches one call makes */
     int32_t reserved;
+    uint64_t off_group_order;     /* groups ordered by descending level */
 } mpc_plan;
 
 /*

@@ -50,7 +50,8 @@ class Plan(ctypes.Structure):
                 ("off_fallback", ctypes.c_uint64), ("fallback_capacity", ctypes.c_uint64),
                 ("off_fb_scratch", ctypes.c_uint64), ("fb_scratch_limbs", ctypes.c_uint64),
                 ("fb_threads", ctypes.c_uint64), ("off_fix_a", ctypes.c_uint64), ("off_fix_b", ctypes.c_uint64),
-                ("ws_bytes", ctypes.c_uint64), ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ws_bytes", ctypes.c_uint64), ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("off_group_order", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         out = {}

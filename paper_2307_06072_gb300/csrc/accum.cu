@@ -6,8 +6,8 @@
 // formula gives them, into two exact accumulators (Re, Im):
 //     4M: Re = rr - ii,        Im = ri + ir
 //     3M: Re = rr - ii,        Im = ss - rr - ii
-// The accumulators are "lazy" radix-2^32 integers (int64 slots in shared
-// memory) normalised once at the end.  Value = Acc * 2^(E_i + F_j - 14 - 8Q).
+// Groups are visited in order of increasing shift; each accumulator keeps two
+// running int64 words in registers and emits finished 32-bit words.  Value = Acc * 2^(E_i + F_j - 14 - 8Q).
 // The result is RN_p(Acc) when no rounding midpoint lies within the error
 // bound b * 2^beta of Acc (then it equals RN_p of the exact product);
 // otherwise the component is queued for k_exact_fallback.
@@ -22,10 +22,11 @@ namespace mpc {
 
 namespace {
 
-struct SlotAcc {   // 32-bit words stored in int64 shared-memory slots (stride T)
-  const int64_t *base;
-  int stride;
-  __device__ __forceinline__ uint32_t operator()(int i) const { return (uint32_t)base[(int64_t)i * stride]; }
+constexpr int kMaxWords = 88;   // 32-bit words of the exact accumulator (Q <= 2s, s <= 160)
+
+struct WordAcc {   // 32-bit words of a thread-local array
+  const uint32_t *base;
+  __device__ __forceinline__ uint32_t operator()(int i) const { return base[i]; }
 };
 
 struct LimbAcc {   // 32-bit words of a little-endian uint64 array
@@ -45,75 +46,88 @@ __device__ __forceinline__ int product_sign(int method, int c, int prod) {
   return prod == 2 ? 1 : -1;
 }
 
-// normalise lazy slots into 32-bit two's-complement words; return sign, leave magnitude
-__device__ __forceinline__ bool normalise_slots(int64_t *my, int nslot, int T) {
-  int64_t carry = 0;
-  for (int s = 0; s < nslot; ++s) {
-    int64_t t = my[(int64_t)s * T] + carry;
-    my[(int64_t)s * T] = t & 0xFFFFFFFFll;
-    carry = t >> 32;
+// Exact signed integer built from terms v * 2^shift with nondecreasing shifts:
+// `lo` holds the current 32-bit word (index `cur`) plus pending carries, `hi`
+// the next; finished words are emitted to `out`.  |lo| stays below 2^43.
+struct Lazy {
+  int64_t lo = 0, hi = 0;
+  int cur = 0;
+  __device__ __forceinline__ void emit(uint32_t *out) {
+    out[cur++] = (uint32_t)lo;
+    lo = (lo >> 32) + hi;
+    hi = 0;
   }
-  bool neg = carry < 0;
-  if (neg) {
-    int64_t c = 1;
-    for (int s = 0; s < nslot; ++s) {
-      int64_t w = ((~my[(int64_t)s * T]) & 0xFFFFFFFFll) + c;
-      my[(int64_t)s * T] = w & 0xFFFFFFFFll;
-      c = w >> 32;
+  __device__ __forceinline__ void add(uint32_t *out, int64_t v, int shift) {
+    const int w = shift >> 5;
+    while (cur < w) emit(out);
+    const int64_t x = v * ((int64_t)1 << (shift & 31));   // |x| < 2^55
+    lo += x & 0xFFFFFFFFll;
+    hi += x >> 32;
+  }
+  // emit the remaining words; returns the sign (magnitude left in out[0, nw))
+  __device__ __forceinline__ bool finish(uint32_t *out, int nw) {
+    while (cur < nw) emit(out);
+    const bool neg = lo < 0;
+    if (neg) {
+      uint64_t c = 1;
+      for (int i = 0; i < nw; ++i) {
+        const uint64_t t = (uint64_t)(uint32_t)~out[i] + c;
+        out[i] = (uint32_t)t;
+        c = t >> 32;
+      }
     }
+    return neg;
   }
-  return neg;
-}
+};
 
 }  // namespace
 
+// Group table (per product, levels ascending) and a merged order of all groups
+// by descending level, i.e. ascending shift 8 (Q - q) for the accumulation.
 __global__ void k_group_table(ProductDesc p0, ProductDesc p1, ProductDesc p2, ProductDesc p3, int n_products,
-                              int Q, int gmax, GroupEntry *table) {
-  if (blockIdx.x != 0 || threadIdx.x >= (unsigned)n_products) return;
-  ProductDesc pd = threadIdx.x == 0 ? p0 : threadIdx.x == 1 ? p1 : threadIdx.x == 2 ? p2 : p3;
-  build_groups((int)threadIdx.x, pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, Q, gmax, table + pd.group0,
-               pd.n_groups);
+                              int Q, int gmax, GroupEntry *table, int32_t *order) {
+  if (blockIdx.x != 0) return;
+  if (threadIdx.x < (unsigned)n_products) {
+    ProductDesc pd = threadIdx.x == 0 ? p0 : threadIdx.x == 1 ? p1 : threadIdx.x == 2 ? p2 : p3;
+    build_groups((int)threadIdx.x, pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, Q, gmax, table + pd.group0,
+                 pd.n_groups);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const ProductDesc pds[4] = {p0, p1, p2, p3};
+  int n = 0, qlo = 0;
+  for (int x = 0; x < n_products; ++x) qlo = min(qlo, pds[x].a_pos0 + pds[x].b_pos0);
+  for (int q = Q; q >= qlo; --q)
+    for (int x = 0; x < n_products; ++x)
+      for (int e = pds[x].group0; e < pds[x].group0 + pds[x].n_groups; ++e)
+        if (table[e].q == q) order[n++] = e;
 }
 
 __global__ void k_oz_accum(AccumArgs a, OutView C) {
-  extern __shared__ int64_t slots[];   // [2][nslot][T]
-  const int T = blockDim.x;
-  const int64_t j = (int64_t)blockIdx.x * T + threadIdx.x;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = blockIdx.y;
-  if (j >= a.n || i >= a.m) return;    // no block-level sync below
-  int64_t *acc[2] = {slots + threadIdx.x, slots + (int64_t)a.nslot * T + threadIdx.x};
-  for (int c = 0; c < 2; ++c)
-    for (int s = 0; s < a.nslot; ++s) acc[c][(int64_t)s * T] = 0;
+  if (j >= a.n || i >= a.m) return;
   const int32_t Ei = a.E[i], Fj = a.F[j];
-  const bool zero = (Ei == INT32_MIN) || (Fj == INT32_MIN);
+  const int64_t o = i * C.ld + j;
+  if (Ei == INT32_MIN || Fj == INT32_MIN) {   // a zero row or column: the product is exactly 0
+    for (int c = 0; c < 2; ++c) store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+    return;
+  }
   const int64_t mn = a.m * a.n, ij = i * a.n + j;
-  if (!zero) {
-    for (int e = 0; e < a.n_entries; ++e) {
-      const GroupEntry g = a.groups[e];
-      const int s0 = product_sign(a.method, 0, g.prod), s1 = product_sign(a.method, 1, g.prod);
-      const int64_t v = (int64_t)a.planes[(int64_t)e * mn + ij];
-      const int shift = 8 * (a.Q - g.q);
-      const int w = shift >> 5, r = shift & 31;
-      if (s0) {
-        const int64_t x = (s0 > 0 ? v : -v) * ((int64_t)1 << r);
-        acc[0][(int64_t)w * T] += x & 0xFFFFFFFFll;
-        acc[0][(int64_t)(w + 1) * T] += x >> 32;
-      }
-      if (s1) {
-        const int64_t x = (s1 > 0 ? v : -v) * ((int64_t)1 << r);
-        acc[1][(int64_t)w * T] += x & 0xFFFFFFFFll;
-        acc[1][(int64_t)(w + 1) * T] += x >> 32;
-      }
-    }
+  uint32_t words[2][kMaxWords];
+  Lazy acc[2];
+  for (int x = 0; x < a.n_entries; ++x) {
+    const int e = a.order[x];
+    const GroupEntry g = a.groups[e];
+    const int64_t v = (int64_t)a.planes[(int64_t)e * mn + ij];
+    const int shift = 8 * (a.Q - g.q);
+    const int s0 = product_sign(a.method, 0, g.prod), s1 = product_sign(a.method, 1, g.prod);
+    if (s0) acc[0].add(words[0], s0 > 0 ? v : -v, shift);
+    if (s1) acc[1].add(words[1], s1 > 0 ? v : -v, shift);
   }
   for (int c = 0; c < 2; ++c) {
-    const int64_t o = i * C.ld + j;
-    if (zero) {
-      store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
-      continue;
-    }
-    const bool neg = normalise_slots(acc[c], a.nslot, T);
-    SlotAcc mag{acc[c], T};
+    const bool neg = acc[c].finish(words[c], a.nslot);
+    WordAcc mag{words[c]};
     const int N = bitlen(mag, a.nslot);
     const uint64_t b = a.bound_drop[c] + (uint64_t)a.k * ((a.lossyA[i] ? a.bound_lossy_a[c] : 0ull) +
                                                           (a.lossyB[j] ? a.bound_lossy_b[c] : 0ull));
@@ -280,19 +294,16 @@ __global__ void k_zero_output(OutView C, int64_t m, int64_t n, int L) {
 // ---------------------------------------------------------------- launchers
 
 void launch_group_table(const ProductDesc *prods, int n_products, int Q, int gmax, GroupEntry *table,
-                        cudaStream_t st) {
+                        int32_t *order, cudaStream_t st) {
   ProductDesc z{};
   k_group_table<<<1, 32, 0, st>>>(prods[0], prods[1], n_products > 2 ? prods[2] : z,
-                                  n_products > 3 ? prods[3] : z, n_products, Q, gmax, table);
+                                  n_products > 3 ? prods[3] : z, n_products, Q, gmax, table, order);
 }
 
 void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st) {
-  int T = 128;
-  while (T > 32 && (size_t)2 * a.nslot * T * sizeof(int64_t) > 200 * 1024) T >>= 1;
-  const size_t smem = (size_t)2 * a.nslot * T * sizeof(int64_t);
-  cudaFuncSetAttribute(k_oz_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int T = 128;
   dim3 g((unsigned)((a.n + T - 1) / T), (unsigned)a.m);
-  k_oz_accum<<<g, T, smem, st>>>(a, C);
+  k_oz_accum<<<g, T, 0, st>>>(a, C);
 }
 
 void launch_fallback(const FallbackArgs &f, const MatView &A, const MatView &B, const OutView &C, int blocks,

@@ -139,6 +139,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   }
   P.n_groups_total = total;
   P.acc_slots = (8 * (Q - qmin) + 64) / 32 + 3;
+  if (P.acc_slots > 88) return MPC_EINVAL;   // the accumulate kernel's word budget
   // bounds: b = bound_drop[c] + k (lossyA * bound_lossy_a[c] + lossyB * bound_lossy_b[c]), times 2^beta
   const int beta = 15 + 8 * (Q - s) > 0 ? 15 + 8 * (Q - s) : 0;
   P.bound_shift = beta;
@@ -167,6 +168,8 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   off = align256(off + (uint64_t)total * m * n * 4);
   P.off_group_table = off;
   off = align256(off + (uint64_t)total * sizeof(GroupEntry));
+  P.off_group_order = off;
+  off = align256(off + (uint64_t)total * 4);
   P.ws_bytes = off;
   P.launches = 9;     // init, row max, column max, group table, 2 x digits, slice GEMM, accumulate, fallback
   return MPC_OK;
@@ -307,9 +310,10 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_
   } else {
     __nv_bfloat16 *dA = (__nv_bfloat16 *)(ws + P.off_digits_a), *dB = (__nv_bfloat16 *)(ws + P.off_digits_b);
     GroupEntry *table = (GroupEntry *)(ws + P.off_group_table);
+    int32_t *order = (int32_t *)(ws + P.off_group_order);
     int32_t *planes = (int32_t *)(ws + P.off_groups);
     const int want_sum = method == MPC_3M;
-    launch_group_table(pl.prod, P.n_products, P.Q, P.gmax, table, st);
+    launch_group_table(pl.prod, P.n_products, P.Q, P.gmax, table, order, st);
     launch_oz_digits(Av, 0, m, k, P.kpad, L, P.s, want_sum, E, lossyA, dA, st);
     launch_oz_digits(Bv, 1, n, k, P.kpad, L, P.s, want_sum, F, lossyB, dB, st);
     mark(1);
@@ -335,6 +339,7 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_
     AccumArgs aa{};
     aa.planes = planes;
     aa.groups = table;
+    aa.order = order;
     aa.n_entries = P.n_groups_total;
     aa.m = m;
     aa.n = n;

@@ -22,6 +22,7 @@ struct SliceGemmArgs {
 struct AccumArgs {
   const int32_t *planes;        // group sums [entry][m][n]
   const GroupEntry *groups;
+  const int32_t *order;         // groups by descending level
   int32_t n_entries;
   int64_t m, n, k;
   int p, L, Q, nslot, method;
@@ -63,7 +64,7 @@ void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int6
 void launch_plain_fix(const MatView &X, int side, int64_t lines, int64_t k, int L, int Lp, const int32_t *E,
                       int32_t *lossy, uint64_t *fix, uint8_t *fsign, cudaStream_t st);
 void launch_group_table(const ProductDesc *prods, int n_products, int Q, int gmax, GroupEntry *table,
-                        cudaStream_t st);
+                        int32_t *order, cudaStream_t st);
 void launch_slicegemm_mma(const SliceGemmArgs &a, cudaStream_t st);
 cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st);
 void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st);

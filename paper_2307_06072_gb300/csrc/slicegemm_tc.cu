@@ -6,7 +6,11 @@
 // concatenated inner dimension K' = count * kpad: for pair (t, q - t) the
 // digit planes D^A_t (rows of A) and D^B_{q-t} (columns of B, K-major).
 //
-// Persistent CTA per SM, warp-specialised, 320 threads:
+// Persistent CTA per SM, warp-specialised, 320 threads.  Units are handed out
+// dynamically (a global counter): the producer takes the next unit index and
+// publishes it to the MMA and epilogue warps through a 4-slot shared ring, so
+// the units in flight on all SMs stay a contiguous window of the unit order
+// (group-major) and share the same digit planes in L2.
 //   warp 0      TMA producer: 64-element k-blocks of A (128 rows) and B (256
 //               rows) into a 4-stage shared-memory ring (128-byte swizzle).
 //   warp 1      TMEM owner (alloc 512 columns) and, on one lane, the MMA
@@ -37,6 +41,8 @@ constexpr int KB_PER_CHUNK = kChunk / BK;       // 15
 constexpr int NUM_THREADS = 320, EPI_WARPS = 8;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long kTimeoutCycles = 4000000000ll;   // ~2 s at 2 GHz
+constexpr int URING = 4;                               // unit-index ring slots
+constexpr int kStUnitCounter = 8;                      // status word used as the unit counter
 static_assert(kChunk % BK == 0, "chunk must be whole k-blocks");
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
 
@@ -182,8 +188,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint64_t *empty = full + STAGES;
   uint64_t *tfull = empty + STAGES;
   uint64_t *tempty = tfull + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+  uint64_t *ufull = tempty + 2;
+  uint64_t *uempty = ufull + URING;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(uempty + URING);
   volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  volatile int *uring = reinterpret_cast<volatile int *>(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -194,6 +203,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], EPI_WARPS);
+    }
+    for (int r = 0; r < URING; ++r) {
+      mbar_init(&ufull[r], 1);
+      mbar_init(&uempty[r], 1 + EPI_WARPS);
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -214,10 +227,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      int stage = 0;
-      uint32_t phase = 0;
+      int stage = 0, slot = 0;
+      uint32_t phase = 0, uphase = 0;
       bool ok = true;
-      for (int64_t u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+      int *counter = reinterpret_cast<int *>(P.status) + kStUnitCounter;
+      while (ok) {
+        if (!mbar_wait(&uempty[slot], uphase ^ 1, abort, P.status)) { ok = false; break; }
+        int64_t u = atomicAdd(counter, 1);
+        if (u >= P.units) u = -1;
+        uring[slot] = (int)u;
+        mbar_arrive(&ufull[slot]);
+        if (++slot == URING) { slot = 0; uphase ^= 1; }
+        if (u < 0) break;
         const Unit x = decode(P, u);
         for (int kb = 0; kb < x.nkb; ++kb) {
           const int pi = kb / P.kbpp;
@@ -242,10 +263,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      int stage = 0, buf = 0;
-      uint32_t phase = 0, tphase = 0;
+      int stage = 0, buf = 0, slot = 0;
+      uint32_t phase = 0, tphase = 0, uphase = 0;
       bool ok = true;
-      for (int64_t u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+      while (ok) {
+        if (!mbar_wait(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
+        const int u = uring[slot];
+        mbar_arrive(&uempty[slot]);
+        if (++slot == URING) { slot = 0; uphase ^= 1; }
+        if (u < 0) break;
         const Unit x = decode(P, u);
         for (int c0 = 0; c0 < x.nkb && ok; c0 += KB_PER_CHUNK) {
           const int cend = min(x.nkb, c0 + KB_PER_CHUNK);
@@ -279,13 +305,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31 (hardware rule: warp id % 4)
     const int half = (warp - 2) >> 2;          // columns half*128 .. +127
     const int row_in_tile = quad * 32 + lane;
-    int buf = 0;
-    uint32_t tphase = 0;
+    int buf = 0, slot = 0;
+    uint32_t tphase = 0, uphase = 0;
     bool ok = true;
     int32_t acc[128];
 #pragma unroll
     for (int x = 0; x < 128; ++x) acc[x] = 0;
-    for (int64_t u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+    while (ok) {
+      if (!mbar_wait(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
+      const int u = uring[slot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&uempty[slot]);
+      if (++slot == URING) { slot = 0; uphase ^= 1; }
+      if (u < 0) break;
       const Unit x = decode(P, u);
       for (int c0 = 0; c0 < x.nkb; c0 += KB_PER_CHUNK) {
         if (!mbar_wait(&tfull[buf], tphase, abort, P.status)) { ok = false; break; }
