@@ -94,16 +94,37 @@ __global__ void k_group_table(ProductDesc p0, ProductDesc p1, ProductDesc p2, Pr
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
+  // merge the per-product lists (each ascending in q) from their ends
   const ProductDesc pds[4] = {p0, p1, p2, p3};
-  int n = 0, qlo = 0;
-  for (int x = 0; x < n_products; ++x) qlo = min(qlo, pds[x].a_pos0 + pds[x].b_pos0);
-  for (int q = Q; q >= qlo; --q)
+  int next[4];
+  for (int x = 0; x < 4; ++x) next[x] = x < n_products ? pds[x].group0 + pds[x].n_groups - 1 : -1;
+  int n = 0;
+  while (true) {
+    int best = -1;
     for (int x = 0; x < n_products; ++x)
-      for (int e = pds[x].group0; e < pds[x].group0 + pds[x].n_groups; ++e)
-        if (table[e].q == q) order[n++] = e;
+      if (next[x] >= pds[x].group0 && (best < 0 || table[next[x]].q > table[next[best]].q)) best = x;
+    if (best < 0) break;
+    order[n++] = next[best]--;
+  }
 }
 
+// One accumulation term per group: plane index, shift and the two signs.
+struct Term {
+  int32_t plane;
+  int16_t shift;
+  int8_t s0, s1;
+};
+constexpr int kMaxTerms = 4096;
+
 __global__ void k_oz_accum(AccumArgs a, OutView C) {
+  __shared__ Term terms[kMaxTerms];
+  for (int x = threadIdx.x; x < a.n_entries; x += blockDim.x) {
+    const int e = a.order[x];
+    const GroupEntry g = a.groups[e];
+    terms[x] = Term{e, (int16_t)(8 * (a.Q - g.q)), (int8_t)product_sign(a.method, 0, g.prod),
+                    (int8_t)product_sign(a.method, 1, g.prod)};
+  }
+  __syncthreads();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = blockIdx.y;
   if (j >= a.n || i >= a.m) return;
@@ -116,14 +137,13 @@ __global__ void k_oz_accum(AccumArgs a, OutView C) {
   const int64_t mn = a.m * a.n, ij = i * a.n + j;
   uint32_t words[2][kMaxWords];
   Lazy acc[2];
+  const int32_t *col = a.planes + ij;
+#pragma unroll 4
   for (int x = 0; x < a.n_entries; ++x) {
-    const int e = a.order[x];
-    const GroupEntry g = a.groups[e];
-    const int64_t v = (int64_t)a.planes[(int64_t)e * mn + ij];
-    const int shift = 8 * (a.Q - g.q);
-    const int s0 = product_sign(a.method, 0, g.prod), s1 = product_sign(a.method, 1, g.prod);
-    if (s0) acc[0].add(words[0], s0 > 0 ? v : -v, shift);
-    if (s1) acc[1].add(words[1], s1 > 0 ? v : -v, shift);
+    const Term t = terms[x];
+    const int64_t v = (int64_t)__ldg(col + (int64_t)t.plane * mn);
+    if (t.s0) acc[0].add(words[0], t.s0 > 0 ? v : -v, t.shift);
+    if (t.s1) acc[1].add(words[1], t.s1 > 0 ? v : -v, t.shift);
   }
   for (int c = 0; c < 2; ++c) {
     const bool neg = acc[c].finish(words[c], a.nslot);
