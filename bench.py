@@ -173,14 +173,16 @@ def run_ours(args):
     dC = mp.DeviceMatrix.empty(m, n, p, dev)
     stream = torch.cuda.current_stream(dev)
     method = args.method
-    pl = mp.plan(m, n, k, p, method, "ozaki")
+    params = {"kernel": args.kernel}
+    pl = mp.plan(m, n, k, p, method, "ozaki", params)
     ws = mp.Workspace(dev)
     ws.get(pl["ws_bytes"])
 
     def timed(method_, algo_, steps, warmup, with_events=False):
         evs = []
+        prm = params if algo_ == "ozaki" else None
         for _ in range(warmup):
-            mp.mpcgemm(dA, dB, dC, p, method_, algo_, workspace=ws, stream=stream)
+            mp.mpcgemm(dA, dB, dC, p, method_, algo_, workspace=ws, stream=stream, params=prm)
         torch.cuda.synchronize(dev)
         if ws_ > 1:
             tdist.barrier()
@@ -189,7 +191,7 @@ def run_ours(args):
         start.record(stream)
         for _ in range(steps):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if with_events else None
-            mp.mpcgemm(dA, dB, dC, p, method_, algo_, workspace=ws, stream=stream, events=ev)
+            mp.mpcgemm(dA, dB, dC, p, method_, algo_, workspace=ws, stream=stream, events=ev, params=prm)
             if ev:
                 evs.append(ev)
         end.record(stream)
@@ -253,7 +255,7 @@ def run_ours(args):
         def e2e_step():
             for dst, src in zip((dA.sign, dA.exp, dA.limb, dB.sign, dB.exp, dB.limb), hA + hB):
                 dst.copy_(src, non_blocking=True)
-            mp.mpcgemm(dA, dB, dC, p, method, "ozaki", workspace=ws, stream=stream)
+            mp.mpcgemm(dA, dB, dC, p, method, "ozaki", workspace=ws, stream=stream, params=params)
             for dst, src in zip(hC, (dC.sign, dC.exp, dC.limb)):
                 dst.copy_(src, non_blocking=True)
         e2e_step()
@@ -279,7 +281,7 @@ def run_ours(args):
             "data": "synthetic (seeded)",
             "config": {"workload": f"{args.workload}: ozaki {method}, m=n=k={m}, p={p} bits, entries u*2^e, "
                                    "e in [-20,20]", "method": method, "algo": "ozaki", "m": m, "n": n, "k": k,
-                       "p_bits": p, "slices": pl["s"], "cut_level_Q": pl["Q"], "pairs": pairs,
+                       "p_bits": p, "kernel": args.kernel, "slices": pl["s"], "cut_level_Q": pl["Q"], "pairs": pairs,
                        "l2": "inputs (A, B: %.2f GB) larger than L2 (126 MB)" % ((A.nbytes() + B.nbytes()) / 1e9),
                        "parallelism": f"replicas x{ws_}"},
             "stage_ms": {"split": stages[0], "slice_gemm": stages[1], "accumulate_round": stages[2],
@@ -354,6 +356,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2_2048_p1024")
     ap.add_argument("--method", choices=["3m", "4m"], default="3m")
+    ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_pair", "mma_sync"], default="auto",
+                    help="slice-GEMM kernel")
     ap.add_argument("--quick", action="store_true", help="skip the 4M / plain side measurements")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

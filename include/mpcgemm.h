@@ -70,7 +70,7 @@ extern "C" {
 /* ---- algorithm selection --------------------------------------------- */
 enum { MPC_4M = 0, MPC_3M = 1 };          /* Eq. (4m_way) / Eq. (3m_way) */
 enum { MPC_PLAIN = 0, MPC_OZAKI = 1 };    /* Eq. (simple_triple_loop) / Alg. 2 */
-enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2 };
+enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2, MPC_KERNEL_TCGEN05_PAIR = 3 };
 
 /* Largest supported precision and inner size. */
 #define MPC_MAX_P_BITS 1024
@@ -92,7 +92,9 @@ typedef struct mpc_mat {
  *   slices      s itself (0 -> the rule above); 1 <= s <= 160.
  *   cut_level   Q + 1, where pairs (t, u) with t + u <= Q are multiplied
  *               (0 -> Q = s - 1, the paper's triangle alpha + beta <= d + 1).
- *   kernel      MPC_KERNEL_*: which slice-GEMM kernel (auto = tcgen05; the mma.sync
+ *   kernel      MPC_KERNEL_*: which slice-GEMM kernel (auto = tcgen05, in CTA pairs
+ *               when m > 128; TCGEN05_PAIR always runs CTA pairs that share the B
+ *               tile by TMA multicast, TCGEN05 single CTAs; the mma.sync
  *               kernel is a second, independent implementation of the same sums).
  */
 typedef struct mpc_oz_params {

@@ -61,7 +61,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   P.p_bits = p;
   P.limbs = L;
   out->kernel = prm ? prm->kernel : MPC_KERNEL_AUTO;
-  if (out->kernel < MPC_KERNEL_AUTO || out->kernel > MPC_KERNEL_MMA_SYNC) return MPC_EINVAL;
+  if (out->kernel < MPC_KERNEL_AUTO || out->kernel > MPC_KERNEL_TCGEN05_PAIR) return MPC_EINVAL;
   uint64_t off = 0;
   P.off_status = off;
   off = align256(off + kStatusWords * 4);
@@ -331,8 +331,9 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_
     sa.status = status;
     if (pl.kernel == MPC_KERNEL_MMA_SYNC) {
       launch_slicegemm_mma(sa, st);
-    } else {   // auto: the tcgen05 kernel
-      const cudaError_t e = launch_slicegemm_tc(sa, st);
+    } else {   // auto: the tcgen05 kernel, in CTA pairs when there are at least two row tiles
+      const int pair = pl.kernel == MPC_KERNEL_TCGEN05_PAIR || (pl.kernel == MPC_KERNEL_AUTO && m > 128);
+      const cudaError_t e = launch_slicegemm_tc(sa, st, pair ? 2 : 1);
       if (e == cudaErrorNotSupported && pl.kernel == MPC_KERNEL_AUTO) launch_slicegemm_mma(sa, st);
       else if (e != cudaSuccess) return e == cudaErrorNotSupported ? MPC_ENOTSUP : cuda_code(e);
     }

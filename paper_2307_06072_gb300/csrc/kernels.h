@@ -66,7 +66,7 @@ void launch_plain_fix(const MatView &X, int side, int64_t lines, int64_t k, int 
 void launch_group_table(const ProductDesc *prods, int n_products, int Q, int gmax, GroupEntry *table,
                         int32_t *order, cudaStream_t st);
 void launch_slicegemm_mma(const SliceGemmArgs &a, cudaStream_t st);
-cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st);
+cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int cluster);
 void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st);
 void launch_fallback(const FallbackArgs &f, const MatView &A, const MatView &B, const OutView &C, int blocks,
                      int threads, cudaStream_t st);

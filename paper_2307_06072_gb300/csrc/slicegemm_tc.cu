@@ -113,6 +113,67 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
       : "memory");
 }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// shared::cluster address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_cluster(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait with cluster-scope acquire (the slot may have been written by the peer CTA)
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                                  int32_t *status) {
+  const long long t0 = clock64();
+  while (!mbar_try_cluster(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kTimeoutCycles) {
+      *abort = 1;
+      atomicOr(reinterpret_cast<int *>(status) + kStTimeout, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+// TMA load multicast to the CTAs in `mask`: same shared-memory offset and barrier offset in each
+__device__ __forceinline__ void tma_load_3d_mc(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                               uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
+      "[%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
+      : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms 1024 B apart.
 __device__ __forceinline__ uint64_t smem_desc(const void *p) {
   const uint64_t addr = smem_u32(p);
@@ -141,6 +202,15 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// arrive on the barrier at this offset in every CTA of `mask` once the issued MMAs complete
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
@@ -163,12 +233,15 @@ struct Unit {
   int e;
 };
 
-__device__ __forceinline__ Unit decode(const TcParams &P, int64_t u) {
+// unit u -> (group, tile); with CL = 2 a unit is a pair of row tiles, CTA `rank` takes one
+template <int CL>
+__device__ __forceinline__ Unit decode(const TcParams &P, int64_t u, uint32_t rank) {
   Unit x;
-  const int tiles = P.tiles_m * P.tiles_n;
+  const int tiles_mu = (P.tiles_m + CL - 1) / CL;
+  const int tiles = tiles_mu * P.tiles_n;
   x.e = (int)(u / tiles);
   const int t = (int)(u % tiles);
-  x.tm = t / P.tiles_n;
+  x.tm = (t / P.tiles_n) * CL + (int)rank;
   x.tn = t % P.tiles_n;
   x.g = P.groups[x.e];
   x.pd = P.prod[x.g.prod];
@@ -178,6 +251,14 @@ __device__ __forceinline__ Unit decode(const TcParams &P, int64_t u) {
 
 }  // namespace
 
+// CL = 1: one CTA per unit tile.  CL = 2: a cluster of two CTAs computes the
+// two vertically adjacent 128 x 256 tiles of one unit; each CTA loads half of
+// the shared 256-row B tile and multicasts it into both CTAs' shared memory,
+// so an SM fetches 32 KB instead of 48 KB per k-block.  Then both MMAs must
+// release a stage (empty barriers count 2, MMA commits are multicast) and the
+// leader CTA hands the unit indices to both CTAs through distributed shared
+// memory.
+template <int CL>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_slicegemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams P) {
   extern __shared__ uint8_t smem_raw[];
@@ -195,10 +276,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   volatile int *uring = reinterpret_cast<volatile int *>(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = CL == 2 ? cluster_rank() : 0u;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -206,7 +288,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     for (int r = 0; r < URING; ++r) {
       mbar_init(&ufull[r], 1);
-      mbar_init(&uempty[r], 1 + EPI_WARPS);
+      mbar_init(&uempty[r], CL == 2 ? 2 * (1 + EPI_WARPS) + 1 : 1 + EPI_WARPS);
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -220,9 +302,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
-  __syncthreads();
+  if (CL == 2) cluster_sync();   // every barrier of both CTAs initialised before any remote use
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // the unit ring is filled by the leader (rank 0); everyone releases slots on the leader's barrier
+  const uint32_t uempty_leader = CL == 2 ? mapa(smem_u32(uempty), 0) : smem_u32(uempty);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -232,14 +317,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       bool ok = true;
       int *counter = reinterpret_cast<int *>(P.status) + kStUnitCounter;
       while (ok) {
-        if (!mbar_wait(&uempty[slot], uphase ^ 1, abort, P.status)) { ok = false; break; }
-        int64_t u = atomicAdd(counter, 1);
-        if (u >= P.units) u = -1;
-        uring[slot] = (int)u;
-        mbar_arrive(&ufull[slot]);
+        int u;
+        if (rank == 0) {
+          if (!mbar_wait(&uempty[slot], uphase ^ 1, abort, P.status)) { ok = false; break; }
+          int64_t v = atomicAdd(counter, 1);
+          u = v >= P.units ? -1 : (int)v;
+          uring[slot] = u;
+          mbar_arrive(&ufull[slot]);
+          if (CL == 2) {
+            st_cluster_u32(mapa(smem_u32((const void *)&uring[slot]), 1), (uint32_t)u);
+            mbar_arrive_cluster(mapa(smem_u32(&ufull[slot]), 1));
+          }
+        } else {
+          if (!mbar_wait_cluster(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
+          u = uring[slot];
+          mbar_arrive_cluster(uempty_leader + 8u * (uint32_t)slot);
+        }
         if (++slot == URING) { slot = 0; uphase ^= 1; }
         if (u < 0) break;
-        const Unit x = decode(P, u);
+        const Unit x = decode<CL>(P, u, rank);
         for (int kb = 0; kb < x.nkb; ++kb) {
           const int pi = kb / P.kbpp;
           const int k0 = (kb - pi * P.kbpp) * BK;
@@ -249,7 +345,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (!mbar_wait(&empty[stage], phase ^ 1, abort, P.status)) { ok = false; break; }
           mbar_expect_tx(&full[stage], STAGE_BYTES);
           tma_load_3d(sA + stage * A_BYTES, &tmA, k0, x.tm * BM, planeA, &full[stage]);
-          tma_load_3d(sB + stage * B_BYTES, &tmB, k0, x.tn * BN, planeB, &full[stage]);
+          if (CL == 1) {
+            tma_load_3d(sB + stage * B_BYTES, &tmB, k0, x.tn * BN, planeB, &full[stage]);
+          } else {   // my half of the B tile, into the same place in both CTAs
+            tma_load_3d_mc(sB + stage * B_BYTES + rank * (B_BYTES / 2), &tmB, k0, x.tn * BN + (int)rank * (BN / 2),
+                           planeB, &full[stage], (uint16_t)0x3);
+          }
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
       }
@@ -267,12 +368,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t phase = 0, tphase = 0, uphase = 0;
       bool ok = true;
       while (ok) {
-        if (!mbar_wait(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
+        if (!mbar_wait_cluster(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
         const int u = uring[slot];
-        mbar_arrive(&uempty[slot]);
+        mbar_arrive_cluster(uempty_leader + 8u * (uint32_t)slot);
         if (++slot == URING) { slot = 0; uphase ^= 1; }
         if (u < 0) break;
-        const Unit x = decode(P, u);
+        const Unit x = decode<CL>(P, u, rank);
         for (int c0 = 0; c0 < x.nkb && ok; c0 += KB_PER_CHUNK) {
           const int cend = min(x.nkb, c0 + KB_PER_CHUNK);
           if (!mbar_wait(&tempty[buf], tphase ^ 1, abort, P.status)) { ok = false; break; }
@@ -286,7 +387,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)   // K = 16 per instruction: +32 B in the swizzled row
               mma_f16(d_tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb > c0 || kk > 0) ? 1u : 0u);
-            mma_commit(&empty[stage]);
+            if (CL == 1) mma_commit(&empty[stage]);
+            else mma_commit_mc(&empty[stage], (uint16_t)0x3);   // both CTAs wait for both MMAs
             if (++stage == STAGES) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
@@ -312,13 +414,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
     for (int x = 0; x < 128; ++x) acc[x] = 0;
     while (ok) {
-      if (!mbar_wait(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
+      if (!mbar_wait_cluster(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
       const int u = uring[slot];
       __syncwarp();
-      if (lane == 0) mbar_arrive(&uempty[slot]);
+      if (lane == 0) mbar_arrive_cluster(uempty_leader + 8u * (uint32_t)slot);
       if (++slot == URING) { slot = 0; uphase ^= 1; }
       if (u < 0) break;
-      const Unit x = decode(P, u);
+      const Unit x = decode<CL>(P, u, rank);
       for (int c0 = 0; c0 < x.nkb; c0 += KB_PER_CHUNK) {
         if (!mbar_wait(&tfull[buf], tphase, abort, P.status)) { ok = false; break; }
         tc_fence_after();
@@ -364,6 +466,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
                  : "memory");
   }
+  if (CL == 2) cluster_sync();   // neither CTA leaves while its peer may still signal it
 }
 
 // ------------------------------------------------------------------ host side
@@ -407,19 +510,21 @@ int num_sms() {
 
 }  // namespace
 
-cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st) {
+cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int cluster) {
   int dev = 0, major = 0, minor = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   if (major != 10 || minor != 3) return cudaErrorNotSupported;   // built for sm_103a only
+  if (cluster != 1 && cluster != 2) return cudaErrorInvalidValue;
   int planes_a = 0, planes_b = 0;
   for (int x = 0; x < 4; ++x) {
     if (a.prod[x].a_plane0 + a.prod[x].a_npos > planes_a) planes_a = a.prod[x].a_plane0 + a.prod[x].a_npos;
     if (a.prod[x].b_plane0 + a.prod[x].b_npos > planes_b) planes_b = a.prod[x].b_plane0 + a.prod[x].b_npos;
   }
   CUtensorMap ma, mb;
-  if (!make_map(&ma, a.dA, a.m, a.kpad, planes_a, BM) || !make_map(&mb, a.dB, a.n, a.kpad, planes_b, BN))
+  if (!make_map(&ma, a.dA, a.m, a.kpad, planes_a, BM) ||
+      !make_map(&mb, a.dB, a.n, a.kpad, planes_b, cluster == 2 ? BN / 2 : BN))
     return cudaErrorNotSupported;
   TcParams P{};
   P.m = a.m;
@@ -428,21 +533,41 @@ cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st) {
   P.n_entries = a.n_entries;
   P.tiles_m = (int)((a.m + BM - 1) / BM);
   P.tiles_n = (int)((a.n + BN - 1) / BN);
-  P.units = (int64_t)a.n_entries * P.tiles_m * P.tiles_n;
+  P.units = (int64_t)a.n_entries * ((P.tiles_m + cluster - 1) / cluster) * P.tiles_n;
   P.groups = a.groups;
   for (int x = 0; x < 4; ++x) P.prod[x] = a.prod[x];
   P.out = a.out;
   P.status = a.status;
   if (P.units == 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_slicegemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  static bool attr[3] = {false, false, false};
+  auto kfn = cluster == 2 ? k_slicegemm_tc<2> : k_slicegemm_tc<1>;
+  if (!attr[cluster]) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr[cluster] = true;
   }
-  const int grid = (int)(P.units < num_sms() ? P.units : num_sms());
-  k_slicegemm_tc<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ma, mb, P);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute la[1];
+  cfg.blockDim = dim3(NUM_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = st;
+  int ctas = num_sms();
+  if (cluster == 2) {
+    la[0].id = cudaLaunchAttributeClusterDimension;
+    la[0].val.clusterDim.x = 2;
+    la[0].val.clusterDim.y = 1;
+    la[0].val.clusterDim.z = 1;
+    cfg.attrs = la;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)ctas, 1, 1);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, kfn, &cfg) != cudaSuccess || clusters < 1) clusters = ctas / 2;
+    ctas = 2 * clusters;
+  }
+  const int64_t need = P.units * cluster;
+  if (need < ctas) ctas = (int)need;
+  cfg.gridDim = dim3((unsigned)ctas, 1, 1);
+  return cudaLaunchKernelEx(&cfg, kfn, ma, mb, P);
 }
 
 }  // namespace mpc
