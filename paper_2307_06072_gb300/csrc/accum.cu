@@ -48,7 +48,8 @@ __device__ __forceinline__ int product_sign(int method, int c, int prod) {
 
 // Exact signed integer built from terms v * 2^shift with nondecreasing shifts:
 // `lo` holds the current 32-bit word (index `cur`) plus pending carries, `hi`
-// the next; finished words are emitted to `out`.  |lo| stays below 2^43.
+// the next; finished words are emitted to `out`.  Any int64 term is split into
+// 32-bit halves first, so no intermediate exceeds 2^56 in magnitude.
 struct Lazy {
   int64_t lo = 0, hi = 0;
   int cur = 0;
@@ -58,11 +59,13 @@ struct Lazy {
     hi = 0;
   }
   __device__ __forceinline__ void add(uint32_t *out, int64_t v, int shift) {
-    const int w = shift >> 5;
+    const int w = shift >> 5, r = shift & 31;
     while (cur < w) emit(out);
-    const int64_t x = v * ((int64_t)1 << (shift & 31));   // |x| < 2^55
-    lo += x & 0xFFFFFFFFll;
-    hi += x >> 32;
+    // v 2^r = vl 2^r + vh 2^(32+r) with vl = v mod 2^32, vh = floor(v / 2^32)
+    const uint64_t xl = (uint64_t)(uint32_t)v << r;        // < 2^56
+    const int64_t vh = v >> 32;                            // |vh| < 2^31
+    lo += (int64_t)(xl & 0xFFFFFFFFull);
+    hi += (int64_t)(xl >> 32) + vh * ((int64_t)1 << r);
   }
   // emit the remaining words; returns the sign (magnitude left in out[0, nw))
   __device__ __forceinline__ bool finish(uint32_t *out, int nw) {
@@ -108,20 +111,48 @@ __global__ void k_group_table(ProductDesc p0, ProductDesc p1, ProductDesc p2, Pr
   }
 }
 
-// One accumulation term per group: plane index, shift and the two signs.
+// One accumulation term per group, in order of descending level: plane index,
+// the two signs, and -- on the last group of a level -- the level's shift.
 struct Term {
   int32_t plane;
-  int16_t shift;
+  int16_t shift;    // 8 (Q - q) on the last group of level q, else -1
   int8_t s0, s1;
 };
-constexpr int kMaxTerms = 4096;
 
-__global__ void k_oz_accum(AccumArgs a, OutView C) {
-  __shared__ Term terms[kMaxTerms];
+// Round (or queue for the exact fallback) one component of one output element.
+__device__ __forceinline__ void finish_component(const AccumArgs &a, const OutView &C, Lazy &acc, uint32_t *words,
+                                                 int c, int64_t i, int64_t j, int32_t Ei, int32_t Fj) {
+  const int64_t o = i * C.ld + j;
+  const bool neg = acc.finish(words, a.nslot);
+  WordAcc mag{words};
+  const int N = bitlen(mag, a.nslot);
+  const uint64_t b = a.bound_drop[c] + (uint64_t)a.k * ((a.lossyA[i] ? a.bound_lossy_a[c] : 0ull) +
+                                                        (a.lossyB[j] ? a.bound_lossy_b[c] : 0ull));
+  if (N == 0 && b == 0) {
+    store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+  } else if (N > 0 && certified(mag, a.nslot, N, a.p, b, a.bound_shift)) {
+    const int64_t scale = (int64_t)Ei + (int64_t)Fj - kProdLog2 - 8 * (int64_t)a.Q;
+    if (!round_store(mag, a.nslot, N, neg, scale, a.p, a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o,
+                     C.plane)) {
+      status_set(a.status, kStErange, 1);
+      store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+    }
+  } else {
+    const int slot = atomicAdd(reinterpret_cast<int *>(a.status) + kStFallbackCount, 1);
+    if (slot < a.fallback_cap) a.fallback[slot] = (i * a.n + j) * 2 + c;
+    else status_set(a.status, kStFallbackOverflow, 1);
+  }
+}
+
+// One thread per output element (i, j).  The groups of one level are summed in
+// plain int64 (|sum| < 2^36) and folded into the exact accumulators once per level.
+__global__ void __launch_bounds__(128) k_oz_accum(AccumArgs a, OutView C) {
+  extern __shared__ Term terms[];
   for (int x = threadIdx.x; x < a.n_entries; x += blockDim.x) {
     const int e = a.order[x];
     const GroupEntry g = a.groups[e];
-    terms[x] = Term{e, (int16_t)(8 * (a.Q - g.q)), (int8_t)product_sign(a.method, 0, g.prod),
+    const bool last = (x + 1 == a.n_entries) || (a.groups[a.order[x + 1]].q != g.q);
+    terms[x] = Term{e, (int16_t)(last ? 8 * (a.Q - g.q) : -1), (int8_t)product_sign(a.method, 0, g.prod),
                     (int8_t)product_sign(a.method, 1, g.prod)};
   }
   __syncthreads();
@@ -129,43 +160,29 @@ __global__ void k_oz_accum(AccumArgs a, OutView C) {
   const int64_t i = blockIdx.y;
   if (j >= a.n || i >= a.m) return;
   const int32_t Ei = a.E[i], Fj = a.F[j];
-  const int64_t o = i * C.ld + j;
   if (Ei == INT32_MIN || Fj == INT32_MIN) {   // a zero row or column: the product is exactly 0
+    const int64_t o = i * C.ld + j;
     for (int c = 0; c < 2; ++c) store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
     return;
   }
-  const int64_t mn = a.m * a.n, ij = i * a.n + j;
+  const int64_t mn = a.m * a.n;
+  const int32_t *col = a.planes + i * a.n + j;
   uint32_t words[2][kMaxWords];
   Lazy acc[2];
-  const int32_t *col = a.planes + ij;
-#pragma unroll 4
+  int64_t sum0 = 0, sum1 = 0;
+#pragma unroll 8
   for (int x = 0; x < a.n_entries; ++x) {
     const Term t = terms[x];
     const int64_t v = (int64_t)__ldg(col + (int64_t)t.plane * mn);
-    if (t.s0) acc[0].add(words[0], t.s0 > 0 ? v : -v, t.shift);
-    if (t.s1) acc[1].add(words[1], t.s1 > 0 ? v : -v, t.shift);
-  }
-  for (int c = 0; c < 2; ++c) {
-    const bool neg = acc[c].finish(words[c], a.nslot);
-    WordAcc mag{words[c]};
-    const int N = bitlen(mag, a.nslot);
-    const uint64_t b = a.bound_drop[c] + (uint64_t)a.k * ((a.lossyA[i] ? a.bound_lossy_a[c] : 0ull) +
-                                                          (a.lossyB[j] ? a.bound_lossy_b[c] : 0ull));
-    if (N == 0 && b == 0) {
-      store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
-    } else if (N > 0 && certified(mag, a.nslot, N, a.p, b, a.bound_shift)) {
-      const int64_t scale = (int64_t)Ei + (int64_t)Fj - kProdLog2 - 8 * (int64_t)a.Q;
-      if (!round_store(mag, a.nslot, N, neg, scale, a.p, a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o,
-                       C.plane)) {
-        status_set(a.status, kStErange, 1);
-        store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
-      }
-    } else {
-      const int slot = atomicAdd(reinterpret_cast<int *>(a.status) + kStFallbackCount, 1);
-      if (slot < a.fallback_cap) a.fallback[slot] = ij * 2 + c;
-      else status_set(a.status, kStFallbackOverflow, 1);
+    sum0 += v * t.s0;
+    sum1 += v * t.s1;
+    if (t.shift >= 0) {
+      acc[0].add(words[0], sum0, t.shift);
+      acc[1].add(words[1], sum1, t.shift);
+      sum0 = sum1 = 0;
     }
   }
+  for (int c = 0; c < 2; ++c) finish_component(a, C, acc[c], words[c], c, i, j, Ei, Fj);
 }
 
 // ------------------------------------------------------------------ fallback
@@ -323,7 +340,7 @@ void launch_group_table(const ProductDesc *prods, int n_products, int Q, int gma
 void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st) {
   const int T = 128;
   dim3 g((unsigned)((a.n + T - 1) / T), (unsigned)a.m);
-  k_oz_accum<<<g, T, 0, st>>>(a, C);
+  k_oz_accum<<<g, T, (size_t)a.n_entries * sizeof(Term), st>>>(a, C);
 }
 
 void launch_fallback(const FallbackArgs &f, const MatView &A, const MatView &B, const OutView &C, int blocks,

@@ -94,82 +94,140 @@ __device__ __forceinline__ bool low_bits_zero(const uint64_t *M, int L, int64_t 
   return true;
 }
 
-// One thread per (line, l): digits of element (line, l) of the operand.
+// 64 bits of the L-limb integer M starting at bit b (zero outside [0, 64L)).
+__device__ __forceinline__ uint64_t word_at_bit(const uint64_t *M, int L, int64_t b) {
+  if (b >= 64 * (int64_t)L || b <= -64) return 0;
+  const int64_t w = b >> 6;           // floor division (b may be negative)
+  const int off = (int)(b & 63);
+  const uint64_t lo = (w >= 0 && w < L) ? M[w] : 0ull;
+  const uint64_t hi = (w + 1 >= 0 && w + 1 < L) ? M[w + 1] : 0ull;
+  return off ? ((lo >> off) | (hi << (64 - off))) : lo;
+}
+
+// Per element: the shifted magnitude |X| = M >> sh, read 64 bits at a time
+// as a two's-complement word stream of X = sign |X|, and turned into balanced
+// base-256 digits (and, for 3M, the digits of X_re + X_im).
+struct DigitStream {
+  uint64_t M[2][kMaxLimbs];
+  int64_t sh[2];
+  int neg[2];
+  uint64_t cneg[2];      // +1 carry of the two's complement
+  uint64_t csum;         // carry of X_re + X_im
+  int cbal[2], cbal_s;   // balanced-digit carries
+};
+
+// One thread per (line, l, l+1): digits of two adjacent elements of a line.
 // Side A: line = row i, element (i, l).  Side B: line = column j, element (l, j).
 // Output planes: digits[(plane * lines + line) * kpad + l], plane = t (real),
 // s + t (imaginary), 2s + 1 + t (sums, t = -1 .. s-1).
 __global__ void k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
                             int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits) {
-  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t line = blockIdx.y;
-  if (l >= kpad || line >= lines) return;
+  const int64_t l0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  const int64_t line = blockIdx.y;
+  if (l0 >= kpad || line >= lines) return;    // kpad is even: l0 + 1 < kpad
   const int64_t pstride = lines * kpad;
-  __nv_bfloat16 *out = digits + line * kpad + l;
+  __nv_bfloat162 *out = reinterpret_cast<__nv_bfloat162 *>(digits + line * kpad + l0);
+  const int64_t pstride2 = pstride / 2;
   const int nplanes = 2 * s + (want_sum ? s + 1 : 0);
-  int32_t e_line = E[line];
-  if (l >= k || e_line == INT32_MIN) {
-    for (int pl = 0; pl < nplanes; ++pl) out[pl * pstride] = __float2bfloat16_rn(0.0f);
-    return;
-  }
-  int64_t idx = side == 0 ? line * X.ld + l : l * X.ld + line;
-  uint64_t M[2][kMaxLimbs];
-  int64_t sh[2];
-  int neg[2];
+  const int32_t e_line = E[line];
+  DigitStream d[2];
   bool ok = true;
+  bool any = false;
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    bool nz = comp_nonzero(X, c, idx, L);
-    for (int j = 0; j < L; ++j) M[c][j] = nz ? X.limb[c][(int64_t)j * X.plane + idx] : 0ull;
-    // |X| bit b  <->  M bit b + sh:  X = |v| 2^(8s-1-E), |v| = M 2^(exp-64L)
-    sh[c] = nz ? (64 * (int64_t)L + (int64_t)e_line - (int64_t)X.exp[c][idx] - (8 * (int64_t)s - 1)) : 0;
-    neg[c] = nz ? X.sign[c][idx] : 0;
-    if (nz) {
-      if (sh[c] >= 64 * (int64_t)L) ok = false;            // every bit dropped (M != 0)
-      else if (!low_bits_zero(M[c], L, sh[c])) ok = false;  // some low bits dropped
-    }
-  }
-  if (!ok) atomicOr(lossy + line, 1);
-  // walk the bytes of the two's-complement integers from the bottom
-  int cneg[2] = {1, 1}, cbal[2] = {0, 0};
-  int csum = 0, cbal_s = 0;
-  for (int pos = 0; pos <= s; ++pos) {
-    int bt[2];
+  for (int q = 0; q < 2; ++q) {
+    const int64_t l = l0 + q;
+    const bool live = (l < k) && (e_line != INT32_MIN);
+    any |= live;
+    const int64_t idx = side == 0 ? line * X.ld + l : l * X.ld + line;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      uint32_t b = (pos < s) ? byte_at(M[c], L, 8 * (int64_t)pos + sh[c]) : 0u;
-      if (neg[c]) {
-        uint32_t v = ((~b) & 0xFFu) + (uint32_t)cneg[c];
-        cneg[c] = (int)(v >> 8);
-        b = v & 0xFFu;
-      }
-      bt[c] = (int)b;
-      if (pos < s) {
-        int d;
-        if (pos == s - 1) {
-          d = (int)(int8_t)(uint8_t)b + cbal[c];            // top digit: signed byte + carry
-        } else {
-          d = (int)b + cbal[c];
-          cbal[c] = d >= 128;
-          if (d >= 128) d -= 256;
-        }
-        int plane = c * s + (s - 1 - pos);
-        out[plane * pstride] = __float2bfloat16_rn((float)d);
+      const bool nz = live && comp_nonzero(X, c, idx, L);
+      for (int j = 0; j < L; ++j) d[q].M[c][j] = nz ? X.limb[c][(int64_t)j * X.plane + idx] : 0ull;
+      // |X| bit b  <->  M bit b + sh:  X = |v| 2^(8s-1-E), |v| = M 2^(exp-64L)
+      d[q].sh[c] = nz ? (64 * (int64_t)L + (int64_t)e_line - (int64_t)X.exp[c][idx] - (8 * (int64_t)s - 1)) : 0;
+      d[q].neg[c] = nz ? X.sign[c][idx] : 0;
+      d[q].cneg[c] = 1;
+      d[q].cbal[c] = 0;
+      if (nz) {
+        if (d[q].sh[c] >= 64 * (int64_t)L) ok = false;                  // every bit dropped (M != 0)
+        else if (!low_bits_zero(d[q].M[c], L, d[q].sh[c])) ok = false;  // some low bits dropped
       }
     }
-    if (want_sum) {
-      int S = bt[0] + bt[1] + csum;
-      csum = S >> 8;
-      S &= 0xFF;
-      int d;
-      if (pos == s) {
-        d = (int)(int8_t)(uint8_t)S + cbal_s;
-      } else {
-        d = S + cbal_s;
-        cbal_s = d >= 128;
-        if (d >= 128) d -= 256;
+    d[q].csum = 0;
+    d[q].cbal_s = 0;
+  }
+  if (!ok) atomicOr(lossy + line, 1);
+  if (!any) {
+    const __nv_bfloat162 z = __floats2bfloat162_rn(0.0f, 0.0f);
+    for (int pl = 0; pl < nplanes; ++pl) out[pl * pstride2] = z;
+    return;
+  }
+  const int nbytes = want_sum ? s + 1 : s;
+  for (int w = 0; 8 * w < nbytes; ++w) {
+    uint64_t wc[2][2];   // two's-complement words [element][component]
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        uint64_t x = word_at_bit(d[q].M[c], L, 64 * (int64_t)w + d[q].sh[c]);
+        if (8 * w + 8 > s) x &= (s - 8 * w >= 8) ? ~0ull : ((1ull << (8 * (s - 8 * w))) - 1ull);   // |X| has 8s bits
+        if (d[q].neg[c]) {
+          const uint64_t t = ~x + d[q].cneg[c];
+          d[q].cneg[c] = (d[q].cneg[c] && t == 0) ? 1ull : 0ull;
+          x = t;
+        }
+        wc[q][c] = x;
       }
-      int plane = 2 * s + (s - pos);   // position t = s-1-pos -> plane 2s + 1 + t
-      out[plane * pstride] = __float2bfloat16_rn((float)d);
+    uint64_t ws_[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint64_t a = wc[q][0] + wc[q][1];
+      const uint64_t c1 = a < wc[q][0];
+      const uint64_t b = a + d[q].csum;
+      const uint64_t c2 = b < a;
+      ws_[q] = b;
+      d[q].csum = c1 | c2;
+    }
+    for (int by = 0; by < 8; ++by) {
+      const int pos = 8 * w + by;
+      if (pos > s || (pos == s && !want_sum)) break;
+      if (pos < s) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          float f[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int b = (int)((wc[q][c] >> (8 * by)) & 0xFF);
+            int dg;
+            if (pos == s - 1) {
+              dg = (int)(int8_t)(uint8_t)b + d[q].cbal[c];   // top digit: signed byte + carry
+            } else {
+              dg = b + d[q].cbal[c];
+              d[q].cbal[c] = dg >= 128;
+              if (dg >= 128) dg -= 256;
+            }
+            f[q] = (float)dg;
+          }
+          out[(int64_t)(c * s + (s - 1 - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
+        }
+      }
+      if (want_sum) {
+        float f[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int S = (int)((ws_[q] >> (8 * by)) & 0xFF);
+          int dg;
+          if (pos == s) {
+            dg = (int)(int8_t)(uint8_t)S + d[q].cbal_s;
+          } else {
+            dg = S + d[q].cbal_s;
+            d[q].cbal_s = dg >= 128;
+            if (dg >= 128) dg -= 256;
+          }
+          f[q] = (float)dg;
+        }
+        out[(int64_t)(2 * s + (s - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
+      }
     }
   }
 }
@@ -234,7 +292,7 @@ void launch_line_max(const MatView &A, const MatView &B, int64_t m, int64_t n, i
 
 void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
                       int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, cudaStream_t st) {
-  dim3 g((unsigned)((kpad + 127) / 128), (unsigned)lines);
+  dim3 g((unsigned)((kpad / 2 + 127) / 128), (unsigned)lines);
   k_oz_digits<<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits);
 }
 
