@@ -44,6 +44,7 @@ WORKLOADS = {
     "c2_1024_p1024": (1024, 1024, 1024, 1024, "uniform_exp", 2),
     "c1_256_p256": (256, 256, 256, 256, "uniform", 1),
 }
+BATCH_WORKLOAD = "c3_batch64"
 PROFILE = os.path.join(ROOT, "profiles", "oz_slicegemm_c2_2048_p1024.md")
 SLICEGEMM_SRC = os.path.join(ROOT, "paper_2307_06072_gb300", "csrc", "slicegemm_tc.cu")
 
@@ -64,6 +65,59 @@ def make_inputs(workload: str, rank: int):
     A = si.random_matrix(m, k, p, si.SEED_BASE + idx + 7919 * rank, dist)
     B = si.random_matrix(k, n, p, si.SEED_BASE + idx + 1000 + 7919 * rank, dist)
     return A, B, p
+
+
+def batch_specs(count: int = 64, seed: int = si.SEED_BASE + 3):
+    """Config 3: m, n, k log-uniform in [64, 1024], p from {256, 512, 1024}, 3M."""
+    rng = np.random.default_rng(seed)
+    mnk = np.exp(rng.uniform(np.log(64), np.log(1024), size=(count, 3))).astype(int)
+    ps = rng.choice([256, 512, 1024], size=count)
+    return [(int(m), int(k), int(n), int(p)) for (m, n, k), p in zip(mnk, ps)]
+
+
+def run_batched(mp, torch, dev, stream, steps: int, warmup: int):
+    """One step = one batched call over the 64 problems, replayed from a CUDA graph."""
+    from paper_2307_06072_gb300.autotune import Autotuner
+    stream = torch.cuda.Stream(dev)          # graphs are captured on a side stream
+    specs = batch_specs()
+    probs = []
+    for x, (m, k, n, p) in enumerate(specs):
+        A = si.random_matrix(m, k, p, si.SEED_BASE + 3000 + 2 * x, "uniform")
+        B = si.random_matrix(k, n, p, si.SEED_BASE + 3001 + 2 * x, "uniform")
+        probs.append((mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(B, dev),
+                      mp.DeviceMatrix.empty(m, n, p, dev), p, "3m", "ozaki"))
+    tuner = Autotuner()
+    best = tuner.choose(probs, stream=stream)
+    total, _ = mp.batched_workspace(probs, best)
+    ws = mp.Workspace(dev)
+    ws.get(total)
+    mp.mpcgemm_batched(probs, best, ws, stream)
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        mp.mpcgemm_batched(probs, best, ws, stream)
+    with torch.cuda.stream(stream):          # replay on the stream the events are recorded on
+        for _ in range(warmup):
+            g.replay()
+        torch.cuda.synchronize(dev)
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(steps):
+            g.replay()
+        end.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = start.elapsed_time(end) / steps
+    work = sum(8.0 * m * n * k for (m, k, n, p) in specs)
+    flops = 0.0
+    for (m, k, n, p) in specs:
+        pl = mp.plan(m, n, k, p, "3m", "ozaki", best)
+        flops += pair_count(pl["s"], pl["Q"], "3m") * 2.0 * m * n * k
+    return {"value": work / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "problems": len(specs),
+            "sum_8mnk": work, "tuned": best, "tuning_ms": {str(c): round(t, 3) for c, t in tuner.last_timings},
+            "workspace_gb": round(total / 1e9, 2),
+            "tensor_tflops_whole_call": round(flops / (ms / 1e3) / 1e12, 1),
+            "launch": "one CUDA graph replay per step (split/accumulate per problem, one persistent "
+                      "tcgen05 slice-GEMM launch for all problems)"}
 
 
 def pair_count(s: int, Q: int, method: str) -> int:
@@ -165,6 +219,28 @@ def run_ours(args):
         tdist.barrier()
     import paper_2307_06072_gb300 as mp
 
+    if args.workload == BATCH_WORKLOAD:
+        stream = torch.cuda.current_stream(dev)
+        with ClockSampler(dev.index or 0) as clocks:
+            r = run_batched(mp, torch, dev, stream, args.steps, args.warmup)
+        if rank == 0:
+            peaks, peak_src = measured_peaks()
+            peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+            line = {"metric": METRIC, "value": r["value"] * ws_, "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
+                    "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None, "dtype": "bf16 slices (exact int), u64 limbs",
+                    "data": "synthetic (seeded)",
+                    "config": {"workload": "c3_batch64: 64 Ozaki 3M GEMMs, m,n,k log-uniform in [64,1024], "
+                                           "p in {256,512,1024}, uniform [-1,1) entries, CUDA-graph replay",
+                               "parallelism": f"replicas x{ws_}"},
+                    "roofline": {"bound": "tensor", "achieved": r["tensor_tflops_whole_call"], "peak": peak,
+                                 "unit": "TFLOP/s", "frac": round(r["tensor_tflops_whole_call"] / peak, 4),
+                                 "traffic": None, "kernel": "whole batched call (slice pairs x 2mnk / call time)",
+                                 "peak_source": f"bf16_tflops_sustained ({peak_src})"},
+                    "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks.summary(),
+                    "batched": r}
+            print(json.dumps(line), flush=True)
+        return
     m, n, k, p, dist, _ = WORKLOADS[args.workload]
     t0 = time.time()
     A, B, p = make_inputs(args.workload, rank)
@@ -228,6 +304,8 @@ def run_ours(args):
         extras["plain_4m"] = {"value": units * ws_ / (max_over_ranks(ms_pl) / 1e3), "ms_per_step": ms_pl,
                               "stage_ms": st_pl}
         extras["ozaki_speedup_vs_plain"] = value / extras["plain_4m"]["value"]
+        if not args.no_batched:
+            extras["batched_c3"] = run_batched(mp, torch, dev, stream, 3, 3)
 
     # roofline of the dominant kernel (the slice GEMM): algorithmic MMA flops / its event time
     pairs = pair_count(pl["s"], pl["Q"], method)
@@ -242,32 +320,74 @@ def run_ours(args):
                 "kernel": "oz_slicegemm", "peak_source": f"bf16_tflops_sustained ({peak_src})",
                 "algorithmic_flops_per_launch": flops, "kernel_ms": round(gemm_ms, 3)}
 
-    # e2e through the public API with host buffers: H2D of A, B and D2H of C inside the region
+    # e2e through the public API with host buffers: every step copies its inputs from
+    # pinned host memory and its result back, inside the timed region.  Two device
+    # buffer sets let step i+1's input copy and step i's output copy (copy stream)
+    # overlap step i's compute (compute stream), as a user of the async API would.
     e2e = None
     if not args.no_e2e:
-        hA = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (A.sign, A.exp, A.limb.view(np.int64))]
-        hB = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (B.sign, B.exp, B.limb.view(np.int64))]
-        hC = [torch.empty_like(dC.sign, device="cpu").pin_memory(), torch.empty_like(dC.exp, device="cpu").pin_memory(),
-              torch.empty_like(dC.limb, device="cpu").pin_memory()]
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hA = [pin(A.sign), pin(A.exp), pin(A.limb.view(np.int64))]
+        hB = [pin(B.sign), pin(B.exp), pin(B.limb.view(np.int64))]
+        hC = [[torch.empty_like(t, device="cpu").pin_memory() for t in (dC.sign, dC.exp, dC.limb)] for _ in range(2)]
         h2d = sum(t.numel() * t.element_size() for t in hA + hB)
-        d2h = sum(t.numel() * t.element_size() for t in hC)
+        d2h = sum(t.numel() * t.element_size() for t in hC[0])
+        sets = [(dA, dB, dC), (mp.DeviceMatrix.empty(m, k, p, dev), mp.DeviceMatrix.empty(k, n, p, dev),
+                             mp.DeviceMatrix.empty(m, n, p, dev))]
+        cstream = torch.cuda.Stream(dev)
+        ev = lambda: torch.cuda.Event()
 
-        def e2e_step():
-            for dst, src in zip((dA.sign, dA.exp, dA.limb, dB.sign, dB.exp, dB.limb), hA + hB):
-                dst.copy_(src, non_blocking=True)
-            mp.mpcgemm(dA, dB, dC, p, method, "ozaki", workspace=ws, stream=stream, params=params)
-            for dst, src in zip(hC, (dC.sign, dC.exp, dC.limb)):
-                dst.copy_(src, non_blocking=True)
-        e2e_step()
-        torch.cuda.synchronize(dev)
+        def run_e2e(steps):
+            h2d_done, comp_done, d2h_done = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+            comp_started = [False, False]
+
+            def copy_in(bset, ready):
+                with torch.cuda.stream(cstream):
+                    if ready is not None:
+                        cstream.wait_event(ready)
+                    X, Y, _ = sets[bset]
+                    for dst, src in zip((X.sign, X.exp, X.limb, Y.sign, Y.exp, Y.limb), hA + hB):
+                        dst.copy_(src, non_blocking=True)
+                    h2d_done[bset].record(cstream)
+            copy_in(0, None)
+            for i in range(steps):
+                b_ = i % 2
+                X, Y, Z = sets[b_]
+                stream.wait_event(h2d_done[b_])
+                if i >= 2:
+                    stream.wait_event(d2h_done[b_])
+                mp.mpcgemm(X, Y, Z, p, method, "ozaki", workspace=ws, stream=stream, params=params)
+                comp_done[b_].record(stream)
+                comp_started[b_] = True
+                if i + 1 < steps:
+                    nb = (i + 1) % 2
+                    copy_in(nb, comp_done[nb] if comp_started[nb] else None)
+                with torch.cuda.stream(cstream):
+                    cstream.wait_event(comp_done[b_])
+                    for dst, src in zip(hC[b_], (Z.sign, Z.exp, Z.limb)):
+                        dst.copy_(src, non_blocking=True)
+                    d2h_done[b_].record(cstream)
+            torch.cuda.synchronize(dev)
+
+        run_e2e(2)
         t1 = time.perf_counter()
-        es = max(1, args.steps // 2)
-        for _ in range(es):
-            e2e_step()
-        torch.cuda.synchronize(dev)
+        es = max(2, args.steps)
+        run_e2e(es)
         e2e_s = max_over_ranks(time.perf_counter() - t1)
+        # raw copy bandwidths, for the record
+        t2 = time.perf_counter()
+        for dst, src in zip((dA.sign, dA.exp, dA.limb, dB.sign, dB.exp, dB.limb), hA + hB):
+            dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        t3 = time.perf_counter()
+        for dst, src in zip(hC[0], (dC.sign, dC.exp, dC.limb)):
+            dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        t4 = time.perf_counter()
         e2e = {"value": units * es * ws_ / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h, "steps": es,
+               "pipeline": "double-buffered: copies of step i+1 / i on a second stream overlap step i",
+               "h2d_gbs": round(h2d / (t3 - t2) / 1e9, 1), "d2h_gbs": round(d2h / (t4 - t3) / 1e9, 1)}
 
     cpu = None
     if rank == 0 and ws_ == 1 and not args.no_cpu:
@@ -354,7 +474,8 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2_2048_p1024")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD], default="c2_2048_p1024")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched side measurement")
     ap.add_argument("--method", choices=["3m", "4m"], default="3m")
     ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_pair", "mma_sync"], default="auto",
                     help="slice-GEMM kernel")

@@ -92,6 +92,8 @@ typedef struct mpc_mat {
  *   slices      s itself (0 -> the rule above); 1 <= s <= 160.
  *   cut_level   Q + 1, where pairs (t, u) with t + u <= Q are multiplied
  *               (0 -> Q = s - 1, the paper's triangle alpha + beta <= d + 1).
+ *   max_group   cap on the slice pairs summed in one group (0 -> the int32 limit
+ *               G_max); smaller groups make more, shorter work units.
  *   kernel      MPC_KERNEL_*: which slice-GEMM kernel (auto = tcgen05, in CTA pairs
  *               when m > 128; TCGEN05_PAIR always runs CTA pairs that share the B
  *               tile by TMA multicast, TCGEN05 single CTAs; the mma.sync
@@ -102,6 +104,8 @@ typedef struct mpc_oz_params {
     int32_t slices;
     int32_t cut_level;
     int32_t kernel;
+    int32_t max_group;
+    int32_t reserved[3];
 } mpc_oz_params;
 
 /*
@@ -184,6 +188,31 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits,
                      int method, int algo, const mpc_oz_params *params,
                      const mpc_stage_events *events,
                      void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Batched form: `count` independent complex GEMMs, possibly of different sizes,
+ * precisions and methods, in one call.  The Ozaki problems share ONE persistent
+ * tcgen05 slice-GEMM launch (48 problems per launch), so small problems fill
+ * the GPU together; the split, accumulation and fallback kernels run per
+ * problem.  The call is asynchronous and allocates nothing, so it can be
+ * captured in a CUDA graph and replayed.  Each problem uses its own region of
+ * the workspace, at offsets[i] from mpcgemm_batched_workspace(); its device
+ * status is read with mpcgemm_read_status(workspace + offsets[i], ...).
+ * This extends the paper's CGEMM (Sec. III) to a batch; the paper has no batch.
+ */
+typedef struct mpc_problem {
+    int64_t m, n, k;
+    int32_t p_bits, method, algo, reserved;
+    const mpc_mat *A, *B;
+    mpc_mat *C;
+} mpc_problem;
+
+/* Per-problem workspace offsets (offsets may be NULL) and the total bytes. */
+int mpcgemm_batched_workspace(int count, const mpc_problem *probs, const mpc_oz_params *params,
+                              uint64_t *offsets, size_t *total);
+
+int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *params,
+                    void *workspace, size_t ws_bytes, void *stream);
 
 /* Bytes of workspace a call with these arguments needs (0 on bad arguments). */
 size_t mpcgemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t p_bits,

@@ -78,11 +78,13 @@ class Params:
 
 
 def make_params(p: int, k: int, method: str = "4m", guard: int = DEFAULT_GUARD,
-                s: int | None = None, Q: int | None = None) -> Params:
-    """Slice count s and cut level Q.
+                s: int | None = None, Q: int | None = None, max_group: int = 0) -> Params:
+    """Slice count s, cut level Q and group size.
 
     s = ceil((p + ceil(log2 k) + guard) / 8) digits; Q = s - 1 (the paper's
-    triangle alpha + beta <= d + 1).  Both may be overridden.
+    triangle alpha + beta <= d + 1).  Both may be overridden.  Groups hold at
+    most Gmax pairs (the int32 limit), or ``max_group`` if smaller; the level
+    sums do not depend on the grouping.
     """
     if s is None:
         s = -(-(p + ceil_log2(k) + guard) // DIGIT_BITS)
@@ -91,6 +93,8 @@ def make_params(p: int, k: int, method: str = "4m", guard: int = DEFAULT_GUARD,
     gmax = INT32_MAX // (k << PROD_LOG2) if k > 0 else 1
     if gmax < 1:
         raise ValueError("k too large for int32 group sums")
+    if max_group > 0:
+        gmax = min(gmax, max_group)
     return Params(p=p, k=k, s=s, Q=Q, gmax=gmax, method=method, guard=guard)
 
 
@@ -364,13 +368,13 @@ class OzakiResult:
 
 
 def ozaki_cgemm(A, B, p: int, method: str = "4m", guard: int = DEFAULT_GUARD,
-                s: int | None = None, Q: int | None = None, fallback=None) -> OzakiResult:
+                s: int | None = None, Q: int | None = None, fallback=None, max_group: int = 0) -> OzakiResult:
     """Emulate the whole Ozaki complex GEMM; ``fallback(i, j) -> (re, im)`` exact values.
 
     Without ``fallback`` the exact O1 triple loop is used for uncertified entries.
     """
     m, k, n = A.rows, A.cols, B.cols
-    prm = make_params(p, k, method, guard, s, Q)
+    prm = make_params(p, k, method, guard, s, Q, max_group)
     spA = split_operand(A, prm.s, "A", method)
     spB = split_operand(B, prm.s, "B", method)
     groups, sums, acc_p = {}, {}, {}

@@ -20,8 +20,8 @@ import numpy as np
 from . import _native
 from ._native import MPCError, check, lib, oz_params, strerror  # noqa: F401
 
-__all__ = ["DeviceMatrix", "mpcgemm", "workspace_size", "plan", "read_status", "strerror", "version",
-           "MPCError", "Workspace"]
+__all__ = ["DeviceMatrix", "mpcgemm", "mpcgemm_batched", "batched_workspace", "workspace_size", "plan",
+           "read_status", "strerror", "version", "MPCError", "Workspace"]
 
 
 def _torch():
@@ -175,9 +175,50 @@ def mpcgemm(A: DeviceMatrix, B: DeviceMatrix, C: DeviceMatrix, p: int, method: s
     return ws
 
 
-def read_status(workspace: Workspace, stream=None) -> dict:
+def _problems(problems):
+    """ctypes array of mpc_problem (and the structs it points to, kept alive)."""
+    arr = (_native.MpcProblem * len(problems))()
+    keep = []
+    for x, (A, B, C, p, method, algo) in enumerate(problems):
+        sa, sb, sc = A.struct(), B.struct(), C.struct()
+        keep += [sa, sb, sc]
+        arr[x] = _native.MpcProblem(A.rows, B.cols, A.cols, p, _native.METHODS[method], _native.ALGOS[algo], 0,
+                                    ctypes.addressof(sa), ctypes.addressof(sb), ctypes.addressof(sc))
+    return arr, keep
+
+
+def batched_workspace(problems, params=None):
+    """(total bytes, per-problem offsets) for ``mpcgemm_batched``."""
+    arr, keep = _problems(problems)
+    prm = params if params is None or isinstance(params, _native.OzParams) else oz_params(**params)
+    offs = (ctypes.c_uint64 * max(1, len(problems)))()
+    total = ctypes.c_size_t()
+    check(lib().mpcgemm_batched_workspace(len(problems), arr, ctypes.byref(prm) if prm is not None else None,
+                                          offs, ctypes.byref(total)))
+    return int(total.value), [int(offs[x]) for x in range(len(problems))]
+
+
+def mpcgemm_batched(problems, params=None, workspace: Workspace | None = None, stream=None) -> Workspace:
+    """Many complex GEMMs in one call; ``problems``: list of (A, B, C, p, method, algo).
+
+    The Ozaki problems share one persistent tcgen05 launch.  Asynchronous and
+    allocation-free inside the library, so it can be captured in a CUDA graph.
+    """
+    arr, keep = _problems(problems)
+    prm = params if params is None or isinstance(params, _native.OzParams) else oz_params(**params)
+    total, _ = batched_workspace(problems, prm)
+    ws = workspace if workspace is not None else Workspace(problems[0][0].sign.device)
+    t = ws.get(total)
+    check(lib().mpcgemm_batched(len(problems), arr, ctypes.byref(prm) if prm is not None else None, t.data_ptr(),
+                                t.numel(), _stream_handle(stream)))
+    return ws
+
+
+def read_status(workspace: Workspace, stream=None, offset: int = 0) -> dict:
+    """Device status of the last call on this workspace (``offset``: a batched problem's region)."""
     st = _native.Status()
-    code = lib().mpcgemm_read_status(workspace.ptr, workspace.nbytes, ctypes.byref(st), _stream_handle(stream))
+    code = lib().mpcgemm_read_status(workspace.ptr + offset, workspace.nbytes - offset, ctypes.byref(st),
+                                     _stream_handle(stream))
     if code not in (_native.MPC_OK, _native.MPC_ERANGE):
         check(code)
     return {"erange": st.erange, "fallback_entries": st.fallback_entries,

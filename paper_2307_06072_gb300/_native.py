@@ -21,7 +21,8 @@ ALGOS = {"plain": 0, "ozaki": 1}
 KERNELS = {"auto": 0, "tcgen05": 1, "mma_sync": 2, "tcgen05_pair": 3}
 
 EXPORTED = ("mpcgemm", "mpcgemm_ex", "mpcgemm_profiled", "mpcgemm_workspace_size", "mpcgemm_plan",
-            "mpcgemm_read_status", "mpcgemm_noalloc", "mpcgemm_strerror", "mpcgemm_version")
+            "mpcgemm_read_status", "mpcgemm_noalloc", "mpcgemm_batched", "mpcgemm_batched_workspace",
+            "mpcgemm_strerror", "mpcgemm_version")
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -32,7 +33,14 @@ class MpcMat(ctypes.Structure):
 
 class OzParams(ctypes.Structure):
     _fields_ = [("guard_bits", ctypes.c_int32), ("slices", ctypes.c_int32),
-                ("cut_level", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+                ("cut_level", ctypes.c_int32), ("kernel", ctypes.c_int32), ("max_group", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class MpcProblem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64), ("p_bits", ctypes.c_int32),
+                ("method", ctypes.c_int32), ("algo", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p)]
 
 
 class Plan(ctypes.Structure):
@@ -97,6 +105,10 @@ def lib():
         L.mpcgemm_plan.restype = ctypes.c_int
         L.mpcgemm_read_status.argtypes = [P, ctypes.c_size_t, P, P]
         L.mpcgemm_read_status.restype = ctypes.c_int
+        L.mpcgemm_batched.argtypes = [ctypes.c_int, P, P, P, ctypes.c_size_t, P]
+        L.mpcgemm_batched.restype = ctypes.c_int
+        L.mpcgemm_batched_workspace.argtypes = [ctypes.c_int, P, P, P, P]
+        L.mpcgemm_batched_workspace.restype = ctypes.c_int
         L.mpcgemm_noalloc.argtypes = [I64, I64, I64, I32, P, P, P, ctypes.c_int, ctypes.c_int, P]
         L.mpcgemm_noalloc.restype = ctypes.c_int
         L.mpcgemm_strerror.argtypes = [ctypes.c_int]
@@ -123,9 +135,9 @@ def check(code: int) -> int:
     return code
 
 
-def oz_params(guard_bits=0, slices=0, cut_level=0, kernel="auto") -> OzParams:
+def oz_params(guard_bits=0, slices=0, cut_level=0, kernel="auto", max_group=0) -> OzParams:
     return OzParams(int(guard_bits), int(slices), int(cut_level), KERNELS[kernel] if isinstance(kernel, str)
-                    else int(kernel))
+                    else int(kernel), int(max_group))
 
 
 def exported_symbols():

@@ -3,6 +3,7 @@
 // caller's stream.  See include/mpcgemm.h for the contract.
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -101,8 +102,10 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   const int Q = (prm && prm->cut_level > 0) ? prm->cut_level - 1 : s - 1;
   if (Q > 2 * s) return MPC_EINVAL;
   const int64_t kk = k > 0 ? k : 1;
-  const int gmax = (int)(((int64_t)INT32_MAX) / (kk << kProdLog2));
+  int gmax = (int)(((int64_t)INT32_MAX) / (kk << kProdLog2));
   if (gmax < 1) return MPC_EINVAL;
+  if (prm && prm->max_group < 0) return MPC_EINVAL;
+  if (prm && prm->max_group > 0 && prm->max_group < gmax) gmax = prm->max_group;
   P.s = s;
   P.Q = Q;
   P.gmax = gmax;
@@ -215,6 +218,162 @@ OutView out_of(mpc_mat *X) {
   return v;
 }
 
+
+// ---------------------------------------------------------------- one call, in stages
+
+struct Call {
+  Plan pl;
+  int64_t m, n, k;
+  int32_t p;
+  bool empty;
+  MatView A, B;
+  OutView C;
+  char *ws;
+  int32_t *status, *E, *F, *lossyA, *lossyB;
+  int64_t *fallback;
+};
+
+int call_setup(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_mat *A, const mpc_mat *B, mpc_mat *C,
+               int method, int algo, const mpc_oz_params *params, void *workspace, size_t ws_bytes, Call *c) {
+  int rc = make_plan(m, n, k, p_bits, method, algo, params, &c->pl);
+  if (rc != MPC_OK) return rc;
+  if (!mat_ok(A, m, k) || !mat_ok(B, k, n) || !mat_ok(C, m, n)) return MPC_EINVAL;
+  c->m = m;
+  c->n = n;
+  c->k = k;
+  c->p = p_bits;
+  c->empty = (m == 0 || n == 0);
+  if (c->empty) return MPC_OK;
+  if (!workspace || ((uintptr_t)workspace & 255)) return MPC_EINVAL;
+  if (ws_bytes < c->pl.pub.ws_bytes) return MPC_ENOSPC;
+  const mpc_plan &P = c->pl.pub;
+  c->ws = (char *)workspace;
+  c->status = (int32_t *)(c->ws + P.off_status);
+  c->E = (int32_t *)(c->ws + P.off_rowexp);
+  c->F = (int32_t *)(c->ws + P.off_colexp);
+  c->lossyA = (int32_t *)(c->ws + P.off_rowlossy);
+  c->lossyB = (int32_t *)(c->ws + P.off_collossy);
+  c->fallback = (int64_t *)(c->ws + P.off_fallback);
+  c->A = view_of(A);
+  c->B = view_of(B);
+  c->C = out_of(C);
+  return MPC_OK;
+}
+
+// exponents, then the split (digits + group tables) or the plain fixed-point operands
+void call_pre(Call &c, cudaStream_t st) {
+  const mpc_plan &P = c.pl.pub;
+  const int L = P.limbs;
+  launch_init(c.status, c.E, c.m, c.F, c.n, c.lossyA, c.lossyB, st);
+  if (c.k == 0) {
+    launch_zero_output(c.C, c.m, c.n, L, st);
+    return;
+  }
+  launch_line_max(c.A, c.B, c.m, c.n, c.k, L, c.E, c.F, st);
+  if (P.algo == MPC_PLAIN) {
+    const int Lp = L + 1;
+    launch_plain_fix(c.A, 0, c.m, c.k, L, Lp, c.E, c.lossyA, (uint64_t *)(c.ws + P.off_fix_a),
+                     (uint8_t *)(c.ws + P.off_digits_a), st);
+    launch_plain_fix(c.B, 1, c.n, c.k, L, Lp, c.F, c.lossyB, (uint64_t *)(c.ws + P.off_fix_b),
+                     (uint8_t *)(c.ws + P.off_digits_b), st);
+  } else {
+    const int want_sum = P.method == MPC_3M;
+    launch_group_table(c.pl.prod, P.n_products, P.Q, P.gmax, (GroupEntry *)(c.ws + P.off_group_table),
+                       (int32_t *)(c.ws + P.off_group_order), st);
+    launch_oz_digits(c.A, 0, c.m, c.k, P.kpad, L, P.s, want_sum, c.E, c.lossyA,
+                     (__nv_bfloat16 *)(c.ws + P.off_digits_a), st);
+    launch_oz_digits(c.B, 1, c.n, c.k, P.kpad, L, P.s, want_sum, c.F, c.lossyB,
+                     (__nv_bfloat16 *)(c.ws + P.off_digits_b), st);
+  }
+}
+
+SliceGemmArgs slice_args(const Call &c) {
+  const mpc_plan &P = c.pl.pub;
+  SliceGemmArgs sa{};
+  sa.dA = (const __nv_bfloat16 *)(c.ws + P.off_digits_a);
+  sa.dB = (const __nv_bfloat16 *)(c.ws + P.off_digits_b);
+  sa.m = c.m;
+  sa.n = c.n;
+  sa.kpad = P.kpad;
+  sa.groups = (const GroupEntry *)(c.ws + P.off_group_table);
+  sa.n_entries = P.n_groups_total;
+  for (int x = 0; x < 4; ++x) sa.prod[x] = c.pl.prod[x];
+  sa.out = (int32_t *)(c.ws + P.off_groups);
+  sa.status = c.status;
+  return sa;
+}
+
+void call_gemm_plain(Call &c, cudaStream_t st) {
+  const mpc_plan &P = c.pl.pub;
+  PlainArgs pa{};
+  pa.fixA = (const uint64_t *)(c.ws + P.off_fix_a);
+  pa.fixB = (const uint64_t *)(c.ws + P.off_fix_b);
+  pa.sgnA = (const uint8_t *)(c.ws + P.off_digits_a);
+  pa.sgnB = (const uint8_t *)(c.ws + P.off_digits_b);
+  pa.m = c.m;
+  pa.n = c.n;
+  pa.k = c.k;
+  pa.p = c.p;
+  pa.L = P.limbs;
+  pa.Lp = P.limbs + 1;
+  pa.E = c.E;
+  pa.F = c.F;
+  pa.lossyA = c.lossyA;
+  pa.lossyB = c.lossyB;
+  pa.fallback = c.fallback;
+  pa.fallback_cap = (int64_t)P.fallback_capacity;
+  pa.status = c.status;
+  launch_plain_gemm(pa, c.C, st);
+}
+
+void call_accum(Call &c, cudaStream_t st) {
+  const mpc_plan &P = c.pl.pub;
+  if (P.algo != MPC_OZAKI) return;   // the plain GEMM rounds in its own epilogue
+  AccumArgs aa{};
+  aa.planes = (const int32_t *)(c.ws + P.off_groups);
+  aa.groups = (const GroupEntry *)(c.ws + P.off_group_table);
+  aa.order = (const int32_t *)(c.ws + P.off_group_order);
+  aa.n_entries = P.n_groups_total;
+  aa.m = c.m;
+  aa.n = c.n;
+  aa.k = c.k;
+  aa.p = c.p;
+  aa.L = P.limbs;
+  aa.Q = P.Q;
+  aa.nslot = P.acc_slots;
+  aa.method = P.method;
+  aa.E = c.E;
+  aa.F = c.F;
+  aa.lossyA = c.lossyA;
+  aa.lossyB = c.lossyB;
+  aa.bound_shift = P.bound_shift;
+  for (int x = 0; x < 2; ++x) {
+    aa.bound_drop[x] = P.bound_drop[x];
+    aa.bound_lossy_a[x] = P.bound_lossy_a[x];
+    aa.bound_lossy_b[x] = P.bound_lossy_b[x];
+  }
+  aa.fallback = c.fallback;
+  aa.fallback_cap = (int64_t)P.fallback_capacity;
+  aa.status = c.status;
+  launch_oz_accum(aa, c.C, st);
+}
+
+void call_fallback(Call &c, cudaStream_t st) {
+  const mpc_plan &P = c.pl.pub;
+  FallbackArgs fa{};
+  fa.m = c.m;
+  fa.n = c.n;
+  fa.k = c.k;
+  fa.p = c.p;
+  fa.L = P.limbs;
+  fa.list = c.fallback;
+  fa.cap = (int64_t)P.fallback_capacity;
+  fa.scratch = (uint64_t *)(c.ws + P.off_fb_scratch);
+  fa.scratch_limbs = (int)P.fb_scratch_limbs;
+  fa.status = c.status;
+  launch_fallback(fa, c.A, c.B, c.C, kFallbackBlocks, kFallbackThreads, st);
+}
+
 }  // namespace
 }  // namespace mpc
 
@@ -240,135 +399,104 @@ size_t mpcgemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t p_bits, i
 int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_mat *A, const mpc_mat *B,
                      mpc_mat *C, int method, int algo, const mpc_oz_params *params, const mpc_stage_events *events,
                      void *workspace, size_t ws_bytes, void *stream) {
-  Plan pl;
-  int rc = make_plan(m, n, k, p_bits, method, algo, params, &pl);
-  if (rc != MPC_OK) return rc;
-  if (!mat_ok(A, m, k) || !mat_ok(B, k, n) || !mat_ok(C, m, n)) return MPC_EINVAL;
-  if (m == 0 || n == 0) return MPC_OK;
-  if (!workspace || ((uintptr_t)workspace & 255)) return MPC_EINVAL;
-  if (ws_bytes < pl.pub.ws_bytes) return MPC_ENOSPC;
+  Call c;
+  int rc = call_setup(m, n, k, p_bits, A, B, C, method, algo, params, workspace, ws_bytes, &c);
+  if (rc != MPC_OK || c.empty) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  const mpc_plan &P = pl.pub;
-  const int L = P.limbs;
-  char *ws = (char *)workspace;
-  int32_t *status = (int32_t *)(ws + P.off_status);
-  int32_t *E = (int32_t *)(ws + P.off_rowexp), *F = (int32_t *)(ws + P.off_colexp);
-  int32_t *lossyA = (int32_t *)(ws + P.off_rowlossy), *lossyB = (int32_t *)(ws + P.off_collossy);
-  int64_t *fallback = (int64_t *)(ws + P.off_fallback);
-  OutView Cv = out_of(C);
   cudaGetLastError();   // clear a stale error of an earlier, unrelated call
   auto mark = [&](int x) {
     if (events && events->ev[x]) cudaEventRecord((cudaEvent_t)events->ev[x], st);
   };
   mark(0);
-  launch_init(status, E, m, F, n, lossyA, lossyB, st);
-  if (k == 0) {
-    launch_zero_output(Cv, m, n, L, st);
-    for (int x = 1; x <= 4; ++x) mark(x);
-    return cuda_code(cudaGetLastError());
-  }
-  MatView Av = view_of(A), Bv = view_of(B);
-  launch_line_max(Av, Bv, m, n, k, L, E, F, st);
-  FallbackArgs fa{};
-  fa.m = m;
-  fa.n = n;
-  fa.k = k;
-  fa.p = p_bits;
-  fa.L = L;
-  fa.list = fallback;
-  fa.cap = (int64_t)P.fallback_capacity;
-  fa.scratch = (uint64_t *)(ws + P.off_fb_scratch);
-  fa.scratch_limbs = (int)P.fb_scratch_limbs;
-  fa.status = status;
-  if (algo == MPC_PLAIN) {
-    const int Lp = L + 1;
-    uint64_t *fixA = (uint64_t *)(ws + P.off_fix_a), *fixB = (uint64_t *)(ws + P.off_fix_b);
-    uint8_t *sgA = (uint8_t *)(ws + P.off_digits_a), *sgB = (uint8_t *)(ws + P.off_digits_b);
-    launch_plain_fix(Av, 0, m, k, L, Lp, E, lossyA, fixA, sgA, st);
-    launch_plain_fix(Bv, 1, n, k, L, Lp, F, lossyB, fixB, sgB, st);
-    mark(1);
-    PlainArgs pa{};
-    pa.fixA = fixA;
-    pa.fixB = fixB;
-    pa.sgnA = sgA;
-    pa.sgnB = sgB;
-    pa.m = m;
-    pa.n = n;
-    pa.k = k;
-    pa.p = p_bits;
-    pa.L = L;
-    pa.Lp = Lp;
-    pa.E = E;
-    pa.F = F;
-    pa.lossyA = lossyA;
-    pa.lossyB = lossyB;
-    pa.fallback = fallback;
-    pa.fallback_cap = (int64_t)P.fallback_capacity;
-    pa.status = status;
-    launch_plain_gemm(pa, Cv, st);
-    mark(2);
-    mark(3);
-  } else {
-    __nv_bfloat16 *dA = (__nv_bfloat16 *)(ws + P.off_digits_a), *dB = (__nv_bfloat16 *)(ws + P.off_digits_b);
-    GroupEntry *table = (GroupEntry *)(ws + P.off_group_table);
-    int32_t *order = (int32_t *)(ws + P.off_group_order);
-    int32_t *planes = (int32_t *)(ws + P.off_groups);
-    const int want_sum = method == MPC_3M;
-    launch_group_table(pl.prod, P.n_products, P.Q, P.gmax, table, order, st);
-    launch_oz_digits(Av, 0, m, k, P.kpad, L, P.s, want_sum, E, lossyA, dA, st);
-    launch_oz_digits(Bv, 1, n, k, P.kpad, L, P.s, want_sum, F, lossyB, dB, st);
-    mark(1);
-    SliceGemmArgs sa{};
-    sa.dA = dA;
-    sa.dB = dB;
-    sa.m = m;
-    sa.n = n;
-    sa.kpad = P.kpad;
-    sa.groups = table;
-    sa.n_entries = P.n_groups_total;
-    for (int x = 0; x < 4; ++x) sa.prod[x] = pl.prod[x];
-    sa.out = planes;
-    sa.status = status;
-    if (pl.kernel == MPC_KERNEL_MMA_SYNC) {
-      launch_slicegemm_mma(sa, st);
-    } else {   // auto: the tcgen05 kernel, in CTA pairs when there are at least two row tiles
-      const int pair = pl.kernel == MPC_KERNEL_TCGEN05_PAIR || (pl.kernel == MPC_KERNEL_AUTO && m > 128);
-      const cudaError_t e = launch_slicegemm_tc(sa, st, pair ? 2 : 1);
-      if (e == cudaErrorNotSupported && pl.kernel == MPC_KERNEL_AUTO) launch_slicegemm_mma(sa, st);
-      else if (e != cudaSuccess) return e == cudaErrorNotSupported ? MPC_ENOTSUP : cuda_code(e);
+  call_pre(c, st);
+  mark(1);
+  if (c.k > 0) {
+    if (c.pl.pub.algo == MPC_PLAIN) {
+      call_gemm_plain(c, st);
+    } else {
+      SliceGemmArgs sa = slice_args(c);
+      if (c.pl.kernel == MPC_KERNEL_MMA_SYNC) {
+        launch_slicegemm_mma(sa, st);
+      } else {   // auto: the tcgen05 kernel, in CTA pairs when there are at least two row tiles
+        const int pair = c.pl.kernel == MPC_KERNEL_TCGEN05_PAIR || (c.pl.kernel == MPC_KERNEL_AUTO && c.m > 128);
+        const cudaError_t e = launch_slicegemm_tc(sa, st, pair ? 2 : 1);
+        if (e == cudaErrorNotSupported && c.pl.kernel == MPC_KERNEL_AUTO) launch_slicegemm_mma(sa, st);
+        else if (e != cudaSuccess) return e == cudaErrorNotSupported ? MPC_ENOTSUP : cuda_code(e);
+      }
     }
-    mark(2);
-    AccumArgs aa{};
-    aa.planes = planes;
-    aa.groups = table;
-    aa.order = order;
-    aa.n_entries = P.n_groups_total;
-    aa.m = m;
-    aa.n = n;
-    aa.k = k;
-    aa.p = p_bits;
-    aa.L = L;
-    aa.Q = P.Q;
-    aa.nslot = P.acc_slots;
-    aa.method = method;
-    aa.E = E;
-    aa.F = F;
-    aa.lossyA = lossyA;
-    aa.lossyB = lossyB;
-    aa.bound_shift = P.bound_shift;
-    for (int c = 0; c < 2; ++c) {
-      aa.bound_drop[c] = P.bound_drop[c];
-      aa.bound_lossy_a[c] = P.bound_lossy_a[c];
-      aa.bound_lossy_b[c] = P.bound_lossy_b[c];
-    }
-    aa.fallback = fallback;
-    aa.fallback_cap = (int64_t)P.fallback_capacity;
-    aa.status = status;
-    launch_oz_accum(aa, Cv, st);
-    mark(3);
   }
-  launch_fallback(fa, Av, Bv, Cv, kFallbackBlocks, kFallbackThreads, st);
+  mark(2);
+  if (c.k > 0) call_accum(c, st);
+  mark(3);
+  if (c.k > 0) call_fallback(c, st);
   mark(4);
+  return cuda_code(cudaGetLastError());
+}
+
+int mpcgemm_batched_workspace(int count, const mpc_problem *probs, const mpc_oz_params *params, uint64_t *offsets,
+                              size_t *total) {
+  if (count < 0 || (count > 0 && !probs) || !total) return MPC_EINVAL;
+  uint64_t off = 0;
+  for (int x = 0; x < count; ++x) {
+    Plan pl;
+    const mpc_problem &q = probs[x];
+    const int rc = make_plan(q.m, q.n, q.k, q.p_bits, q.method, q.algo, params, &pl);
+    if (rc != MPC_OK) return rc;
+    if (offsets) offsets[x] = off;
+    off = align256(off + pl.pub.ws_bytes);
+  }
+  *total = (size_t)off;
+  return MPC_OK;
+}
+
+int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *params, void *workspace,
+                    size_t ws_bytes, void *stream) {
+  if (count < 0 || (count > 0 && !probs)) return MPC_EINVAL;
+  if (count == 0) return MPC_OK;
+  thread_local std::vector<Call> calls;   // reused: no host allocation once it has grown
+  if (calls.size() < (size_t)count) calls.resize((size_t)count);
+  uint64_t off = 0;
+  for (int x = 0; x < count; ++x) {   // plan and check everything before any launch
+    const mpc_problem &q = probs[x];
+    if (!workspace || ws_bytes < off) return MPC_ENOSPC;
+    const int rc = call_setup(q.m, q.n, q.k, q.p_bits, q.A, q.B, q.C, q.method, q.algo, params,
+                              (char *)workspace + off, ws_bytes - (size_t)off, &calls[x]);
+    if (rc != MPC_OK) return rc;
+    off = align256(off + calls[x].pl.pub.ws_bytes);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaGetLastError();
+  for (int x = 0; x < count; ++x)
+    if (!calls[x].empty) call_pre(calls[x], st);
+  thread_local std::vector<SliceGemmArgs> slices;
+  slices.clear();
+  bool any_tall = false;
+  const int kernel = params ? params->kernel : MPC_KERNEL_AUTO;
+  for (int x = 0; x < count; ++x) {
+    Call &c = calls[x];
+    if (c.empty || c.k == 0) continue;
+    if (c.pl.pub.algo == MPC_PLAIN) {
+      call_gemm_plain(c, st);
+    } else if (kernel == MPC_KERNEL_MMA_SYNC) {
+      launch_slicegemm_mma(slice_args(c), st);
+    } else {
+      slices.push_back(slice_args(c));
+      any_tall |= c.m > 128;
+    }
+  }
+  if (!slices.empty()) {   // one persistent launch for every Ozaki problem (48 per launch)
+    const int pair = kernel == MPC_KERNEL_TCGEN05_PAIR || (kernel == MPC_KERNEL_AUTO && any_tall);
+    const cudaError_t e = launch_slicegemm_tc_batch(slices.data(), (int)slices.size(), st, pair ? 2 : 1);
+    if (e == cudaErrorNotSupported && kernel == MPC_KERNEL_AUTO) {
+      for (const SliceGemmArgs &sa : slices) launch_slicegemm_mma(sa, st);
+    } else if (e != cudaSuccess) {
+      return e == cudaErrorNotSupported ? MPC_ENOTSUP : cuda_code(e);
+    }
+  }
+  for (int x = 0; x < count; ++x)
+    if (!calls[x].empty && calls[x].k > 0) call_accum(calls[x], st);
+  for (int x = 0; x < count; ++x)
+    if (!calls[x].empty && calls[x].k > 0) call_fallback(calls[x], st);
   return cuda_code(cudaGetLastError());
 }
 

@@ -67,6 +67,7 @@ void launch_group_table(const ProductDesc *prods, int n_products, int Q, int gma
                         int32_t *order, cudaStream_t st);
 void launch_slicegemm_mma(const SliceGemmArgs &a, cudaStream_t st);
 cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int cluster);
+cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, int cluster);
 void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st);
 void launch_fallback(const FallbackArgs &f, const MatView &A, const MatView &B, const OutView &C, int blocks,
                      int threads, cudaStream_t st);

@@ -28,6 +28,9 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -42,19 +45,34 @@ constexpr int NUM_THREADS = 320, EPI_WARPS = 8;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long kTimeoutCycles = 4000000000ll;   // ~2 s at 2 GHz
 constexpr int URING = 4;                               // unit-index ring slots
+constexpr int kMaxBatch = 48;                          // problems per launch (kernel parameter space)
 constexpr int kStUnitCounter = 8;                      // status word used as the unit counter
 static_assert(kChunk % BK == 0, "chunk must be whole k-blocks");
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
 
-struct TcParams {
+// One launch serves a set of up to kMaxBatch independent problems (a single
+// GEMM is a set of one): their units are numbered consecutively and each
+// problem brings its own tensor maps, group table and output planes.
+struct TcProblem {
   int64_t m, n;
+  int64_t unit0;       // first unit of this problem
   int kbpp;            // k-blocks per pair (kpad / 64)
-  int n_entries, tiles_m, tiles_n;
-  int64_t units;
+  int tiles_m, tiles_n, pad_;
   const GroupEntry *groups;
-  ProductDesc prod[4];
   int32_t *out;
+  ProductDesc prod[4];
+};
+
+struct TcMaps {
+  CUtensorMap a[kMaxBatch];
+  CUtensorMap b[kMaxBatch];
+};
+
+struct TcParams {
+  int count;
+  int64_t units;
   int32_t *status;
+  TcProblem prob[kMaxBatch];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -231,21 +249,27 @@ struct Unit {
   ProductDesc pd;
   int tm, tn, nkb;
   int e;
+  int prob;
 };
 
 // unit u -> (group, tile); with CL = 2 a unit is a pair of row tiles, CTA `rank` takes one
 template <int CL>
 __device__ __forceinline__ Unit decode(const TcParams &P, int64_t u, uint32_t rank) {
   Unit x;
-  const int tiles_mu = (P.tiles_m + CL - 1) / CL;
-  const int tiles = tiles_mu * P.tiles_n;
-  x.e = (int)(u / tiles);
-  const int t = (int)(u % tiles);
-  x.tm = (t / P.tiles_n) * CL + (int)rank;
-  x.tn = t % P.tiles_n;
-  x.g = P.groups[x.e];
-  x.pd = P.prod[x.g.prod];
-  x.nkb = x.g.count * P.kbpp;
+  int pi = 0;
+  while (pi + 1 < P.count && P.prob[pi + 1].unit0 <= u) ++pi;
+  const TcProblem &q = P.prob[pi];
+  const int64_t r = u - q.unit0;
+  const int tiles_mu = (q.tiles_m + CL - 1) / CL;
+  const int tiles = tiles_mu * q.tiles_n;
+  x.prob = pi;
+  x.e = (int)(r / tiles);
+  const int t = (int)(r % tiles);
+  x.tm = (t / q.tiles_n) * CL + (int)rank;
+  x.tn = t % q.tiles_n;
+  x.g = q.groups[x.e];
+  x.pd = q.prod[x.g.prod];
+  x.nkb = x.g.count * q.kbpp;
   return x;
 }
 
@@ -260,7 +284,7 @@ __device__ __forceinline__ Unit decode(const TcParams &P, int64_t u, uint32_t ra
 // memory.
 template <int CL>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-    k_slicegemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams P) {
+    k_slicegemm_tc(const __grid_constant__ TcMaps maps, const __grid_constant__ TcParams P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   uint8_t *sA = smem;
@@ -292,8 +316,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    for (int q = 0; q < P.count; ++q) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[q])) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[q])) : "memory");
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -336,19 +362,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (++slot == URING) { slot = 0; uphase ^= 1; }
         if (u < 0) break;
         const Unit x = decode<CL>(P, u, rank);
+        const int kbpp = P.prob[x.prob].kbpp;
+        const CUtensorMap *tmA = &maps.a[x.prob], *tmB = &maps.b[x.prob];
         for (int kb = 0; kb < x.nkb; ++kb) {
-          const int pi = kb / P.kbpp;
-          const int k0 = (kb - pi * P.kbpp) * BK;
+          const int pi = kb / kbpp;
+          const int k0 = (kb - pi * kbpp) * BK;
           const int t = x.g.t0 + pi, uu = x.g.q - t;
           const int planeA = x.pd.a_plane0 + t - x.pd.a_pos0;
           const int planeB = x.pd.b_plane0 + uu - x.pd.b_pos0;
           if (!mbar_wait(&empty[stage], phase ^ 1, abort, P.status)) { ok = false; break; }
           mbar_expect_tx(&full[stage], STAGE_BYTES);
-          tma_load_3d(sA + stage * A_BYTES, &tmA, k0, x.tm * BM, planeA, &full[stage]);
+          tma_load_3d(sA + stage * A_BYTES, tmA, k0, x.tm * BM, planeA, &full[stage]);
           if (CL == 1) {
-            tma_load_3d(sB + stage * B_BYTES, &tmB, k0, x.tn * BN, planeB, &full[stage]);
+            tma_load_3d(sB + stage * B_BYTES, tmB, k0, x.tn * BN, planeB, &full[stage]);
           } else {   // my half of the B tile, into the same place in both CTAs
-            tma_load_3d_mc(sB + stage * B_BYTES + rank * (B_BYTES / 2), &tmB, k0, x.tn * BN + (int)rank * (BN / 2),
+            tma_load_3d_mc(sB + stage * B_BYTES + rank * (B_BYTES / 2), tmB, k0, x.tn * BN + (int)rank * (BN / 2),
                            planeB, &full[stage], (uint16_t)0x3);
           }
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
@@ -440,18 +468,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
       if (!ok) break;
       // store the int32 tile rows of this thread
+      const int64_t pm = P.prob[x.prob].m, pn = P.prob[x.prob].n;
       const int64_t row = (int64_t)x.tm * BM + row_in_tile;
       const int64_t col0 = (int64_t)x.tn * BN + half * 128;
-      if (row < P.m) {
-        int32_t *dst = P.out + (int64_t)x.e * P.m * P.n + row * P.n + col0;
-        if (col0 + 128 <= P.n && ((P.n & 3) == 0)) {
+      if (row < pm) {
+        int32_t *dst = P.prob[x.prob].out + (int64_t)x.e * pm * pn + row * pn + col0;
+        if (col0 + 128 <= pn && ((pn & 3) == 0)) {
 #pragma unroll
           for (int v = 0; v < 32; ++v)
             reinterpret_cast<int4 *>(dst)[v] = make_int4(acc[4 * v], acc[4 * v + 1], acc[4 * v + 2], acc[4 * v + 3]);
         } else {
 #pragma unroll
           for (int v = 0; v < 128; ++v)
-            if (col0 + v < P.n) dst[v] = acc[v];
+            if (col0 + v < pn) dst[v] = acc[v];
         }
       }
 #pragma unroll
@@ -510,35 +539,39 @@ int num_sms() {
 
 }  // namespace
 
-cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int cluster) {
-  int dev = 0, major = 0, minor = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  if (major != 10 || minor != 3) return cudaErrorNotSupported;   // built for sm_103a only
-  if (cluster != 1 && cluster != 2) return cudaErrorInvalidValue;
-  int planes_a = 0, planes_b = 0;
-  for (int x = 0; x < 4; ++x) {
-    if (a.prod[x].a_plane0 + a.prod[x].a_npos > planes_a) planes_a = a.prod[x].a_plane0 + a.prod[x].a_npos;
-    if (a.prod[x].b_plane0 + a.prod[x].b_npos > planes_b) planes_b = a.prod[x].b_plane0 + a.prod[x].b_npos;
+// One persistent launch over the units of up to kMaxBatch problems (the unit
+// counter lives in the first problem's status block, zeroed by its init).
+static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t st, int cluster) {
+  static TcMaps maps;    // host staging of the kernel parameters (copied at launch)
+  static TcParams P;
+  std::memset(&P, 0, sizeof(P));
+  int64_t units = 0;
+  for (int q = 0; q < count; ++q) {
+    const SliceGemmArgs &a = list[q];
+    int planes_a = 0, planes_b = 0;
+    for (int x = 0; x < 4; ++x) {
+      if (a.prod[x].a_plane0 + a.prod[x].a_npos > planes_a) planes_a = a.prod[x].a_plane0 + a.prod[x].a_npos;
+      if (a.prod[x].b_plane0 + a.prod[x].b_npos > planes_b) planes_b = a.prod[x].b_plane0 + a.prod[x].b_npos;
+    }
+    if (!make_map(&maps.a[q], a.dA, a.m, a.kpad, planes_a, BM) ||
+        !make_map(&maps.b[q], a.dB, a.n, a.kpad, planes_b, cluster == 2 ? BN / 2 : BN))
+      return cudaErrorNotSupported;
+    TcProblem &t = P.prob[q];
+    t.m = a.m;
+    t.n = a.n;
+    t.kbpp = (int)(a.kpad / BK);
+    t.tiles_m = (int)((a.m + BM - 1) / BM);
+    t.tiles_n = (int)((a.n + BN - 1) / BN);
+    t.unit0 = units;
+    t.groups = a.groups;
+    t.out = a.out;
+    for (int x = 0; x < 4; ++x) t.prod[x] = a.prod[x];
+    units += (int64_t)a.n_entries * ((t.tiles_m + cluster - 1) / cluster) * t.tiles_n;
   }
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, a.dA, a.m, a.kpad, planes_a, BM) ||
-      !make_map(&mb, a.dB, a.n, a.kpad, planes_b, cluster == 2 ? BN / 2 : BN))
-    return cudaErrorNotSupported;
-  TcParams P{};
-  P.m = a.m;
-  P.n = a.n;
-  P.kbpp = (int)(a.kpad / BK);
-  P.n_entries = a.n_entries;
-  P.tiles_m = (int)((a.m + BM - 1) / BM);
-  P.tiles_n = (int)((a.n + BN - 1) / BN);
-  P.units = (int64_t)a.n_entries * ((P.tiles_m + cluster - 1) / cluster) * P.tiles_n;
-  P.groups = a.groups;
-  for (int x = 0; x < 4; ++x) P.prod[x] = a.prod[x];
-  P.out = a.out;
-  P.status = a.status;
-  if (P.units == 0) return cudaSuccess;
+  P.count = count;
+  P.units = units;
+  P.status = list[0].status;
+  if (units == 0) return cudaSuccess;
   static bool attr[3] = {false, false, false};
   auto kfn = cluster == 2 ? k_slicegemm_tc<2> : k_slicegemm_tc<1>;
   if (!attr[cluster]) {
@@ -560,14 +593,36 @@ cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int clu
     cfg.attrs = la;
     cfg.numAttrs = 1;
     cfg.gridDim = dim3((unsigned)ctas, 1, 1);
-    int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, kfn, &cfg) != cudaSuccess || clusters < 1) clusters = ctas / 2;
+    static int clusters = 0;      // queried once (also keeps the call free of queries under graph capture)
+    if (clusters == 0 && (cudaOccupancyMaxActiveClusters(&clusters, kfn, &cfg) != cudaSuccess || clusters < 1))
+      clusters = ctas / 2;
     ctas = 2 * clusters;
   }
-  const int64_t need = P.units * cluster;
+  const int64_t need = units * cluster;
   if (need < ctas) ctas = (int)need;
   cfg.gridDim = dim3((unsigned)ctas, 1, 1);
-  return cudaLaunchKernelEx(&cfg, kfn, ma, mb, P);
+  return cudaLaunchKernelEx(&cfg, kfn, maps, P);
+}
+
+cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, int cluster) {
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3) return cudaErrorNotSupported;   // built for sm_103a only
+  if (cluster != 1 && cluster != 2) return cudaErrorInvalidValue;
+  static std::mutex mu;            // the parameter staging below is shared
+  std::lock_guard<std::mutex> lock(mu);
+  for (int q0 = 0; q0 < count; q0 += kMaxBatch) {
+    const int c = count - q0 < kMaxBatch ? count - q0 : kMaxBatch;
+    const cudaError_t e = launch_set(list + q0, c, st, cluster);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int cluster) {
+  return launch_slicegemm_tc_batch(&a, 1, st, cluster);
 }
 
 }  // namespace mpc

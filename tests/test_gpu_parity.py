@@ -77,6 +77,24 @@ def test_config1_stage_parity(method):
     _check_against_o1(C, A, B, p)
 
 
+@pytest.mark.parametrize("kernel", ["auto", "tcgen05", "mma_sync"])
+def test_group_cap_stage_parity(kernel):
+    """Groups capped at 5 pairs: every group sum still equals O2's (same cap)."""
+    p = 256
+    A = si.random_matrix(130, 300, p, 341, "uniform_exp")
+    B = si.random_matrix(300, 140, p, 342, "uniform_exp")
+    params = dict(max_group=5, kernel=kernel)
+    C, ws, st = gu.run(A, B, p, "3m", "ozaki", params=params)
+    pl = gu.plan(A, B, p, "3m", params=params)
+    r = ozaki.ozaki_cgemm(A, B, p, "3m", max_group=5, fallback=lambda i, j: ((0, 0), (0, 0)))
+    G = gu.ws_groups(ws, pl, A.rows, B.cols)
+    ref = [Gr for pr in r.params.products for Gr in r.group_sums[pr]]
+    assert G.shape[0] == len(ref) and all(g.count <= 5 for pr in r.params.products for g in r.groups[pr])
+    for e, Gr in enumerate(ref):
+        assert np.array_equal(G[e], Gr), e
+    _check_against_o1(C, A, B, p)
+
+
 @pytest.mark.parametrize("method", ["4m", "3m"])
 def test_forced_fallbacks_stay_exact(method):
     """Two guard bits: many components fail certification and are recomputed exactly."""
