@@ -214,6 +214,24 @@ int mpcgemm_batched_workspace(int count, const mpc_problem *probs, const mpc_oz_
 int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *params,
                     void *workspace, size_t ws_bytes, void *stream);
 
+/*
+ * Complex linear solve A X = B by blocked right-looking LU with partial
+ * pivoting (Kouya, Sec. IV-C, Fig. 3: each block of `block` columns is
+ * factored, then A22 - L21 U12 is updated by the Ozaki complex GEMM with
+ * `method`; block = 1 is the paper's "Normal LU"), then forward and backward
+ * substitution (Sec. IV-C).  A (n x n) is overwritten by its factors (unit L
+ * below the diagonal, U on and above), ipiv[j] (device int32, n entries) gets
+ * the row swapped with row j, B (n x nrhs) is overwritten by X.  Every scalar
+ * result is computed exactly and rounded once to p bits (nearest-even); the
+ * pivot of column j is the first row maximising RN_p(|Re| + |Im|).
+ * Device status (mpcgemm_read_status on the workspace): erange as for the
+ * GEMM; `uncertified` = some exact window was truncated; word 5 (read it as
+ * an int32 at workspace + 20) = 1 + the first column whose pivot is zero.
+ */
+size_t mpcgesv_workspace_size(int64_t n, int32_t p_bits, int32_t block, int method);
+int mpcgesv(int64_t n, int32_t p_bits, mpc_mat *A, int32_t *ipiv, mpc_mat *B, int32_t block, int method,
+            void *workspace, size_t ws_bytes, void *stream);
+
 /* Bytes of workspace a call with these arguments needs (0 on bad arguments). */
 size_t mpcgemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t p_bits,
                               int method, int algo);

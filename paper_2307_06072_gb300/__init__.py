@@ -20,7 +20,7 @@ import numpy as np
 from . import _native
 from ._native import MPCError, check, lib, oz_params, strerror  # noqa: F401
 
-__all__ = ["DeviceMatrix", "mpcgemm", "mpcgemm_batched", "batched_workspace", "workspace_size", "plan",
+__all__ = ["DeviceMatrix", "mpcgemm", "mpcgemm_batched", "batched_workspace", "mpcgesv", "workspace_size", "plan",
            "read_status", "strerror", "version", "MPCError", "Workspace"]
 
 
@@ -224,6 +224,30 @@ def read_status(workspace: Workspace, stream=None, offset: int = 0) -> dict:
     return {"erange": st.erange, "fallback_entries": st.fallback_entries,
             "fallback_overflow": st.fallback_overflow, "uncertified": st.uncertified,
             "device_timeout": st.device_timeout}
+
+
+def mpcgesv(A: DeviceMatrix, B: DeviceMatrix, p: int, block: int = 128, method: str = "3m",
+            workspace: Workspace | None = None, stream=None):
+    """Solve A X = B in place (A <- LU factors, B <- X); returns (ipiv tensor, workspace)."""
+    torch = _torch()
+    n = A.rows
+    need = int(lib().mpcgesv_workspace_size(n, p, block, _native.METHODS[method]))
+    if need == 0 and n > 0:
+        raise MPCError(_native.MPC_EINVAL)
+    ws = workspace if workspace is not None else Workspace(A.sign.device)
+    t = ws.get(max(need, 256))
+    ipiv = torch.zeros(max(n, 1), dtype=torch.int32, device=A.sign.device)
+    sa, sb = A.struct(), B.struct()
+    check(lib().mpcgesv(n, p, ctypes.byref(sa), ipiv.data_ptr(), ctypes.byref(sb), block, _native.METHODS[method],
+                        t.data_ptr(), t.numel(), _stream_handle(stream)))
+    return ipiv[:n], ws
+
+
+def lu_singular_column(workspace: Workspace) -> int:
+    """1 + the first column whose pivot was zero (0 if none); synchronises."""
+    torch = _torch()
+    torch.cuda.synchronize()
+    return int(workspace.tensor[20:24].view(torch.int32).item())
 
 
 def version() -> int:

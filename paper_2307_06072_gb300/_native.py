@@ -22,7 +22,7 @@ KERNELS = {"auto": 0, "tcgen05": 1, "mma_sync": 2, "tcgen05_pair": 3}
 
 EXPORTED = ("mpcgemm", "mpcgemm_ex", "mpcgemm_profiled", "mpcgemm_workspace_size", "mpcgemm_plan",
             "mpcgemm_read_status", "mpcgemm_noalloc", "mpcgemm_batched", "mpcgemm_batched_workspace",
-            "mpcgemm_strerror", "mpcgemm_version")
+            "mpcgesv", "mpcgesv_workspace_size", "mpcgemm_strerror", "mpcgemm_version")
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -109,6 +109,10 @@ def lib():
         L.mpcgemm_batched.restype = ctypes.c_int
         L.mpcgemm_batched_workspace.argtypes = [ctypes.c_int, P, P, P, P]
         L.mpcgemm_batched_workspace.restype = ctypes.c_int
+        L.mpcgesv.argtypes = [I64, I32, P, P, P, I32, ctypes.c_int, P, ctypes.c_size_t, P]
+        L.mpcgesv.restype = ctypes.c_int
+        L.mpcgesv_workspace_size.argtypes = [I64, I32, I32, ctypes.c_int]
+        L.mpcgesv_workspace_size.restype = ctypes.c_size_t
         L.mpcgemm_noalloc.argtypes = [I64, I64, I64, I32, P, P, P, ctypes.c_int, ctypes.c_int, P]
         L.mpcgemm_noalloc.restype = ctypes.c_int
         L.mpcgemm_strerror.argtypes = [ctypes.c_int]

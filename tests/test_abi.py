@@ -24,7 +24,7 @@ def mp():
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mpcgemm\w*)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(mpcge(?:mm|sv)\w*)\s*\(", src)))
 
 
 def test_every_declared_symbol_is_exported(mp):
