@@ -120,6 +120,67 @@ def run_batched(mp, torch, dev, stream, steps: int, warmup: int):
                       "tcgen05 slice-GEMM launch for all problems)"}
 
 
+def run_lu(mp, torch, dev, n: int = 2048, p: int = 512, block: int = 128, method: str = "3m"):
+    """Config 4: A = U + n I, x = 1 + i, b = RN(A x) (by this library's GEMM), solve, error of x."""
+    from fractions import Fraction
+    A = si.shifted_diagonal_matrix(n, p, si.SEED_BASE + 4)
+    ones = np.zeros((2, n, 1), np.int64)
+    ones[:] = 1
+    X1 = si.from_integers(ones, p)
+    dA, dx = mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(X1, dev)
+    db = mp.DeviceMatrix.empty(n, 1, p, dev)
+    mp.mpcgemm(dA, dx, db, p, "4m", "ozaki")
+    torch.cuda.synchronize(dev)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    start.record(stream)
+    ipiv, ws = mp.mpcgesv(dA, db, p, block, method, stream=stream)
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    st = mp.read_status(ws)
+    s, e, l = db.to_host()
+    worst = Fraction(0)
+    for i in range(n):
+        for c in range(2):
+            Mv = 0
+            for j in range(l.shape[1] - 1, -1, -1):
+                Mv = (Mv << 64) | int(l[c, j, i, 0])
+            v = Fraction(-Mv if s[c, i, 0] else Mv) * Fraction(2) ** (int(e[c, i, 0]) - 64 * l.shape[1]) if Mv else 0
+            worst = max(worst, abs(v - 1))
+    rel = float(worst)   # |x_i - (1 + i)| per component relative to 1
+    return {"n": n, "p_bits": p, "block": block, "method": method, "seconds": start.elapsed_time(end) / 1e3,
+            "max_rel_err_component": rel, "rel_err_in_ulps_of_2^-p": rel * 2.0 ** p,
+            "singular": mp.lu_singular_column(ws), "status": st,
+            "note": "A = U + nI (U uniform [-1,1)), x = 1+i, b = RN(Ax) by this library's GEMM"}
+
+
+def run_serving(mp, torch, dev, seed: int = si.SEED_BASE + 5, count: int = 40):
+    """Mixed GEMM (config-3 shapes) and LU (n 128..256) requests with Poisson arrivals."""
+    from paper_2307_06072_gb300.serve import Request, Server
+    rng = np.random.default_rng(seed)
+    reqs, t = [], 0.0
+    for x in range(count):
+        t += float(rng.exponential(0.004))
+        if x % 6 == 5:
+            n, p = int(rng.choice([128, 256])), int(rng.choice([256, 512]))
+            A = si.shifted_diagonal_matrix(n, p, seed + 10 * x)
+            B = si.random_matrix(n, 1, p, seed + 10 * x + 1)
+            reqs.append(Request(x, "lu", t, mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(B, dev), p,
+                                block=64, work=8.0 * n ** 3 / 3))
+        else:
+            m, k, n = (int(v) for v in np.exp(rng.uniform(np.log(64), np.log(1024), 3)))
+            p = int(rng.choice([256, 512, 1024]))
+            A = si.random_matrix(m, k, p, seed + 10 * x)
+            B = si.random_matrix(k, n, p, seed + 10 * x + 1)
+            reqs.append(Request(x, "gemm", t, mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(B, dev), p,
+                                C=mp.DeviceMatrix.empty(m, n, p, dev), work=8.0 * m * n * k))
+    srv = Server(slots=4, hbm_budget=48 << 30, device=dev)
+    out = srv.run(reqs)
+    out["note"] = (f"{count} requests (every 6th an LU solve, n in {{128, 256}}), Poisson arrivals with a 4 ms "
+                   "mean gap, 4 stream slots, 48 GB budget; latency = completion - arrival")
+    return out
+
+
 def pair_count(s: int, Q: int, method: str) -> int:
     """Kept slice pairs over all real products (Alg. 2's triangle t + u <= Q)."""
     def tri(a0, na, b0, nb):
@@ -306,6 +367,9 @@ def run_ours(args):
         extras["ozaki_speedup_vs_plain"] = value / extras["plain_4m"]["value"]
         if not args.no_batched:
             extras["batched_c3"] = run_batched(mp, torch, dev, stream, 3, 3)
+        if not args.no_lu:
+            extras["lu_c4"] = run_lu(mp, torch, dev)
+            extras["serving"] = run_serving(mp, torch, dev)
 
     # roofline of the dominant kernel (the slice GEMM): algorithmic MMA flops / its event time
     pairs = pair_count(pl["s"], pl["Q"], method)
@@ -476,6 +540,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD], default="c2_2048_p1024")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched side measurement")
+    ap.add_argument("--no-lu", action="store_true", help="skip the LU and serving side measurements")
     ap.add_argument("--method", choices=["3m", "4m"], default="3m")
     ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_pair", "mma_sync"], default="auto",
                     help="slice-GEMM kernel")

@@ -187,6 +187,31 @@ def identity_matrix(n: int, p: int) -> MPCMatrix:
     return from_integers(v, p)
 
 
+def shifted_diagonal_matrix(n: int, p: int, seed: int) -> MPCMatrix:
+    """A = U + n I with U uniform on [-1, 1) per component (the LU workload).
+
+    Off-diagonal entries are drawn as in ``random_matrix``; the real diagonal
+    is n + u with u uniform on the grid of spacing 2**-(p - 1 - bitlen(n)),
+    so that n + u is exactly a p-bit number and no rounding is needed.
+    """
+    import random as _random
+    A = random_matrix(n, n, p, seed, "uniform")
+    rng = _random.Random(seed + 1)
+    L = limbs_for(p)
+    nb = int(n).bit_length()
+    frac_bits = p - 1 - nb
+    for i in range(n):
+        u = rng.getrandbits(frac_bits + 1) - (1 << frac_bits)      # u * 2^-frac_bits in [-1, 1)
+        v = (n << frac_bits) + u                                     # value * 2^frac_bits, > 0
+        bl = v.bit_length()
+        M = v << (64 * L - bl)
+        A.sign[0, i, i] = 0
+        A.exp[0, i, i] = bl - frac_bits
+        for j in range(L):
+            A.limb[0, j, i, i] = (M >> (64 * j)) & 0xFFFFFFFFFFFFFFFF
+    return A
+
+
 def config_inputs(name: str):
     """The seeded workloads of the benchmark configurations.
 
