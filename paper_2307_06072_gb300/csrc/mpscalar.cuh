@@ -8,7 +8,8 @@
 //     4m_way_base per component);
 //   * mp_cdiv_round: a component of the complex quotient a / d, i.e.
 //     (a_re d_re + a_im d_im) / |d|^2 or (a_im d_re - a_re d_im) / |d|^2,
-//     from exact numerator and denominator by binary long division.
+//     from exact numerator and denominator by long division on 32-bit
+//     digits (Knuth's Algorithm D).
 // If a term lies more than the window below the largest one, its low bits
 // are dropped and `truncated` is reported (the caller records it).
 #pragma once
@@ -173,16 +174,68 @@ __device__ inline bool mp_sum_round(const Term *t, int nt, int p, int L, MPOut o
   return round_store(mag, 2 * nw, N, neg, lsb, p, L, o.s, o.e, o.limb, o.stride);
 }
 
-// compare magnitudes a, b (n limbs each): -1, 0, 1
-__device__ __forceinline__ int limbs_cmp(const uint64_t *a, const uint64_t *b, int n) {
-  for (int i = n - 1; i >= 0; --i)
-    if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
-  return 0;
+// Quotient and remainder of unsigned 32-bit-digit integers (Knuth, TAOCP vol. 2,
+// Sec. 4.3.1, Algorithm D): u[0..m) / v[0..n), v[n-1] != 0, m >= n.  q gets
+// m - n + 1 digits; returns true iff the remainder is nonzero.  u is clobbered.
+__device__ inline bool divmod_digits(uint32_t *u, int m, const uint32_t *v, int n, uint32_t *q) {
+  if (n == 1) {
+    uint64_t r = 0;
+    for (int i = m - 1; i >= 0; --i) {
+      const uint64_t cur = (r << 32) | u[i];
+      q[i] = (uint32_t)(cur / v[0]);
+      r = cur - (uint64_t)q[i] * v[0];
+    }
+    return r != 0;
+  }
+  constexpr int kMaxV = 80;
+  uint32_t vn[kMaxV];
+  const int s = __clz(v[n - 1]);     // normalise: top digit of the divisor gets its high bit set
+  for (int i = n - 1; i > 0; --i) vn[i] = (v[i] << s) | (s ? (uint32_t)((uint64_t)v[i - 1] >> (32 - s)) : 0u);
+  vn[0] = v[0] << s;
+  // un = u << s, one digit longer
+  uint32_t top = s ? (uint32_t)((uint64_t)u[m - 1] >> (32 - s)) : 0u;
+  for (int i = m - 1; i > 0; --i) u[i] = (u[i] << s) | (s ? (uint32_t)((uint64_t)u[i - 1] >> (32 - s)) : 0u);
+  u[0] = u[0] << s;
+  u[m] = top;
+  for (int j = m - n; j >= 0; --j) {
+    const uint64_t num2 = ((uint64_t)u[j + n] << 32) | u[j + n - 1];
+    uint64_t qhat = num2 / vn[n - 1];
+    uint64_t rhat = num2 - qhat * vn[n - 1];
+    while (qhat >= (1ull << 32) || qhat * vn[n - 2] > ((rhat << 32) | u[j + n - 2])) {
+      --qhat;
+      rhat += vn[n - 1];
+      if (rhat >= (1ull << 32)) break;
+    }
+    int64_t borrow = 0;   // multiply and subtract
+    for (int i = 0; i < n; ++i) {
+      const uint64_t prod = qhat * vn[i];
+      const int64_t t = (int64_t)u[i + j] - borrow - (int64_t)(prod & 0xFFFFFFFFull);
+      u[i + j] = (uint32_t)t;
+      borrow = (int64_t)(prod >> 32) - (t >> 32);
+    }
+    const int64_t t = (int64_t)u[j + n] - borrow;
+    u[j + n] = (uint32_t)t;
+    if (t < 0) {   // qhat was one too large: add the divisor back
+      --qhat;
+      uint64_t carry = 0;
+      for (int i = 0; i < n; ++i) {
+        const uint64_t s2 = (uint64_t)u[i + j] + vn[i] + carry;
+        u[i + j] = (uint32_t)s2;
+        carry = s2 >> 32;
+      }
+      u[j + n] += (uint32_t)carry;
+    }
+    q[j] = (uint32_t)qhat;
+  }
+  bool rem = false;
+  for (int i = 0; i < n; ++i) rem |= u[i] != 0;
+  return rem;
 }
 
 // RN_p of (num / den) where num, den are exact magnitudes (bit 0 worth 2^lsb_n, 2^lsb_d).
-// Restoring binary long division yields >= p + 2 quotient bits; the remainder
-// gives the sticky bit, appended below them, so one RNE rounding is exact.
+// Q = floor(num 2^sh / den) has p + 3 or p + 4 bits; the remainder (and any
+// numerator bits shifted out) gives a sticky bit appended below Q, so one RNE
+// rounding of 2Q + sticky is the correct rounding of the quotient.
 __device__ inline bool mp_div_round(const uint64_t *num, int nwn, int64_t lsb_n, bool neg, const uint64_t *den,
                                     int nwd, int64_t lsb_d, int p, int L, MPOut o) {
   WinAcc an{num}, ad{den};
@@ -191,52 +244,35 @@ __device__ inline bool mp_div_round(const uint64_t *num, int nwn, int64_t lsb_n,
     store_zero(L, o.s, o.e, o.limb, o.stride);
     return true;
   }
-  // quotient Q = floor(num * 2^sh / den) with bit length p + 2 or p + 3
-  const int sh = (p + 3) - (nN - nD);     // num * 2^sh has nD + p + 3 bits
-  const int qbits = nN + sh;              // bits of num * 2^sh
-  const int dl = (nD + 63) / 64 + 1;      // remainder limbs
-  uint64_t R[kWinLimbs / 2 + 2], D[kWinLimbs / 2 + 2], Q[kMaxLimbs + 2];
-  if (dl > kWinLimbs / 2 + 2) return false;
-  for (int i = 0; i < dl; ++i) {
-    R[i] = 0;
-    D[i] = i < nwd ? den[i] : 0;
+  constexpr int kMaxU = 160, kMaxQ = 48;
+  const int sh = (p + 3) - (nN - nD);     // num 2^sh has nD + p + 3 bits
+  const int ubits = nN + sh;
+  const int m = (ubits + 31) / 32, n = (nD + 31) / 32;
+  if (m + 1 > kMaxU || n > 80 || m - n + 1 > kMaxQ) return false;
+  uint32_t u[kMaxU], v[80], q[kMaxQ];
+  for (int i = 0; i < m; ++i) {            // digits of num 2^sh (low bits dropped if sh < 0)
+    const uint64_t w = bits64_at(an, 2 * nwn, 32 * i - sh);
+    u[i] = (uint32_t)w;
   }
-  const int ql = (p + 3 + 63) / 64 + 1;
-  for (int i = 0; i < ql; ++i) Q[i] = 0;
-  // bits of num * 2^sh from the top: bit b of the shifted value = bit (b - sh) of num
-  for (int b = qbits - 1; b >= 0; --b) {
-    uint64_t carry = (uint64_t)bit_at(an, 2 * nwn, b - sh);   // shift the remainder left, bring in a bit
-    for (int i = 0; i < dl; ++i) {
-      const uint64_t nc = R[i] >> 63;
-      R[i] = (R[i] << 1) | carry;
-      carry = nc;
-    }
-    if (limbs_cmp(R, D, dl) >= 0) {
-      uint64_t br = 0;
-      for (int i = 0; i < dl; ++i) {
-        const uint64_t d = R[i] - D[i];
-        const uint64_t b1 = R[i] < D[i];
-        const uint64_t d2 = d - br;
-        br = b1 | (d < br);
-        R[i] = d2;
-      }
-      if (b < 64 * ql) Q[b >> 6] |= 1ull << (b & 63);
-    }
-  }
-  bool sticky = false;
-  for (int i = 0; i < dl; ++i) sticky |= R[i] != 0;
+  if (ubits % 32) u[m - 1] &= (1u << (ubits % 32)) - 1u;
+  for (int i = 0; i < n; ++i) v[i] = word_at(ad, i, 2 * nwd);
+  bool sticky = (m >= n) ? divmod_digits(u, m, v, n, q) : true;
   if (sh < 0) sticky |= any_below(an, 2 * nwn, -sh);   // numerator bits below the shifted window
-  // Q' = 2 Q + sticky, value = Q' 2^(lsb_n - lsb_d - sh - 1)
-  uint64_t Qs[kMaxLimbs + 3];
+  const int ql = m - n + 1;
+  // Q' = 2 Q + sticky as 64-bit limbs, value = Q' 2^(lsb_n - lsb_d - sh - 1)
+  uint64_t Qs[kMaxQ / 2 + 2];
+  const int qw = (ql + 1) / 2 + 1;
+  for (int i = 0; i < qw; ++i) Qs[i] = 0;
+  for (int i = 0; i < ql; ++i) Qs[i >> 1] |= (uint64_t)q[i] << (32 * (i & 1));
   uint64_t c = sticky ? 1ull : 0ull;
-  for (int i = 0; i < ql; ++i) {
-    Qs[i] = (Q[i] << 1) | c;
-    c = Q[i] >> 63;
+  for (int i = 0; i < qw; ++i) {
+    const uint64_t nc = Qs[i] >> 63;
+    Qs[i] = (Qs[i] << 1) | c;
+    c = nc;
   }
-  Qs[ql] = c;
   WinAcc aq{Qs};
-  const int NQ = bitlen(aq, 2 * (ql + 1));
-  return round_store(aq, 2 * (ql + 1), NQ, neg, lsb_n - lsb_d - (int64_t)sh - 1, p, L, o.s, o.e, o.limb, o.stride);
+  const int NQ = bitlen(aq, 2 * qw);
+  return round_store(aq, 2 * qw, NQ, neg, lsb_n - lsb_d - (int64_t)sh - 1, p, L, o.s, o.e, o.limb, o.stride);
 }
 
 }  // namespace mpc
