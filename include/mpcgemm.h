@@ -47,7 +47,8 @@
  *     all scratch space lives in the caller's `workspace` of `ws_bytes`
  *     bytes (device memory, 256-byte aligned), sized by
  *     mpcgemm_workspace_size().  C must not alias A, B or the workspace.
- *   * k == 0 gives C = 0; m == 0 or n == 0 is a no-op.
+ *   * k == 0 gives C = 0; m == 0 or n == 0 is a no-op (the workspace may be
+ *     NULL); inside a batched call such a problem's status block is cleared.
  */
 #ifndef MPCGEMM_H
 #define MPCGEMM_H
@@ -130,7 +131,7 @@ typedef struct mpc_plan {
     uint64_t off_status, off_rowexp, off_colexp, off_rowlossy, off_collossy;
     uint64_t off_digits_a, off_digits_b, off_groups, off_group_table;
     uint64_t off_fallback, fallback_capacity, off_fb_scratch, fb_scratch_limbs, fb_threads;
-    uint64_t off_fix_a, off_fix_b;  /* plain path: fixed-point operands */
+    uint64_t off_fix_a, off_fix_b;  /* unused (0) */
     uint64_t ws_bytes;
     int32_t launches;             /* kernel launches one call makes */
     int32_t reserved;
@@ -143,7 +144,7 @@ typedef struct mpc_plan {
  * on `stream` at that stage boundary:
  *   ev[0] call start, ev[1] after the split (row/column exponents, digits or
  *   fixed-point operands), ev[2] after the slice products (Ozaki) or the plain
- *   GEMM, ev[3] after the accumulation and rounding (Ozaki; = ev[2] for plain),
+ *   GEMM, ev[3] after the accumulation (plain: combination) and rounding,
  *   ev[4] after the exact fallback.  ev[5..7] unused.
  */
 typedef struct mpc_stage_events {
@@ -166,8 +167,10 @@ typedef struct mpc_status {
  * exact arithmetic both give the same C).  algo: MPC_OZAKI (Alg. 2 on the
  * tensor cores: balanced 8-bit integer slices, exact slice products, exact
  * accumulation, certified rounding with exact fallback) or MPC_PLAIN (the
- * triple loop of Eq. simple_triple_loop as an exact fixed-point multi-limb
- * GEMM on the CUDA cores; method must be MPC_4M).  Sizes use A->rows == m,
+ * triple loop of Eq. simple_triple_loop as an exact fixed-point GEMM on the
+ * CUDA cores: base-2^28 digit products summed exactly, 4 real products for
+ * MPC_4M, 3 for MPC_3M (Eq. 3m_way_base), certified rounding with exact
+ * fallback).  Sizes use A->rows == m,
  * A->cols == k, B->rows == k, B->cols == n, C->rows == m, C->cols == n.
  * Returns MPC_OK, MPC_EINVAL, MPC_ENOSPC, MPC_ENOTSUP or MPC_ECUDA - e.
  */
@@ -256,7 +259,7 @@ int mpcgemm_read_status(const void *workspace, size_t ws_bytes, mpc_status *stat
  * this entry point keeps that array until the process exits.  A problem whose
  * mpcgemm_workspace_size() exceeds it is rejected with MPC_ENOSPC before
  * anything is enqueued (for example m = n = k = 192 fits at p = 256 and 128 at
- * p = 1024 for Ozaki 4M/3M, 256 at p = 1024 for plain; 256 at p = 256 for Ozaki
+ * p = 1024 for Ozaki 4M/3M and for plain; 256 at p = 256 for Ozaki
  * does not).  The first call on a device looks
  * up the array's device address (it allocates nothing); make that first call
  * outside any stream capture.  Every call uses the same array and finds the

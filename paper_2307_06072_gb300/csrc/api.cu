@@ -82,17 +82,30 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   P.off_fb_scratch = off;
   off = align256(off + P.fb_threads * P.fb_scratch_limbs * 8);
   if (algo == MPC_PLAIN) {
-    const int Lp = L + 1;
-    P.off_fix_a = off;
-    off = align256(off + (uint64_t)2 * Lp * m * k * 8);
-    P.off_fix_b = off;
-    off = align256(off + (uint64_t)2 * Lp * n * k * 8);
-    P.off_digits_a = off;   // fixed-point signs of A, then of B
-    off = align256(off + (uint64_t)2 * m * k);
+    // signed base-2^28 digits of X = sign floor(|x| 2^(W - E)), W = 28 D - 2 >= p + 32
+    const int D = plain_digits_for(p);
+    if (D < 0) return MPC_EINVAL;
+    const int DP = (D + 3) & ~3, NLP = plain_limbs(D);
+    P.s = D;
+    P.kpad = DP;
+    P.bound_shift = kPlainDigitBits * D - 2;   // W: bounds are b 2^W in units of 2^(E+F-2W)
+    P.n_products = method == MPC_4M ? 4 : 3;
+    P.planes_A = P.planes_B = method == MPC_4M ? 2 : 3;
+    P.acc_slots = 2 * NLP;
+    for (int c = 0; c < 2; ++c) {
+      // per unit of k and lossy operand: Re = rr - ii and 4M Im = ri + ir carry 2 terms;
+      // 3M Im = ss - rr - ii: the sums' truncation is up to 2 + 2 (4), plus 1 + 1
+      const uint64_t coef = (c == 1 && method == MPC_3M) ? 6 : 2;
+      P.bound_lossy_a[c] = P.bound_lossy_b[c] = coef;
+    }
+    P.off_digits_a = off;
+    off = align256(off + (uint64_t)P.planes_A * m * k * DP * 4);
     P.off_digits_b = off;
-    off = align256(off + (uint64_t)2 * n * k);
+    off = align256(off + (uint64_t)P.planes_B * n * k * DP * 4);
+    P.off_groups = off;   // exact product sums [product][limb][i][j]
+    off = align256(off + (uint64_t)P.n_products * NLP * m * n * 8);
     P.ws_bytes = off;
-    P.launches = 8;   // init, row max, column max, 2 x fix, plain GEMM, fallback (+1 zero fill when k == 0)
+    P.launches = 8;   // init, row max, column max, 2 x digits, plain GEMM, combine, fallback (+1 zero fill when k == 0)
     return MPC_OK;
   }
   // ---- Ozaki: Alg. 2's number of slices and the kept triangle
@@ -243,7 +256,11 @@ int call_setup(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_mat *A
   c->k = k;
   c->p = p_bits;
   c->empty = (m == 0 || n == 0);
-  if (c->empty) return MPC_OK;
+  if (c->empty) {   // nothing to compute; a batched call still clears the problem's status block
+    const bool ws_ok = workspace && !((uintptr_t)workspace & 255) && ws_bytes >= kStatusWords * 4;
+    c->status = ws_ok ? (int32_t *)((char *)workspace + c->pl.pub.off_status) : nullptr;
+    return MPC_OK;
+  }
   if (!workspace || ((uintptr_t)workspace & 255)) return MPC_EINVAL;
   if (ws_bytes < c->pl.pub.ws_bytes) return MPC_ENOSPC;
   const mpc_plan &P = c->pl.pub;
@@ -271,11 +288,11 @@ void call_pre(Call &c, cudaStream_t st) {
   }
   launch_line_max(c.A, c.B, c.m, c.n, c.k, L, c.E, c.F, st);
   if (P.algo == MPC_PLAIN) {
-    const int Lp = L + 1;
-    launch_plain_fix(c.A, 0, c.m, c.k, L, Lp, c.E, c.lossyA, (uint64_t *)(c.ws + P.off_fix_a),
-                     (uint8_t *)(c.ws + P.off_digits_a), st);
-    launch_plain_fix(c.B, 1, c.n, c.k, L, Lp, c.F, c.lossyB, (uint64_t *)(c.ws + P.off_fix_b),
-                     (uint8_t *)(c.ws + P.off_digits_b), st);
+    const int W = P.bound_shift, want_sum = P.method == MPC_3M;
+    launch_plain_digits(c.A, 0, c.m, c.k, L, P.s, P.kpad, W, want_sum, c.E, c.lossyA,
+                        (int32_t *)(c.ws + P.off_digits_a), st);
+    launch_plain_digits(c.B, 1, c.n, c.k, L, P.s, P.kpad, W, want_sum, c.F, c.lossyB,
+                        (int32_t *)(c.ws + P.off_digits_b), st);
   } else {
     const int want_sum = P.method == MPC_3M;
     launch_group_table(c.pl.prod, P.n_products, P.Q, P.gmax, (GroupEntry *)(c.ws + P.off_group_table),
@@ -305,30 +322,55 @@ SliceGemmArgs slice_args(const Call &c) {
 
 void call_gemm_plain(Call &c, cudaStream_t st) {
   const mpc_plan &P = c.pl.pub;
-  PlainArgs pa{};
-  pa.fixA = (const uint64_t *)(c.ws + P.off_fix_a);
-  pa.fixB = (const uint64_t *)(c.ws + P.off_fix_b);
-  pa.sgnA = (const uint8_t *)(c.ws + P.off_digits_a);
-  pa.sgnB = (const uint8_t *)(c.ws + P.off_digits_b);
-  pa.m = c.m;
-  pa.n = c.n;
-  pa.k = c.k;
-  pa.p = c.p;
-  pa.L = P.limbs;
-  pa.Lp = P.limbs + 1;
-  pa.E = c.E;
-  pa.F = c.F;
-  pa.lossyA = c.lossyA;
-  pa.lossyB = c.lossyB;
-  pa.fallback = c.fallback;
-  pa.fallback_cap = (int64_t)P.fallback_capacity;
-  pa.status = c.status;
-  launch_plain_gemm(pa, c.C, st);
+  PlainGemmArgs ga{};
+  ga.dA = (const int32_t *)(c.ws + P.off_digits_a);
+  ga.dB = (const int32_t *)(c.ws + P.off_digits_b);
+  ga.m = c.m;
+  ga.n = c.n;
+  ga.k = c.k;
+  ga.D = P.s;
+  ga.n_products = P.n_products;
+  // operand planes: 4M rr, ii, ri, ir; 3M rr, ii, ss (plane 2 = X_re + X_im)
+  static const int pa4[4] = {0, 1, 0, 1}, pb4[4] = {0, 1, 1, 0}, pa3[4] = {0, 1, 2, 0}, pb3[4] = {0, 1, 2, 0};
+  for (int x = 0; x < 4; ++x) {
+    ga.planeA[x] = P.method == MPC_4M ? pa4[x] : pa3[x];
+    ga.planeB[x] = P.method == MPC_4M ? pb4[x] : pb3[x];
+  }
+  ga.sums = (uint64_t *)(c.ws + P.off_groups);
+  launch_plain_gemm(ga, st);
+}
+
+// the plain path's accumulate-and-round stage: combine the exact product sums, certify, round
+void call_plain_combine(Call &c, cudaStream_t st) {
+  const mpc_plan &P = c.pl.pub;
+  PlainCombineArgs ca{};
+  ca.sums = (const uint64_t *)(c.ws + P.off_groups);
+  ca.m = c.m;
+  ca.n = c.n;
+  ca.k = c.k;
+  ca.p = c.p;
+  ca.L = P.limbs;
+  ca.D = P.s;
+  ca.W = P.bound_shift;
+  ca.method = P.method;
+  ca.coef[0] = P.bound_lossy_a[0];
+  ca.coef[1] = P.bound_lossy_a[1];
+  ca.E = c.E;
+  ca.F = c.F;
+  ca.lossyA = c.lossyA;
+  ca.lossyB = c.lossyB;
+  ca.fallback = c.fallback;
+  ca.fallback_cap = (int64_t)P.fallback_capacity;
+  ca.status = c.status;
+  launch_plain_combine(ca, c.C, st);
 }
 
 void call_accum(Call &c, cudaStream_t st) {
   const mpc_plan &P = c.pl.pub;
-  if (P.algo != MPC_OZAKI) return;   // the plain GEMM rounds in its own epilogue
+  if (P.algo != MPC_OZAKI) {
+    call_plain_combine(c, st);
+    return;
+  }
   AccumArgs aa{};
   aa.planes = (const int32_t *)(c.ws + P.off_groups);
   aa.groups = (const GroupEntry *)(c.ws + P.off_group_table);
@@ -466,8 +508,10 @@ int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *pa
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaGetLastError();
-  for (int x = 0; x < count; ++x)
+  for (int x = 0; x < count; ++x) {
     if (!calls[x].empty) call_pre(calls[x], st);
+    else if (calls[x].status) cudaMemsetAsync(calls[x].status, 0, kStatusWords * 4, st);
+  }
   thread_local std::vector<SliceGemmArgs> slices;
   slices.clear();
   bool any_tall = false;

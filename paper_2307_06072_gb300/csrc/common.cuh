@@ -18,6 +18,12 @@ constexpr int kChunk = 960;            // K elements per fp32 drain: 960 * 2^14 
 constexpr int kKBlock = 64;            // digit-plane row padding (one 128-byte bf16 row)
 constexpr int kMaxSlices = 160;
 constexpr int kMaxLimbs = 16;          // p <= 1024
+// plain path: base-2^28 digits, D <= 40 at p <= 1024 (28 D - 2 >= p + 32, D a multiple of 4)
+constexpr int kPlainDigitBits = 28;
+constexpr int kMaxPlainDigits = 40;
+// 64-bit limbs of an exact plain-path sum of k <= 2^17 digit products
+// (|sum| < k 2^(56 D - 1), plus the sign and the 3M combination)
+__host__ __device__ constexpr int plain_limbs(int D) { return (56 * D + 18 + 63) / 64; }
 constexpr int kStatusWords = 16;
 constexpr int kDefaultGuard = 40;
 

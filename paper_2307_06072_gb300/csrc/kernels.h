@@ -44,16 +44,31 @@ struct FallbackArgs {
   int32_t *status;
 };
 
-struct PlainArgs {
-  const uint64_t *fixA, *fixB;  // [c][limb][line][k]
-  const uint8_t *sgnA, *sgnB;   // [c][line][k]
+// Plain path (k_plain_gemm / k_plain_combine).  Operand digits [plane][line][l][DP]
+// (int32, base 2^28, least significant first); exact product sums
+// [product][limb][i][j] (two's complement, plain_limbs(D) 64-bit limbs).
+struct PlainGemmArgs {
+  const int32_t *dA, *dB;
   int64_t m, n, k;
-  int p, L, Lp;
+  int D;
+  int n_products;
+  int planeA[4], planeB[4];   // operand planes of each real product
+  uint64_t *sums;
+};
+
+struct PlainCombineArgs {
+  const uint64_t *sums;
+  int64_t m, n, k;
+  int p, L, D, W, method;
+  uint64_t coef[2];           // lossy bound per unit of k and lossy operand, Re / Im
   const int32_t *E, *F, *lossyA, *lossyB;
   int64_t *fallback;
   int64_t fallback_cap;
   int32_t *status;
 };
+
+// digits per operand of the plain path at precision p (an instantiated size)
+int plain_digits_for(int p);
 
 void launch_init(int32_t *status, int32_t *E, int64_t m, int32_t *F, int64_t n, int32_t *lossyA, int32_t *lossyB,
                  cudaStream_t st);
@@ -61,8 +76,8 @@ void launch_line_max(const MatView &A, const MatView &B, int64_t m, int64_t n, i
                      int32_t *F, cudaStream_t st);
 void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
                       int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, cudaStream_t st);
-void launch_plain_fix(const MatView &X, int side, int64_t lines, int64_t k, int L, int Lp, const int32_t *E,
-                      int32_t *lossy, uint64_t *fix, uint8_t *fsign, cudaStream_t st);
+void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, int L, int D, int DP, int W,
+                         int want_sum, const int32_t *E, int32_t *lossy, int32_t *digits, cudaStream_t st);
 void launch_group_table(const ProductDesc *prods, int n_products, int Q, int gmax, GroupEntry *table,
                         int32_t *order, cudaStream_t st);
 void launch_slicegemm_mma(const SliceGemmArgs &a, cudaStream_t st);
@@ -71,7 +86,8 @@ cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cuda
 void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st);
 void launch_fallback(const FallbackArgs &f, const MatView &A, const MatView &B, const OutView &C, int blocks,
                      int threads, cudaStream_t st);
-void launch_plain_gemm(const PlainArgs &a, const OutView &C, cudaStream_t st);
+void launch_plain_gemm(const PlainGemmArgs &a, cudaStream_t st);
+void launch_plain_combine(const PlainCombineArgs &a, const OutView &C, cudaStream_t st);
 void launch_zero_output(const OutView &C, int64_t m, int64_t n, int L, cudaStream_t st);
 
 }  // namespace mpc

@@ -11,7 +11,8 @@
 //    first; digit t stands for slice A_{t+1}.  For the 3M form (Eq. 3m_way)
 //    the digits of X_re + X_im are produced as well (s+1 digits).  B is split
 //    by columns and stored transposed (K-major), as the tensor cores read it.
-//  * k_plain_fix: the plain path's fixed-point operands (L+1 limbs).
+//  * k_plain_digits: the plain path's fixed-point operands as signed
+//    base-2^28 digits.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -234,43 +235,70 @@ __global__ void k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64
 
 // Plain path: X = floor(|a| 2^(64 Lp - E)) as Lp limbs (Lp = L + 1), sign kept apart.
 // Layout: fix[(c * Lp + j) * lines * k + line * k + l], fsign[c * lines * k + line * k + l].
-__global__ void k_plain_fix(MatView X, int side, int64_t lines, int64_t k, int L, int Lp, const int32_t *E,
-                            int32_t *lossy, uint64_t *fix, uint8_t *fsign) {
-  int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t line = blockIdx.y;
-  if (l >= k || line >= lines) return;
-  const int64_t plane = lines * k;
-  const int64_t o = line * k + l;
-  int32_t e_line = E[line];
-  int64_t idx = side == 0 ? line * X.ld + l : l * X.ld + line;
-  bool ok = true;
+// Plain path operands.  Per row of A (column of B) the fixed point
+//     X = sign * floor(|x| 2^(W - E_line)),   |X| < 2^W,  W = 28 D - 2,
+// written in D balanced base-2^28 digits, least significant first:
+// X = sum_t d_t 2^(28 t) with |d_t| <= 2^27, so that every digit product is
+// below 2^54 in magnitude and a signed 64-bit column sum absorbs hundreds of
+// them.  With want_sum (3M) a third plane holds the digits of X_re + X_im
+// (|X_re + X_im| < 2^(W+1); its top digit is left unnormalised, still
+// |d| <= 2^27).  Layout [plane][line][l][DP] (DP = D rounded up to 4).  A
+// line is lossy when some element dropped nonzero bits (exponent more than
+// W - p below E_line).  Threads run along the contiguous index of the matrix
+// (l for A, the column for B); the second grid dimension strides.
+__global__ void k_plain_digits(MatView X, int side, int64_t lines, int64_t k, int L, int D, int DP, int W,
+                               int want_sum, const int32_t *E, int32_t *lossy, int32_t *digits) {
+  const int64_t fast = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nslow = side == 0 ? lines : k;
+  if (fast >= (side == 0 ? k : lines)) return;
+  for (int64_t slow = blockIdx.y; slow < nslow; slow += gridDim.y) {
+    const int64_t line = side == 0 ? slow : fast, l = side == 0 ? fast : slow;
+    const int64_t idx = side == 0 ? line * X.ld + l : l * X.ld + line;
+    const int32_t e_line = E[line];
+    const int64_t plane = lines * k * DP;
+    int32_t *out = digits + (line * k + l) * DP;
+    int32_t dsum[kMaxPlainDigits];
+    bool ok = true;
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    bool nz = (e_line != INT32_MIN) && comp_nonzero(X, c, idx, L);
-    uint64_t M[kMaxLimbs];
-    for (int j = 0; j < L; ++j) M[j] = nz ? X.limb[c][(int64_t)j * X.plane + idx] : 0ull;
-    // |X| bit b <-> M bit b - sl, sl = 64(Lp - L) - (E - exp)
-    int64_t sl = nz ? (64 * (int64_t)(Lp - L) - ((int64_t)e_line - (int64_t)X.exp[c][idx])) : 0;
-    if (nz && sl < 0) {
-      if (-sl >= 64 * (int64_t)L || !low_bits_zero(M, L, -sl)) ok = false;
-    }
-    for (int j = 0; j < Lp; ++j) {
-      uint64_t v = 0;
-      if (nz) {
-        int64_t b = 64 * (int64_t)j - sl;   // M bit of X bit 64j
-        if (b < 64 * (int64_t)L && b > -64) {
-          int64_t w = b >> 6;
-          int off = (int)(b & 63);
-          uint64_t lo = (w >= 0 && w < L) ? M[w] : 0ull;
-          uint64_t hi = (w + 1 >= 0 && w + 1 < L) ? M[w + 1] : 0ull;
-          v = off ? ((lo >> off) | (hi << (64 - off))) : lo;
-        }
+    for (int c = 0; c < 2; ++c) {
+      const bool nz = (e_line != INT32_MIN) && comp_nonzero(X, c, idx, L);
+      uint64_t M[kMaxLimbs];
+#pragma unroll
+      for (int j = 0; j < kMaxLimbs; ++j) M[j] = (nz && j < L) ? X.limb[c][(int64_t)j * X.plane + idx] : 0ull;
+      // |X| = M 2^sh (truncated); exp <= E_line, so sh <= W - 64 L
+      const int64_t sh = nz ? (int64_t)W - 64 * (int64_t)L - ((int64_t)e_line - (int64_t)X.exp[c][idx]) : 0;
+      if (nz && sh < 0 && (-sh >= 64 * (int64_t)L || !low_bits_zero(M, L, -sh))) ok = false;
+      const bool neg = nz && X.sign[c][idx];
+      int32_t carry = 0;
+#pragma unroll
+      for (int t = 0; t < kMaxPlainDigits; ++t) {
+        if (t >= D) break;
+        const uint32_t u = nz ? (uint32_t)(word_at_bit(M, L, 28 * (int64_t)t - sh) & 0xFFFFFFFull) : 0u;
+        int32_t v = (int32_t)u + carry;              // [0, 2^28]
+        carry = v >= (1 << 27) ? 1 : 0;
+        v -= carry << 28;                            // [-2^27, 2^27)
+        const int32_t d = neg ? -v : v;
+        out[(int64_t)c * plane + t] = d;
+        dsum[t] = c == 0 ? d : dsum[t] + d;
       }
-      fix[((int64_t)c * Lp + j) * plane + o] = v;
+      for (int t = D; t < DP; ++t) out[(int64_t)c * plane + t] = 0;
     }
-    fsign[(int64_t)c * plane + o] = nz ? X.sign[c][idx] : 0;
+    if (want_sum) {
+      int32_t cy = 0;
+#pragma unroll
+      for (int t = 0; t < kMaxPlainDigits; ++t) {
+        if (t >= D) break;
+        int32_t v = dsum[t] + cy;                    // |v| <= 2^28 + 1
+        if (t < D - 1) {
+          cy = (v + (1 << 27)) >> 28;                // floor: v - cy 2^28 in [-2^27, 2^27)
+          v -= cy * (1 << 28);
+        }
+        out[2 * plane + t] = v;
+      }
+      for (int t = D; t < DP; ++t) out[2 * plane + t] = 0;
+    }
+    if (!ok) atomicOr(lossy + line, 1);
   }
-  if (!ok) atomicOr(lossy + line, 1);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -296,10 +324,11 @@ void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int6
   k_oz_digits<<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits);
 }
 
-void launch_plain_fix(const MatView &X, int side, int64_t lines, int64_t k, int L, int Lp, const int32_t *E,
-                      int32_t *lossy, uint64_t *fix, uint8_t *fsign, cudaStream_t st) {
-  dim3 g((unsigned)((k + 127) / 128), (unsigned)lines);
-  k_plain_fix<<<g, 128, 0, st>>>(X, side, lines, k, L, Lp, E, lossy, fix, fsign);
+void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, int L, int D, int DP, int W,
+                         int want_sum, const int32_t *E, int32_t *lossy, int32_t *digits, cudaStream_t st) {
+  const int64_t fast = side == 0 ? k : lines, slow = side == 0 ? lines : k;
+  dim3 g((unsigned)((fast + 127) / 128), (unsigned)(slow < 65535 ? slow : 65535));
+  k_plain_digits<<<g, 128, 0, st>>>(X, side, lines, k, L, D, DP, W, want_sum, E, lossy, digits);
 }
 
 }  // namespace mpc

@@ -21,9 +21,10 @@ def _check_against_o1(C, A, B, p):
     assert len(bad) == 0, f"{len(bad)} mismatching components, first {bad[:5].tolist()}"
 
 
-def test_plain_config0_bit_exact():
+@pytest.mark.parametrize("method", ["4m", "3m"])
+def test_plain_config0_bit_exact(method):
     A, B, p = si.make_config("c0_plain_32_p128")
-    C, ws, st = gu.run(A, B, p, "4m", "plain")
+    C, ws, st = gu.run(A, B, p, method, "plain")
     assert gu.same(C, exact.rounded_cgemm(A, B, p))
     assert st["erange"] == 0
 
@@ -40,11 +41,49 @@ def test_ozaki_ragged_tiles_bit_exact(method, dist, zf):
     assert st["fallback_overflow"] == 0 and st["uncertified"] == 0
 
 
-def test_plain_ragged_bit_exact():
-    p = 192
+@pytest.mark.parametrize("method", ["4m", "3m"])
+@pytest.mark.parametrize("p", [192, 1000])
+def test_plain_ragged_bit_exact(method, p):
+    """5 x 2 output tiles of 8 x 16 with ragged edges, a k tail (70 = 8 * 8 + 6); p = 1000
+    takes the largest digit count (38 digits of 28 bits)."""
     A = si.random_matrix(37, 70, p, 311, "uniform_exp", zero_frac=0.1)
     B = si.random_matrix(70, 29, p, 312, "uniform_exp")
-    C, ws, st = gu.run(A, B, p, "4m", "plain")
+    C, ws, st = gu.run(A, B, p, method, "plain")
+    _check_against_o1(C, A, B, p)
+    assert st["uncertified"] == 0
+
+
+def _largest_digit_mantissa(pl, L):
+    """Mantissa whose plain-path digits are all -2^27 (the largest magnitude) above the
+    bits that the fixed-point shift leaves zero, for an element at the row's exponent."""
+    D, W = pl["s"], pl["bound_shift"]
+    sh = W - 64 * L                              # X = M 2^sh
+    t0 = -(-sh // 28) + 1
+    X = (1 << 27) << (28 * t0)
+    for t in range(t0 + 1, D - 1):
+        X += ((1 << 27) - 1) << (28 * t)
+    X += ((1 << 26) - 1) << (28 * (D - 1))       # top group: bit W-1 set (normalised)
+    assert X >> (W - 1) == 1 and X % (1 << sh) == 0
+    M = X >> sh
+    return [(M >> (64 * j)) & 0xFFFFFFFFFFFFFFFF for j in range(L)]
+
+
+@pytest.mark.parametrize("method", ["4m", "3m"])
+def test_plain_long_k_largest_sums(method):
+    """k = 20000 products of digits at their largest magnitude, all of one sign: every
+    column sum of the plain kernel and its signed top column reach their largest values."""
+    p, k = 256, 20000
+    A = si.random_matrix(3, k, p, 315)
+    B = si.random_matrix(k, 4, p, 316)
+    L = si.limbs_for(p)
+    limbs = _largest_digit_mantissa(gu.plan(A, B, p, method, "plain"), L)
+    for X in (A, B):
+        for j in range(L):
+            X.limb[:, j] = np.uint64(limbs[j])
+        X.sign[:] = 0
+        X.exp[:] = 0
+    B.sign[1] = 1                      # Im(B) < 0: Re(AB) = rr - ii adds up, Im(AB) cancels to 0
+    C, ws, st = gu.run(A, B, p, method, "plain")
     _check_against_o1(C, A, B, p)
 
 
@@ -121,8 +160,9 @@ def test_methods_and_algorithms_agree_bitwise():
     p = 320
     A = si.random_matrix(150, 140, p, 341, "uniform_exp")
     B = si.random_matrix(140, 130, p, 342, "uniform_exp")
-    outs = [gu.run(A, B, p, m_, a_)[0] for m_, a_ in (("4m", "ozaki"), ("3m", "ozaki"), ("4m", "plain"))]
-    assert gu.same(outs[0], outs[1]) and gu.same(outs[0], outs[2])
+    outs = [gu.run(A, B, p, m_, a_)[0] for m_, a_ in (("4m", "ozaki"), ("3m", "ozaki"), ("4m", "plain"),
+                                                       ("3m", "plain"))]
+    assert all(gu.same(outs[0], o) for o in outs[1:])
     _check_against_o1(outs[0], A, B, p)
 
 
@@ -137,7 +177,7 @@ def test_k_zero_gives_zero(algo):
     assert not C.limb.any() and not C.sign.any() and np.all(C.exp == si.INT32_MIN)
 
 
-@pytest.mark.parametrize("algo,method", [("ozaki", "4m"), ("ozaki", "3m"), ("plain", "4m")])
+@pytest.mark.parametrize("algo,method", [("ozaki", "4m"), ("ozaki", "3m"), ("plain", "4m"), ("plain", "3m")])
 def test_zero_rows_columns_identity_and_padded_ld(algo, method):
     p = 256
     A = si.random_matrix(20, 20, p, 351, "uniform_exp")
@@ -153,7 +193,7 @@ def test_zero_rows_columns_identity_and_padded_ld(algo, method):
     _check_against_o1(C2, A, B2, p)
 
 
-@pytest.mark.parametrize("algo,method", [("ozaki", "4m"), ("ozaki", "3m"), ("plain", "4m")])
+@pytest.mark.parametrize("algo,method", [("ozaki", "4m"), ("ozaki", "3m"), ("plain", "4m"), ("plain", "3m")])
 def test_tiny_and_one_by_one(algo, method):
     for (m, k, n, p) in ((1, 1, 1, 64), (1, 3, 2, 1), (3, 1, 2, 1000), (2, 2, 2, 65)):
         A = si.random_matrix(m, k, p, 360 + m, "uniform_exp")
@@ -162,7 +202,7 @@ def test_tiny_and_one_by_one(algo, method):
         assert gu.same(C, exact.rounded_cgemm(A, B, p)), (m, k, n, p)
 
 
-@pytest.mark.parametrize("algo,method", [("ozaki", "4m"), ("ozaki", "3m"), ("plain", "4m")])
+@pytest.mark.parametrize("algo,method", [("ozaki", "4m"), ("ozaki", "3m"), ("plain", "4m"), ("plain", "3m")])
 def test_huge_exponent_spread(algo, method):
     """Exponents over +-3000: lossy splits, uncertified entries, exact fallbacks."""
     p = 128
@@ -210,7 +250,17 @@ def test_config2_2048_p1024_3m_sampled():
     _sampled(C, A, B, p, 96, 8)
 
 
-def test_plain_1024_p512_sampled():
+@pytest.mark.parametrize("method", ["4m", "3m"])
+def test_plain_1024_p512_sampled(method):
     A, B, p = si.make_config("c2_1024_p512")
-    C, ws, st = gu.run(A, B, p, "4m", "plain")
+    C, ws, st = gu.run(A, B, p, method, "plain")
+    assert st["uncertified"] == 0
     _sampled(C, A, B, p, 96, 9)
+
+
+def test_plain_2048_p1024_3m_sampled():
+    """The plain GEMM at the size and launch configuration the benchmark times."""
+    A, B, p = si.make_config("c2_2048_p1024")
+    C, ws, st = gu.run(A, B, p, "3m", "plain")
+    assert st["uncertified"] == 0
+    _sampled(C, A, B, p, 64, 10)
