@@ -6,7 +6,7 @@ cores, exact accumulation + certified rounding, exact fallback.
 
 Default workload: m = n = k = 2048, p = 1024 bits, Ozaki 3M, entries
 u * 2^e (u uniform on the p-bit grid of [-1, 1), e uniform in [-20, 20]),
-seeded.  Ozaki 4M and the plain multi-limb GEMM are timed beside it.
+seeded.  Ozaki 4M and the plain GEMM (3M and 4M) are timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -75,15 +75,24 @@ def batch_specs(count: int = 64, seed: int = si.SEED_BASE + 3):
     return [(int(m), int(k), int(n), int(p)) for (m, n, k), p in zip(mnk, ps)]
 
 
+def batch_host_problems(specs):
+    """The seeded operands of the batched workload (host side)."""
+    out = []
+    for x, (m, k, n, p) in enumerate(specs):
+        A = si.random_matrix(m, k, p, si.SEED_BASE + 3000 + 2 * x, "uniform")
+        B = si.random_matrix(k, n, p, si.SEED_BASE + 3001 + 2 * x, "uniform")
+        out.append((A, B, p))
+    return out
+
+
 def run_batched(mp, torch, dev, stream, steps: int, warmup: int):
     """One step = one batched call over the 64 problems, replayed from a CUDA graph."""
     from paper_2307_06072_gb300.autotune import Autotuner
     stream = torch.cuda.Stream(dev)          # graphs are captured on a side stream
     specs = batch_specs()
     probs = []
-    for x, (m, k, n, p) in enumerate(specs):
-        A = si.random_matrix(m, k, p, si.SEED_BASE + 3000 + 2 * x, "uniform")
-        B = si.random_matrix(k, n, p, si.SEED_BASE + 3001 + 2 * x, "uniform")
+    for x, (A, B, p) in enumerate(batch_host_problems(specs)):
+        m, k, n = A.rows, A.cols, B.cols
         probs.append((mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(B, dev),
                       mp.DeviceMatrix.empty(m, n, p, dev), p, "3m", "ozaki"))
     tuner = Autotuner()
@@ -179,6 +188,25 @@ def run_serving(mp, torch, dev, seed: int = si.SEED_BASE + 5, count: int = 40):
     out["note"] = (f"{count} requests (every 6th an LU solve, n in {{128, 256}}), Poisson arrivals with a 4 ms "
                    "mean gap, 4 stream slots, 48 GB budget; latency = completion - arrival")
     return out
+
+
+# Plain path roof: 64 IMAD lanes per clock per SM, two lane-operations (low and high
+# word) per 32 x 32 -> 64-bit digit product, 152 SMs at the 2070 MHz maximum SM clock.
+PLAIN_PRODUCTS_PER_CLK_SM = 32
+SMS, MAX_SM_GHZ = 152, 2.07
+
+
+def plain_roofline(mp, m, n, k, p, method, gemm_ms):
+    """ALU roofline of the plain GEMM kernel: schoolbook digit products / its event time."""
+    pl = mp.plan(m, n, k, p, method, "plain")
+    products = pl["n_products"] * pl["s"] ** 2 * m * n * k
+    peak = PLAIN_PRODUCTS_PER_CLK_SM * SMS * MAX_SM_GHZ * 1e9
+    achieved = products / (gemm_ms / 1e3)
+    return {"bound": "alu", "kernel": "k_plain_gemm", "achieved": round(achieved / 1e12, 3),
+            "peak": round(peak / 1e12, 3), "unit": "T digit-products/s (32x32->64 bit)",
+            "frac": round(achieved / peak, 4), "traffic": None, "digits": pl["s"],
+            "algorithmic_products_per_launch": products, "kernel_ms": round(gemm_ms, 3),
+            "peak_source": "64 IMAD lanes/clk/SM / 2 per wide product x 152 SMs x 2.07 GHz"}
 
 
 def pair_count(s: int, Q: int, method: str) -> int:
@@ -310,8 +338,9 @@ def run_ours(args):
     dC = mp.DeviceMatrix.empty(m, n, p, dev)
     stream = torch.cuda.current_stream(dev)
     method = args.method
-    params = {"kernel": args.kernel}
-    pl = mp.plan(m, n, k, p, method, "ozaki", params)
+    algo = args.algo
+    params = {"kernel": args.kernel} if algo == "ozaki" else None
+    pl = mp.plan(m, n, k, p, method, algo, params)
     ws = mp.Workspace(dev)
     ws.get(pl["ws_bytes"])
 
@@ -350,21 +379,22 @@ def run_ours(args):
 
     units = 8.0 * m * n * k
     with ClockSampler(dev.index or 0) as clocks:
-        ms_main, stages = timed(method, "ozaki", args.steps, args.warmup, with_events=True)
+        ms_main, stages = timed(method, algo, args.steps, args.warmup, with_events=True)
     ms_main = max_over_ranks(ms_main)
     st = mp.read_status(ws, stream)
     value = units * args.steps * ws_ / (ms_main / 1e3)
     extras = {}
-    if not args.quick:
+    if not args.quick and algo == "ozaki":
         other = "4m" if method == "3m" else "3m"
         ms_o, st_o = timed(other, "ozaki", max(1, args.steps // 2), 1, with_events=True)
         extras[f"ozaki_{other}"] = {"value": units * max(1, args.steps // 2) * ws_ / (max_over_ranks(ms_o) / 1e3),
                                     "ms_per_step": ms_o / max(1, args.steps // 2),
                                     "stage_ms": st_o}
-        ms_pl, st_pl = timed("4m", "plain", 1, 1, with_events=True)
-        extras["plain_4m"] = {"value": units * ws_ / (max_over_ranks(ms_pl) / 1e3), "ms_per_step": ms_pl,
-                              "stage_ms": st_pl}
-        extras["ozaki_speedup_vs_plain"] = value / extras["plain_4m"]["value"]
+        for pm in (method, other):
+            ms_pl, st_pl = timed(pm, "plain", 1, 1, with_events=True)
+            extras[f"plain_{pm}"] = {"value": units * ws_ / (max_over_ranks(ms_pl) / 1e3), "ms_per_step": ms_pl,
+                                     "stage_ms": st_pl, "roofline": plain_roofline(mp, m, n, k, p, pm, st_pl[1])}
+        extras["ozaki_speedup_vs_plain"] = value / extras[f"plain_{method}"]["value"]
         if not args.no_batched:
             extras["batched_c3"] = run_batched(mp, torch, dev, stream, 3, 3)
         if not args.no_lu:
@@ -372,7 +402,7 @@ def run_ours(args):
             extras["serving"] = run_serving(mp, torch, dev)
 
     # roofline of the dominant kernel (the slice GEMM): algorithmic MMA flops / its event time
-    pairs = pair_count(pl["s"], pl["Q"], method)
+    pairs = pair_count(pl["s"], pl["Q"], method) if algo == "ozaki" else 0
     flops = pairs * 2.0 * m * n * k
     gemm_ms = stages[1]
     peaks, peak_src = measured_peaks()
@@ -383,6 +413,8 @@ def run_ours(args):
                 "frac": round(achieved / peak, 4), "traffic": committed_traffic(khash),
                 "kernel": "oz_slicegemm", "peak_source": f"bf16_tflops_sustained ({peak_src})",
                 "algorithmic_flops_per_launch": flops, "kernel_ms": round(gemm_ms, 3)}
+    if algo == "plain":
+        roofline = plain_roofline(mp, m, n, k, p, method, gemm_ms)
 
     # e2e through the public API with host buffers: every step copies its inputs from
     # pinned host memory and its result back, inside the timed region.  Two device
@@ -420,7 +452,7 @@ def run_ours(args):
                 stream.wait_event(h2d_done[b_])
                 if i >= 2:
                     stream.wait_event(d2h_done[b_])
-                mp.mpcgemm(X, Y, Z, p, method, "ozaki", workspace=ws, stream=stream, params=params)
+                mp.mpcgemm(X, Y, Z, p, method, algo, workspace=ws, stream=stream, params=params)
                 comp_done[b_].record(stream)
                 comp_started[b_] = True
                 if i + 1 < steps:
@@ -463,8 +495,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_main / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16 slices (exact int), u64 limbs",
             "data": "synthetic (seeded)",
-            "config": {"workload": f"{args.workload}: ozaki {method}, m=n=k={m}, p={p} bits, entries u*2^e, "
-                                   "e in [-20,20]", "method": method, "algo": "ozaki", "m": m, "n": n, "k": k,
+            "config": {"workload": f"{args.workload}: {algo} {method}, m=n=k={m}, p={p} bits, entries u*2^e, "
+                                   "e in [-20,20]", "method": method, "algo": algo, "m": m, "n": n, "k": k,
                        "p_bits": p, "kernel": args.kernel, "slices": pl["s"], "cut_level_Q": pl["Q"], "pairs": pairs,
                        "l2": "inputs (A, B: %.2f GB) larger than L2 (126 MB)" % ((A.nbytes() + B.nbytes()) / 1e9),
                        "parallelism": f"replicas x{ws_}"},
@@ -503,12 +535,59 @@ def cpu_baseline(A, B, p, seconds: float, entries_hint: int = 0):
                       f"exact C oracle, {dt:.1f} s"}
 
 
+def cpu_baseline_batch(problems, seconds: float):
+    """The oracle on the same number of random output entries of every problem of the batch."""
+    from oracle import c_oracle
+    rng = np.random.default_rng(12346)
+
+    def once(cnt):
+        units, t0 = 0.0, time.perf_counter()
+        for (A, B, p) in problems:
+            ent = np.stack([rng.integers(0, A.rows, cnt), rng.integers(0, B.cols, cnt)], axis=1)
+            c_oracle.rounded_cgemm(A, B, p, ent)
+            units += 8.0 * A.cols * cnt
+        return units, time.perf_counter() - t0
+    _, dt1 = once(1)
+    cnt = max(1, int(seconds / max(dt1, 1e-6)))
+    units, dt = once(cnt)
+    return {"value": units / dt, "unit": UNIT, "cores": c_oracle.max_threads(), "kind": "oracle",
+            "sample": f"{cnt} random output entries of each of the {len(problems)} problems, exact C oracle, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference_batch(args, ws_):
+    specs = batch_specs()
+    problems = batch_host_problems(specs)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline_batch(problems, min(per_step, 5.0))
+    vals, cb = [], None
+    for _ in range(args.steps):
+        cb = cpu_baseline_batch(problems, per_step)
+        vals.append(cb["value"])
+    value = float(np.mean(vals))
+    cb["value"] = value
+    work = sum(8.0 * m * n * k for (m, k, n, p) in specs)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": work / value * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "exact integer (u64 limbs)", "data": "synthetic (seeded)",
+            "config": {"workload": "c3_batch64: 64 complex GEMMs, m,n,k log-uniform in [64,1024], "
+                                   "p in {256,512,1024}, uniform [-1,1) entries, exact oracle"},
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     ws_, rank, _ = dist_env()
     if rank != 0:
         return
     from oracle import c_oracle
     c_oracle.build()
+    if args.workload == BATCH_WORKLOAD:
+        run_reference_batch(args, ws_)
+        return
     m, n, k, p, dist, _ = WORKLOADS[args.workload]
     A, B, p = make_inputs(args.workload, 0)
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
@@ -542,6 +621,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched side measurement")
     ap.add_argument("--no-lu", action="store_true", help="skip the LU and serving side measurements")
     ap.add_argument("--method", choices=["3m", "4m"], default="3m")
+    ap.add_argument("--algo", choices=["ozaki", "plain"], default="ozaki",
+                    help="the timed step's algorithm (plain: the CUDA-core GEMM, no side measurements)")
     ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_pair", "mma_sync"], default="auto",
                     help="slice-GEMM kernel")
     ap.add_argument("--quick", action="store_true", help="skip the 4M / plain side measurements")
