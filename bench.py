@@ -46,7 +46,17 @@ WORKLOADS = {
 }
 BATCH_WORKLOAD = "c3_batch64"
 PROFILE = os.path.join(ROOT, "profiles", "oz_slicegemm_c2_2048_p1024.md")
-SLICEGEMM_SRC = os.path.join(ROOT, "paper_2307_06072_gb300", "csrc", "slicegemm_tc.cu")
+# the slice GEMM kernel and the group table / unit schedule it runs over
+SLICEGEMM_SRC = [os.path.join(ROOT, "paper_2307_06072_gb300", "csrc", f) for f in ("slicegemm_tc.cu", "accum.cu")]
+
+
+def sources_hash(paths) -> str:
+    h = hashlib.sha256()
+    for f in paths:
+        if not os.path.exists(f):
+            return ""
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def log(*a):
@@ -408,7 +418,7 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
     achieved = flops / (gemm_ms / 1e3) / 1e12
-    khash = hashlib.sha256(open(SLICEGEMM_SRC, "rb").read()).hexdigest()[:16] if os.path.exists(SLICEGEMM_SRC) else ""
+    khash = sources_hash(SLICEGEMM_SRC)
     roofline = {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": committed_traffic(khash),
                 "kernel": "oz_slicegemm", "peak_source": f"bf16_tflops_sustained ({peak_src})",

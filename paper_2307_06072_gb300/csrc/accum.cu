@@ -15,6 +15,8 @@
 // k_exact_fallback: one thread per queued component; the exact dot product
 // of Eq. (simple_triple_loop) with Eq. (4m_way_base), in a fixed-point window
 // wide enough for every product, then RN_p.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -109,6 +111,22 @@ __global__ void k_group_table(ProductDesc p0, ProductDesc p1, ProductDesc p2, Pr
     if (best < 0) break;
     order[n++] = next[best]--;
   }
+  // the slice GEMM's schedule: product by product, groups by descending pair
+  // count (stable), so that consecutive units take nearly equally long and the
+  // groups of adjacent levels, which share digit planes, stay next to each other
+  // (counting sort per product; count <= kMaxSlices + 1)
+  int32_t *sched = order + n;
+  int out = 0;
+  for (int x = 0; x < n_products; ++x) {
+    const int g0 = pds[x].group0, g1 = g0 + pds[x].n_groups;
+    int start[kMaxSlices + 3];
+    for (int c = 0; c < kMaxSlices + 3; ++c) start[c] = 0;
+    for (int e = g0; e < g1; ++e) ++start[kMaxSlices + 1 - table[e].count + 1];
+    start[0] = out;
+    for (int c = 1; c < kMaxSlices + 3; ++c) start[c] += start[c - 1];
+    for (int e = g0; e < g1; ++e) sched[start[kMaxSlices + 1 - table[e].count]++] = e;
+    out += g1 - g0;
+  }
 }
 
 // One accumulation term per group, in order of descending level: plane index,
@@ -144,43 +162,104 @@ __device__ __forceinline__ void finish_component(const AccumArgs &a, const OutVi
   }
 }
 
-// One thread per output element (i, j).  The groups of one level are summed in
-// plain int64 (|sum| < 2^36) and folded into the exact accumulators once per level.
-__global__ void __launch_bounds__(128) k_oz_accum(AccumArgs a, OutView C) {
-  extern __shared__ Term terms[];
-  for (int x = threadIdx.x; x < a.n_entries; x += blockDim.x) {
+// One thread per output element (i, j); a block takes kAccT consecutive
+// elements of one row.  The group values are staged through shared memory
+// kAccBatch groups at a time, double-buffered with cp.async: while the block
+// folds one batch the next one is in flight.  Each warp copies contiguous runs
+// of one group plane (16-byte copies when n is a multiple of 4).  The groups of
+// one level are summed in plain int64 (|sum| < 2^36) and folded into the exact
+// accumulators once per level.
+constexpr int kAccT = 256, kAccBatch = 32;
+constexpr size_t kAccStageBytes = 2ull * kAccBatch * kAccT * 4;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+__global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
+  extern __shared__ __align__(16) unsigned char acc_smem[];
+  int32_t(*stage)[kAccBatch][kAccT] = reinterpret_cast<int32_t(*)[kAccBatch][kAccT]>(acc_smem);
+  Term *terms = reinterpret_cast<Term *>(acc_smem + kAccStageBytes);
+  const int tid = threadIdx.x;
+  for (int x = tid; x < a.n_entries; x += blockDim.x) {
     const int e = a.order[x];
     const GroupEntry g = a.groups[e];
     const bool last = (x + 1 == a.n_entries) || (a.groups[a.order[x + 1]].q != g.q);
     terms[x] = Term{e, (int16_t)(last ? 8 * (a.Q - g.q) : -1), (int8_t)product_sign(a.method, 0, g.prod),
                     (int8_t)product_sign(a.method, 1, g.prod)};
   }
-  __syncthreads();
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = blockIdx.y;
-  if (j >= a.n || i >= a.m) return;
-  const int32_t Ei = a.E[i], Fj = a.F[j];
-  if (Ei == INT32_MIN || Fj == INT32_MIN) {   // a zero row or column: the product is exactly 0
-    const int64_t o = i * C.ld + j;
-    for (int c = 0; c < 2; ++c) store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+  const int64_t j0 = (int64_t)blockIdx.x * kAccT, j = j0 + tid;
+  const int32_t Ei = a.E[i];
+  if (Ei == INT32_MIN) {   // a zero row: the whole block's products are exactly 0 (block-uniform exit)
+    if (j < a.n) {
+      const int64_t o = i * C.ld + j;
+      for (int c = 0; c < 2; ++c) store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+    }
     return;
   }
+  const int32_t Fj = j < a.n ? a.F[j] : INT32_MIN;
+  const bool active = j < a.n && Fj != INT32_MIN;
   const int64_t mn = a.m * a.n;
-  const int32_t *col = a.planes + i * a.n + j;
+  const int32_t *row = a.planes + i * a.n + j0;
+  const int nrun = (int)(a.n - j0 < kAccT ? a.n - j0 : kAccT);   // valid elements of this block's run
+  const bool vec = (a.n & 3) == 0;
+  __syncthreads();   // the term table is complete
+  auto issue = [&](int x0, int buf) {
+    const int nb = a.n_entries - x0 < kAccBatch ? a.n_entries - x0 : kAccBatch;
+    if (vec) {
+      for (int q = tid; q < nb * (kAccT / 4); q += kAccT) {
+        const int g = q / (kAccT / 4), c4 = 4 * (q % (kAccT / 4));
+        const int valid = nrun - c4 >= 4 ? 4 : (nrun > c4 ? nrun - c4 : 0);
+        const int32_t *src = row + (int64_t)terms[x0 + g].plane * mn + (valid ? c4 : 0);
+        cp_async16(&stage[buf][g][c4], src, 4 * valid);   // bytes beyond `valid` are zero-filled
+      }
+    } else {
+      for (int q = tid; q < nb * kAccT; q += kAccT) {
+        const int g = q / kAccT, c = q % kAccT;
+        const int32_t *src = row + (int64_t)terms[x0 + g].plane * mn + (c < nrun ? c : 0);
+        cp_async4(&stage[buf][g][c], src, c < nrun ? 4 : 0);
+      }
+    }
+    cp_async_commit();
+  };
   uint32_t words[2][kMaxWords];
   Lazy acc[2];
   int64_t sum0 = 0, sum1 = 0;
-#pragma unroll 8
-  for (int x = 0; x < a.n_entries; ++x) {
-    const Term t = terms[x];
-    const int64_t v = (int64_t)__ldg(col + (int64_t)t.plane * mn);
-    sum0 += v * t.s0;
-    sum1 += v * t.s1;
-    if (t.shift >= 0) {
-      acc[0].add(words[0], sum0, t.shift);
-      acc[1].add(words[1], sum1, t.shift);
-      sum0 = sum1 = 0;
+  issue(0, 0);
+  for (int x0 = 0, buf = 0; x0 < a.n_entries; x0 += kAccBatch, buf ^= 1) {
+    if (x0 + kAccBatch < a.n_entries) issue(x0 + kAccBatch, buf ^ 1);
+    else cp_async_commit();   // an empty group keeps the wait count uniform
+    cp_async_wait1();
+    __syncthreads();
+    if (active) {
+      const int nb = a.n_entries - x0 < kAccBatch ? a.n_entries - x0 : kAccBatch;
+      for (int u = 0; u < nb; ++u) {
+        const Term t = terms[x0 + u];   // block-uniform: the branches below do not diverge
+        const int64_t v = stage[buf][u][tid];
+        if (t.s0 > 0) sum0 += v; else if (t.s0 < 0) sum0 -= v;
+        if (t.s1 > 0) sum1 += v; else if (t.s1 < 0) sum1 -= v;
+        if (t.shift >= 0) {
+          acc[0].add(words[0], sum0, t.shift);
+          acc[1].add(words[1], sum1, t.shift);
+          sum0 = sum1 = 0;
+        }
+      }
     }
+    __syncthreads();   // the buffer is free for the copy issued in the next iteration
+  }
+  if (j >= a.n) return;
+  if (!active) {   // a zero column
+    const int64_t o = i * C.ld + j;
+    for (int c = 0; c < 2; ++c) store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
+    return;
   }
   for (int c = 0; c < 2; ++c) finish_component(a, C, acc[c], words[c], c, i, j, Ei, Fj);
 }
@@ -338,9 +417,14 @@ void launch_group_table(const ProductDesc *prods, int n_products, int Q, int gma
 }
 
 void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st) {
-  const int T = 128;
-  dim3 g((unsigned)((a.n + T - 1) / T), (unsigned)a.m);
-  k_oz_accum<<<g, T, (size_t)a.n_entries * sizeof(Term), st>>>(a, C);
+  const size_t smem = kAccStageBytes + (size_t)a.n_entries * sizeof(Term);
+  static std::once_flag once;   // allow the largest table any plan can have, once per process
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_oz_accum, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kAccStageBytes + (size_t)kMaxGroupsTotal * sizeof(Term)));
+  });
+  dim3 g((unsigned)((a.n + kAccT - 1) / kAccT), (unsigned)a.m);
+  k_oz_accum<<<g, kAccT, smem, st>>>(a, C);
 }
 
 void launch_fallback(const FallbackArgs &f, const MatView &A, const MatView &B, const OutView &C, int blocks,

@@ -154,7 +154,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
     if (d.a_pos0 + d.b_pos0 < qmin) qmin = d.a_pos0 + d.b_pos0;
   }
   P.n_groups_total = total;
-  if (total > 6000) return MPC_EINVAL;       // the accumulate kernel's term table (48 KB of shared memory)
+  if (total > kMaxGroupsTotal) return MPC_EINVAL;   // the accumulate kernel's term table in shared memory
   P.acc_slots = (8 * (Q - qmin) + 64) / 32 + 3;
   if (P.acc_slots > 88) return MPC_EINVAL;   // the accumulate kernel's word budget
   // bounds: b = bound_drop[c] + k (lossyA * bound_lossy_a[c] + lossyB * bound_lossy_b[c]), times 2^beta
@@ -185,8 +185,8 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   off = align256(off + (uint64_t)total * m * n * 4);
   P.off_group_table = off;
   off = align256(off + (uint64_t)total * sizeof(GroupEntry));
-  P.off_group_order = off;
-  off = align256(off + (uint64_t)total * 4);
+  P.off_group_order = off;   // accumulation order, then the slice GEMM's schedule
+  off = align256(off + (uint64_t)total * 8);
   P.ws_bytes = off;
   P.launches = 9;     // init, row max, column max, group table, 2 x digits, slice GEMM, accumulate, fallback
   return MPC_OK;
@@ -313,6 +313,7 @@ SliceGemmArgs slice_args(const Call &c) {
   sa.n = c.n;
   sa.kpad = P.kpad;
   sa.groups = (const GroupEntry *)(c.ws + P.off_group_table);
+  sa.sched = (const int32_t *)(c.ws + P.off_group_order) + P.n_groups_total;
   sa.n_entries = P.n_groups_total;
   for (int x = 0; x < 4; ++x) sa.prod[x] = c.pl.prod[x];
   sa.out = (int32_t *)(c.ws + P.off_groups);

@@ -21,6 +21,8 @@ constexpr int kMaxLimbs = 16;          // p <= 1024
 // plain path: base-2^28 digits, D <= 40 at p <= 1024 (28 D - 2 >= p + 32, D a multiple of 4)
 constexpr int kPlainDigitBits = 28;
 constexpr int kMaxPlainDigits = 40;
+// group planes of one Ozaki call (the accumulate kernel keeps their table in shared memory)
+constexpr int kMaxGroupsTotal = 6000;
 // 64-bit limbs of an exact plain-path sum of k <= 2^17 digit products
 // (|sum| < k 2^(56 D - 1), plus the sign and the 3M combination)
 __host__ __device__ constexpr int plain_limbs(int D) { return (56 * D + 18 + 63) / 64; }

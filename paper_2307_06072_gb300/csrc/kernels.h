@@ -13,6 +13,7 @@ struct SliceGemmArgs {
   const __nv_bfloat16 *dB;      // digit planes of B: [plane][n][kpad]
   int64_t m, n, kpad;
   const GroupEntry *groups;     // group table (n_entries)
+  const int32_t *sched;         // order in which the groups' units are handed out (null: table order)
   int32_t n_entries;
   ProductDesc prod[4];
   int32_t *out;                 // group sums: [entry][m][n] int32

@@ -10,7 +10,9 @@
 // dynamically (a global counter): the producer takes the next unit index and
 // publishes it to the MMA and epilogue warps through a 4-slot shared ring, so
 // the units in flight on all SMs stay a contiguous window of the unit order
-// (group-major) and share the same digit planes in L2.
+// (group-major, groups of equal pair count next to each other, so that the
+// units in flight take equally long and stay in step) and share the same
+// digit planes in L2.
 //   warp 0      TMA producer: 64-element k-blocks of A (128 rows) and B (256
 //               rows) into a 4-stage shared-memory ring (128-byte swizzle).
 //   warp 1      TMEM owner (alloc 512 columns) and, on one lane, the MMA
@@ -59,6 +61,7 @@ struct TcProblem {
   int kbpp;            // k-blocks per pair (kpad / 64)
   int tiles_m, tiles_n, pad_;
   const GroupEntry *groups;
+  const int32_t *sched;   // unit order over the groups (null: table order)
   int32_t *out;
   ProductDesc prod[4];
 };
@@ -263,7 +266,7 @@ __device__ __forceinline__ Unit decode(const TcParams &P, int64_t u, uint32_t ra
   const int tiles_mu = (q.tiles_m + CL - 1) / CL;
   const int tiles = tiles_mu * q.tiles_n;
   x.prob = pi;
-  x.e = (int)(r / tiles);
+  x.e = q.sched ? q.sched[r / tiles] : (int)(r / tiles);
   const int t = (int)(r % tiles);
   x.tm = (t / q.tiles_n) * CL + (int)rank;
   x.tn = t % q.tiles_n;
@@ -564,6 +567,7 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
     t.tiles_n = (int)((a.n + BN - 1) / BN);
     t.unit0 = units;
     t.groups = a.groups;
+    t.sched = a.sched;
     t.out = a.out;
     for (int x = 0; x < 4; ++x) t.prod[x] = a.prod[x];
     units += (int64_t)a.n_entries * ((t.tiles_m + cluster - 1) / cluster) * t.tiles_n;
