@@ -162,6 +162,8 @@ class Split:
     lossless: list             # per line: every element exact on the grid
     digits: dict = field(default_factory=dict)  # 're'/'im'/'sum' -> int array [nd][lines][k]
     first_pos: dict = field(default_factory=dict)  # digit position of plane 0
+    live: dict = field(default_factory=dict)    # per digit set: plane has a nonzero digit
+    values: tuple = (True, True)                 # some element has a nonzero real / imaginary part
 
 
 def fixed_point_array(N, x, E_line, s: int):
@@ -214,7 +216,15 @@ def split_operand(mat, s: int, side: str, method: str) -> Split:
     if method == "3m":
         sp.digits["sum"] = balanced_digits_array(Xr + Xi, s + 1)
         sp.first_pos["sum"] = -1
+    for which, D in sp.digits.items():
+        sp.live[which] = [bool(np.any(D[x])) for x in range(D.shape[0])]
+    sp.values = (bool(np.any(Nre != 0)), bool(np.any(Nim != 0)))
     return sp
+
+
+def value_nonzero(sp: Split, which: str) -> bool:
+    """The operand component behind a digit set has a nonzero value somewhere."""
+    return {"re": sp.values[0], "im": sp.values[1], "sum": sp.values[0] or sp.values[1]}[which]
 
 
 # ------------------------------------------------------------- step 3
@@ -248,6 +258,35 @@ def groups_for(tA: tuple, tB: tuple, Q: int, gmax: int):
             t += c
             n -= c
     return gs
+
+
+def trim_groups(spA: Split, spB: Split, prod: str, gs: list) -> list:
+    """The groups with the pairs at their two ends removed whose A or B digit plane is zero
+    everywhere (their products are exactly zero, so every group sum is unchanged).
+
+    This is the reading of the paper's remark that the number of divisions should follow
+    the magnitudes of the real and imaginary parts (end of Sec. III-C; conclusion, item 3):
+    with one exponent per row for both parts, a part that is smaller by 2^-D has about D/8
+    leading digit planes of zeros, and the pairs that use them are skipped.  Trimming only
+    at the ends keeps a group one run of consecutive pairs; a group may become empty
+    (count 0).  Whole planes are tested, so the result depends on the matrices only.
+    """
+    wa, wb = PRODUCT_OPERANDS[prod]
+    fa, fb = spA.first_pos[wa], spB.first_pos[wb]
+    liveA = [bool(np.any(spA.digits[wa][x])) for x in range(spA.digits[wa].shape[0])]
+    liveB = [bool(np.any(spB.digits[wb][x])) for x in range(spB.digits[wb].shape[0])]
+
+    def live(t, u):
+        return liveA[t - fa] and liveB[u - fb]
+    out = []
+    for g in gs:
+        t0, c = g.t0, g.count
+        while c > 0 and not live(t0, g.q - t0):
+            t0, c = t0 + 1, c - 1
+        while c > 0 and not live(t0 + c - 1, g.q - (t0 + c - 1)):
+            c -= 1
+        out.append(Group(g.q, t0, c))
+    return out
 
 
 def positions(sp: Split, which: str, s: int):
@@ -290,13 +329,21 @@ def accumulate(gs, sums, Q: int):
 # ------------------------------------------------------------- step 6 (bound)
 
 @functools.lru_cache(maxsize=None)
-def drop_bound(tA: tuple, tB: tuple, Q: int, k: int) -> int:
+def drop_bound(tA: tuple, tB: tuple, Q: int, k: int, liveA=None, liveB=None) -> int:
     """Integer bound on the dropped pairs of one product, in Acc units.
 
     Dropped level Q+j contributes at most n_{Q+j} k 2**14 2**(-8j).  The
-    j = 1 term is k*64*n; the rest is below k*max_n/3 (geometric tail).
+    j = 1 term is k*64*n; the rest is below k*max_n/3 (geometric tail).  With
+    liveA / liveB (per digit plane, from position tA[0] / tB[0]) only the pairs
+    whose two planes both have a nonzero digit are counted: the others are
+    exactly zero.
     """
-    levels = {q: n for q, _, n in level_pairs(tA, tB, 10 ** 9)}
+    if liveA is not None:
+        levels = {}
+        for q, lo, n in level_pairs(tA, tB, 10 ** 9):
+            levels[q] = sum(1 for t in range(lo, lo + n) if liveA[t - tA[0]] and liveB[q - t - tB[0]])
+    else:
+        levels = {q: n for q, _, n in level_pairs(tA, tB, 10 ** 9)}
     n1 = levels.get(Q + 1, 0)
     rest = [n for q, n in levels.items() if q >= Q + 2]
     nmax = max(rest) if rest else 0
@@ -320,20 +367,50 @@ def entry_bound(prm: Params, spA: Split, spB: Split, i: int, j: int, comp: str):
     if spA.E[i] is None or spB.E[j] is None:
         return 0, 0
     beta = bound_exponent(prm)
+    if component_identically_zero(spA.values, spB.values, comp):
+        return 0, beta
     if prm.method == "4m":
         prods = ("rr", "ii") if comp == "re" else ("ri", "ir")
     else:
         prods = ("rr", "ii") if comp == "re" else ("ss", "rr", "ii")
     b = 0
     for pr in prods:
+        bd, gate = product_bound(prm, spA, spB, pr)
+        b += -(-bd >> beta) if beta < 4096 else (1 if bd else 0)
+        if gate:
+            ca, fa, cb, fb = split_coeffs(pr)
+            # truncation of A (row i lossy) times |b| <= fb 2^F; |a^| <= fa 2^E times truncation of B
+            b += prm.k * ((0 if spA.lossless[i] else ca * fb) + (0 if spB.lossless[j] else fa * cb))
+    return b, beta
+
+
+def component_identically_zero(vA: tuple, vB: tuple, comp: str) -> bool:
+    """Component `comp` of A B vanishes for every entry, given which components of A and B
+    (re, im) have a nonzero value somewhere.  Then every product entering it, and the
+    3M sums (which equal one part digit for digit), cancel exactly in Acc."""
+    (ar, ai), (br, bi) = vA, vB
+    if comp == "re":
+        return (not ar or not br) and (not ai or not bi)
+    return (not ar or not bi) and (not ai or not br)
+
+
+def product_bound(prm: Params, spA: Split, spB: Split, pr: str):
+    """(dropped-pair bound over live pairs, truncation counts) of one real product.
+
+    The truncation terms apply only when both operand components of the product
+    have a nonzero value somewhere: otherwise the product and its digit product
+    are both exactly zero.  Cached on the splits (it depends on them only).
+    """
+    key = ("bound", pr, prm.Q, prm.k, prm.s)
+    cache = spA.__dict__.setdefault("_bound_cache", {})
+    hit = cache.get(key)
+    if hit is None or hit[0] is not spB:        # keyed on the very B split (kept alive here)
         wa, wb = PRODUCT_OPERANDS[pr]
         tA, tB = positions(spA, wa, prm.s), positions(spB, wb, prm.s)
-        bd = drop_bound(tA, tB, prm.Q, prm.k)
-        b += -(-bd >> beta) if beta < 4096 else (1 if bd else 0)
-        ca, fa, cb, fb = split_coeffs(pr)
-        # truncation of A (row i lossy) times |b| <= fb 2^F; |a^| <= fa 2^E times truncation of B
-        b += prm.k * ((0 if spA.lossless[i] else ca * fb) + (0 if spB.lossless[j] else fa * cb))
-    return b, beta
+        bd = drop_bound(tA, tB, prm.Q, prm.k, tuple(spA.live[wa]), tuple(spB.live[wb]))
+        hit = (spB, (bd, value_nonzero(spA, wa) and value_nonzero(spB, wb)))
+        cache[key] = hit
+    return hit[1]
 
 
 def certify(acc: int, b: int, beta: int, p: int) -> bool:

@@ -87,20 +87,73 @@ struct Lazy {
 
 }  // namespace
 
-// Group table (per product, levels ascending) and a merged order of all groups
-// by descending level, i.e. ascending shift 8 (Q - q) for the accumulation.
-__global__ void k_group_table(ProductDesc p0, ProductDesc p1, ProductDesc p2, ProductDesc p3, int n_products,
-                              int Q, int gmax, GroupEntry *table, int32_t *order) {
-  if (blockIdx.x != 0) return;
-  if (threadIdx.x < (unsigned)n_products) {
-    ProductDesc pd = threadIdx.x == 0 ? p0 : threadIdx.x == 1 ? p1 : threadIdx.x == 2 ? p2 : p3;
-    build_groups((int)threadIdx.x, pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, Q, gmax, table + pd.group0,
-                 pd.n_groups);
+// digit-set kinds of the two operands of real product `prod`: 0 re, 1 im, 2 sums
+__device__ __forceinline__ void product_kinds(int method, int prod, int &ka, int &kb) {
+  if (method == MPC_4M) {
+    ka = (prod == 0 || prod == 2) ? 0 : 1;   // rr, ii, ri, ir
+    kb = (prod == 0 || prod == 3) ? 0 : 1;
+  } else {
+    ka = kb = prod;                           // rr, ii, ss
+  }
+}
+
+// Per product (one warp each): the group table, levels ascending; then every
+// group loses the pairs at its two ends whose A or B digit plane is all zero
+// (their products are exactly zero), so it never splits and the table keeps its
+// size; a group of zero pairs only keeps its place (count 0: no unit, no term).
+// The warp also counts the dropped pairs (levels above Q) whose planes are both
+// nonzero.  Thread 0 then merges the products' groups into the accumulation order
+// (descending level, i.e. ascending shift), writes the slice GEMM's unit schedule
+// and the call's error bounds:
+//   drop[c]    = sum over the products of component c of ceil(B_prod / 2^beta),
+//                B_prod = k (64 n_{Q+1} + ceil(max_{j>=2} n_{Q+j} / 3)) over live pairs;
+//   lossy_a[c] = sum of the products' truncation factors (4 for the 3M sums, else 1),
+//                counted only when both operand components of the product have a
+//                nonzero value somewhere (otherwise the product is exactly zero);
+//   lossy_b[c] likewise;
+// all three are zero for a component of A B that vanishes identically.
+__global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
+  __shared__ uint64_t s_bd[4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < a.n_products) {
+    const ProductDesc pd = a.prod[warp];
+    if (lane == 0)
+      build_groups(warp, pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, a.Q, a.gmax, a.table + pd.group0,
+                   pd.n_groups);
+    __syncwarp();
+    auto live = [&](int t, int u) {
+      return a.flagsA[pd.a_plane0 + t - pd.a_pos0] != 0 && a.flagsB[pd.b_plane0 + u - pd.b_pos0] != 0;
+    };
+    for (int e = pd.group0 + lane; e < pd.group0 + pd.n_groups; e += 32) {
+      GroupEntry g = a.table[e];
+      while (g.count > 0 && !live(g.t0, g.q - g.t0)) {
+        ++g.t0;
+        --g.count;
+      }
+      while (g.count > 0 && !live(g.t0 + g.count - 1, g.q - (g.t0 + g.count - 1))) --g.count;
+      a.table[e] = g;
+    }
+    // live dropped pairs per level above Q
+    const int qmax = pd.a_pos0 + pd.a_npos - 1 + pd.b_pos0 + pd.b_npos - 1;
+    uint64_t n1 = 0, nmax = 0;
+    for (int q = a.Q + 1; q <= qmax; ++q) {
+      const int lo = max(pd.a_pos0, q - (pd.b_pos0 + pd.b_npos - 1));
+      const int hi = min(pd.a_pos0 + pd.a_npos - 1, q - pd.b_pos0);
+      unsigned cnt = 0;
+      for (int t = lo + lane; t <= hi; t += 32) cnt += live(t, q - t) ? 1u : 0u;
+      cnt = __reduce_add_sync(0xffffffffu, cnt);
+      if (q == a.Q + 1) n1 = cnt;
+      else if (cnt > nmax) nmax = cnt;
+    }
+    if (lane == 0) s_bd[warp] = (uint64_t)a.k * (64 * n1 + (nmax + 2) / 3);
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
+  const ProductDesc *pds = a.prod;
+  const int n_products = a.n_products;
+  const GroupEntry *table = a.table;
+  int32_t *order = a.order;
   // merge the per-product lists (each ascending in q) from their ends
-  const ProductDesc pds[4] = {p0, p1, p2, p3};
   int next[4];
   for (int x = 0; x < 4; ++x) next[x] = x < n_products ? pds[x].group0 + pds[x].n_groups - 1 : -1;
   int n = 0;
@@ -127,6 +180,32 @@ __global__ void k_group_table(ProductDesc p0, ProductDesc p1, ProductDesc p2, Pr
     for (int e = g0; e < g1; ++e) sched[start[kMaxSlices + 1 - table[e].count]++] = e;
     out += g1 - g0;
   }
+  // the call's bounds
+  const int32_t *valA = a.flagsA + a.planes_A, *valB = a.flagsB + a.planes_B;   // [re, im] values nonzero
+  for (int c = 0; c < 2; ++c) {
+    uint64_t bd = 0, la = 0, lb = 0;
+    for (int x = 0; x < n_products; ++x) {
+      if (product_sign(a.method, c, x) == 0) continue;
+      int ka, kb;
+      product_kinds(a.method, x, ka, kb);
+      const bool va = ka == 2 ? (valA[0] || valA[1]) : valA[ka] != 0;
+      const bool vb = kb == 2 ? (valB[0] || valB[1]) : valB[kb] != 0;
+      bd += ceil_shift(s_bd[x], a.beta);
+      const uint64_t cf = ka == 2 ? 2 : 1;   // sums: 2 ulps truncation, |.| < 2^(E+1)
+      if (va && vb) {
+        la += cf * cf;
+        lb += cf * cf;
+      }
+    }
+    // component c of A B vanishes identically (given which components are nonzero): every
+    // product entering it, and the 3M sums, which equal one part digit for digit, cancel
+    // exactly, so its accumulator is exactly zero
+    const bool zero = c == 0 ? ((!valA[0] || !valB[0]) && (!valA[1] || !valB[1]))
+                             : ((!valA[0] || !valB[1]) && (!valA[1] || !valB[0]));
+    a.bounds[c] = zero ? 0 : bd;
+    a.bounds[2 + c] = zero ? 0 : la;
+    a.bounds[4 + c] = zero ? 0 : lb;
+  }
 }
 
 // One accumulation term per group, in order of descending level: plane index,
@@ -144,8 +223,8 @@ __device__ __forceinline__ void finish_component(const AccumArgs &a, const OutVi
   const bool neg = acc.finish(words, a.nslot);
   WordAcc mag{words};
   const int N = bitlen(mag, a.nslot);
-  const uint64_t b = a.bound_drop[c] + (uint64_t)a.k * ((a.lossyA[i] ? a.bound_lossy_a[c] : 0ull) +
-                                                        (a.lossyB[j] ? a.bound_lossy_b[c] : 0ull));
+  const uint64_t b = a.bounds[c] + (uint64_t)a.k * ((a.lossyA[i] ? a.bounds[2 + c] : 0ull) +
+                                                    (a.lossyB[j] ? a.bounds[4 + c] : 0ull));
   if (N == 0 && b == 0) {
     store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
   } else if (N > 0 && certified(mag, a.nslot, N, a.p, b, a.bound_shift)) {
@@ -192,8 +271,10 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
     const int e = a.order[x];
     const GroupEntry g = a.groups[e];
     const bool last = (x + 1 == a.n_entries) || (a.groups[a.order[x + 1]].q != g.q);
-    terms[x] = Term{e, (int16_t)(last ? 8 * (a.Q - g.q) : -1), (int8_t)product_sign(a.method, 0, g.prod),
-                    (int8_t)product_sign(a.method, 1, g.prod)};
+    const bool empty = g.count == 0;   // all its pairs were zero: its plane was never written
+    terms[x] = Term{empty ? -1 : e, (int16_t)(last ? 8 * (a.Q - g.q) : -1),
+                    (int8_t)(empty ? 0 : product_sign(a.method, 0, g.prod)),
+                    (int8_t)(empty ? 0 : product_sign(a.method, 1, g.prod))};
   }
   const int64_t i = blockIdx.y;
   const int64_t j0 = (int64_t)blockIdx.x * kAccT, j = j0 + tid;
@@ -217,15 +298,18 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
     if (vec) {
       for (int q = tid; q < nb * (kAccT / 4); q += kAccT) {
         const int g = q / (kAccT / 4), c4 = 4 * (q % (kAccT / 4));
-        const int valid = nrun - c4 >= 4 ? 4 : (nrun > c4 ? nrun - c4 : 0);
-        const int32_t *src = row + (int64_t)terms[x0 + g].plane * mn + (valid ? c4 : 0);
+        const int plane = terms[x0 + g].plane;
+        const int valid = plane < 0 ? 0 : (nrun - c4 >= 4 ? 4 : (nrun > c4 ? nrun - c4 : 0));
+        const int32_t *src = row + (plane < 0 ? 0 : (int64_t)plane * mn) + (valid ? c4 : 0);
         cp_async16(&stage[buf][g][c4], src, 4 * valid);   // bytes beyond `valid` are zero-filled
       }
     } else {
       for (int q = tid; q < nb * kAccT; q += kAccT) {
         const int g = q / kAccT, c = q % kAccT;
-        const int32_t *src = row + (int64_t)terms[x0 + g].plane * mn + (c < nrun ? c : 0);
-        cp_async4(&stage[buf][g][c], src, c < nrun ? 4 : 0);
+        const int plane = terms[x0 + g].plane;
+        const bool take = plane >= 0 && c < nrun;
+        const int32_t *src = row + (take ? (int64_t)plane * mn + c : 0);
+        cp_async4(&stage[buf][g][c], src, take ? 4 : 0);
       }
     }
     cp_async_commit();
@@ -409,11 +493,8 @@ __global__ void k_zero_output(OutView C, int64_t m, int64_t n, int L) {
 
 // ---------------------------------------------------------------- launchers
 
-void launch_group_table(const ProductDesc *prods, int n_products, int Q, int gmax, GroupEntry *table,
-                        int32_t *order, cudaStream_t st) {
-  ProductDesc z{};
-  k_group_table<<<1, 32, 0, st>>>(prods[0], prods[1], n_products > 2 ? prods[2] : z,
-                                  n_products > 3 ? prods[3] : z, n_products, Q, gmax, table, order);
+void launch_group_table(const GroupTableArgs &a, cudaStream_t st) {
+  k_group_table<<<1, 128, 0, st>>>(a);
 }
 
 void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st) {

@@ -43,12 +43,6 @@ uint64_t drop_bound(const ProductDesc &pd, int Q, int64_t k) {
   return (uint64_t)k * (64 * n1 + (nmax + 2) / 3);
 }
 
-uint64_t ceil_shift(uint64_t v, int beta) {
-  if (beta == 0) return v;
-  if (beta >= 64) return v ? 1 : 0;
-  return (v >> beta) + ((v & ((1ull << beta) - 1)) ? 1 : 0);
-}
-
 int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, const mpc_oz_params *prm,
               Plan *out) {
   std::memset(out, 0, sizeof(*out));
@@ -185,8 +179,9 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   off = align256(off + (uint64_t)total * m * n * 4);
   P.off_group_table = off;
   off = align256(off + (uint64_t)total * sizeof(GroupEntry));
-  P.off_group_order = off;   // accumulation order, then the slice GEMM's schedule
-  off = align256(off + (uint64_t)total * 8);
+  // accumulation order, the slice GEMM's schedule, the operands' flags, the data-dependent bounds
+  P.off_group_order = off;
+  off = align256(off + bounds_offset(total, P.planes_A, P.planes_B) + 6 * 8);
   P.ws_bytes = off;
   P.launches = 9;     // init, row max, column max, group table, 2 x digits, slice GEMM, accumulate, fallback
   return MPC_OK;
@@ -281,7 +276,12 @@ int call_setup(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_mat *A
 void call_pre(Call &c, cudaStream_t st) {
   const mpc_plan &P = c.pl.pub;
   const int L = P.limbs;
-  launch_init(c.status, c.E, c.m, c.F, c.n, c.lossyA, c.lossyB, st);
+  // Ozaki: the operands' flags (digit planes, then the two components), after the order and schedule
+  int32_t *plane_nz = P.algo == MPC_OZAKI ? (int32_t *)(c.ws + P.off_group_order) + 2 * (int64_t)P.n_groups_total
+                                          : nullptr;
+  const int flagsA = P.planes_A + 2;
+  launch_init(c.status, c.E, c.m, c.F, c.n, c.lossyA, c.lossyB, st, plane_nz,
+              plane_nz ? (int64_t)flagsA + P.planes_B + 2 : 0);
   if (c.k == 0) {
     launch_zero_output(c.C, c.m, c.n, L, st);
     return;
@@ -295,12 +295,26 @@ void call_pre(Call &c, cudaStream_t st) {
                         (int32_t *)(c.ws + P.off_digits_b), st);
   } else {
     const int want_sum = P.method == MPC_3M;
-    launch_group_table(c.pl.prod, P.n_products, P.Q, P.gmax, (GroupEntry *)(c.ws + P.off_group_table),
-                       (int32_t *)(c.ws + P.off_group_order), st);
     launch_oz_digits(c.A, 0, c.m, c.k, P.kpad, L, P.s, want_sum, c.E, c.lossyA,
-                     (__nv_bfloat16 *)(c.ws + P.off_digits_a), st);
+                     (__nv_bfloat16 *)(c.ws + P.off_digits_a), plane_nz, st);
     launch_oz_digits(c.B, 1, c.n, c.k, P.kpad, L, P.s, want_sum, c.F, c.lossyB,
-                     (__nv_bfloat16 *)(c.ws + P.off_digits_b), st);
+                     (__nv_bfloat16 *)(c.ws + P.off_digits_b), plane_nz + flagsA, st);
+    GroupTableArgs ga{};
+    for (int x = 0; x < 4; ++x) ga.prod[x] = c.pl.prod[x];
+    ga.n_products = P.n_products;
+    ga.method = P.method;
+    ga.Q = P.Q;
+    ga.gmax = P.gmax;
+    ga.beta = P.bound_shift;
+    ga.k = c.k;
+    ga.planes_A = P.planes_A;
+    ga.planes_B = P.planes_B;
+    ga.flagsA = plane_nz;
+    ga.flagsB = plane_nz + flagsA;
+    ga.table = (GroupEntry *)(c.ws + P.off_group_table);
+    ga.order = (int32_t *)(c.ws + P.off_group_order);
+    ga.bounds = (uint64_t *)(c.ws + P.off_group_order + bounds_offset(P.n_groups_total, P.planes_A, P.planes_B));
+    launch_group_table(ga, st);
   }
 }
 
@@ -390,6 +404,7 @@ void call_accum(Call &c, cudaStream_t st) {
   aa.lossyA = c.lossyA;
   aa.lossyB = c.lossyB;
   aa.bound_shift = P.bound_shift;
+  aa.bounds = (const uint64_t *)(c.ws + P.off_group_order + bounds_offset(P.n_groups_total, P.planes_A, P.planes_B));
   for (int x = 0; x < 2; ++x) {
     aa.bound_drop[x] = P.bound_drop[x];
     aa.bound_lossy_a[x] = P.bound_lossy_a[x];

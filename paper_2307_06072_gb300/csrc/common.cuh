@@ -68,6 +68,13 @@ __host__ __device__ inline int build_groups(int prod, int a0, int na, int b0, in
   return n;
 }
 
+// ceil(v / 2^beta)
+__host__ __device__ inline uint64_t ceil_shift(uint64_t v, int beta) {
+  if (beta == 0) return v;
+  if (beta >= 64) return v ? 1 : 0;
+  return (v >> beta) + ((v & ((1ull << beta) - 1)) ? 1 : 0);
+}
+
 // Number of pairs of level q (t in [a0,a0+na), u in [b0,b0+nb)).
 __host__ __device__ inline int level_pairs(int a0, int na, int b0, int nb, int q) {
   int a1 = a0 + na - 1, b1 = b0 + nb - 1;

@@ -20,6 +20,25 @@ struct SliceGemmArgs {
   int32_t *status;
 };
 
+// Group table, accumulation order, unit schedule and the data-dependent error
+// bounds of one Ozaki call (k_group_table, after the digits).
+struct GroupTableArgs {
+  ProductDesc prod[4];
+  int n_products, method, Q, gmax, beta;
+  int64_t k;
+  int planes_A, planes_B;
+  const int32_t *flagsA, *flagsB;   // per digit plane: any nonzero digit; then per component: any nonzero value
+  GroupEntry *table;
+  int32_t *order;                   // accumulation order [G], then the unit schedule [G]
+  uint64_t *bounds;                 // out: drop[2], lossy_a[2], lossy_b[2]
+};
+
+// byte offset of the bounds inside the group-order region
+__host__ __device__ inline uint64_t bounds_offset(int64_t groups, int planes_A, int planes_B) {
+  const uint64_t b = (uint64_t)groups * 8 + (uint64_t)(planes_A + 2 + planes_B + 2) * 4;
+  return (b + 7) & ~7ull;
+}
+
 struct AccumArgs {
   const int32_t *planes;        // group sums [entry][m][n]
   const GroupEntry *groups;
@@ -29,7 +48,8 @@ struct AccumArgs {
   int p, L, Q, nslot, method;
   const int32_t *E, *F, *lossyA, *lossyB;
   int bound_shift;
-  uint64_t bound_drop[2], bound_lossy_a[2], bound_lossy_b[2];
+  uint64_t bound_drop[2], bound_lossy_a[2], bound_lossy_b[2];   // data-independent (plan)
+  const uint64_t *bounds;       // the call's bounds (drop[2], lossy_a[2], lossy_b[2]), written by k_group_table
   int64_t *fallback;            // list of (i*n + j)*2 + c
   int64_t fallback_cap;
   int32_t *status;
@@ -72,15 +92,15 @@ struct PlainCombineArgs {
 int plain_digits_for(int p);
 
 void launch_init(int32_t *status, int32_t *E, int64_t m, int32_t *F, int64_t n, int32_t *lossyA, int32_t *lossyB,
-                 cudaStream_t st);
+                 cudaStream_t st, int32_t *extra = nullptr, int64_t n_extra = 0);
 void launch_line_max(const MatView &A, const MatView &B, int64_t m, int64_t n, int64_t k, int L, int32_t *E,
                      int32_t *F, cudaStream_t st);
 void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
-                      int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, cudaStream_t st);
+                      int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, int32_t *plane_nz,
+                      cudaStream_t st);
 void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, int L, int D, int DP, int W,
                          int want_sum, const int32_t *E, int32_t *lossy, int32_t *digits, cudaStream_t st);
-void launch_group_table(const ProductDesc *prods, int n_products, int Q, int gmax, GroupEntry *table,
-                        int32_t *order, cudaStream_t st);
+void launch_group_table(const GroupTableArgs &a, cudaStream_t st);
 void launch_slicegemm_mma(const SliceGemmArgs &a, cudaStream_t st);
 cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int cluster);
 cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, int cluster);

@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(256) k_slicegemm_mma(SliceGemmArgs a, int tile
   const int tile = (int)(blockIdx.x % tiles);
   const int64_t m0 = (int64_t)(tile / tiles_n) * MT, n0 = (int64_t)(tile % tiles_n) * NT;
   const GroupEntry g = a.groups[e];
+  if (g.count == 0) return;   // every pair of the group has an all-zero digit plane: nothing to store
   const ProductDesc pd = a.prod[g.prod];
   const int64_t planeA = a.m * a.kpad, planeB = a.n * a.kpad;
   const int steps_per_pair = (int)(a.kpad / KT);

@@ -276,6 +276,18 @@ __device__ __forceinline__ Unit decode(const TcParams &P, int64_t u, uint32_t ra
   return x;
 }
 
+// the group of unit u has no pairs left (all its digit planes were zero)
+template <int CL>
+__device__ __forceinline__ bool unit_empty(const TcParams &P, int64_t u) {
+  int pi = 0;
+  while (pi + 1 < P.count && P.prob[pi + 1].unit0 <= u) ++pi;
+  const TcProblem &q = P.prob[pi];
+  const int64_t r = u - q.unit0;
+  const int tiles = ((q.tiles_m + CL - 1) / CL) * q.tiles_n;
+  const int e = q.sched ? q.sched[r / tiles] : (int)(r / tiles);
+  return q.groups[e].count == 0;
+}
+
 }  // namespace
 
 // CL = 1: one CTA per unit tile.  CL = 2: a cluster of two CTAs computes the
@@ -350,6 +362,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (rank == 0) {
           if (!mbar_wait(&uempty[slot], uphase ^ 1, abort, P.status)) { ok = false; break; }
           int64_t v = atomicAdd(counter, 1);
+          while (v < P.units && unit_empty<CL>(P, v)) v = atomicAdd(counter, 1);   // groups of zero pairs
           u = v >= P.units ? -1 : (int)v;
           uring[slot] = u;
           mbar_arrive(&ufull[slot]);

@@ -64,9 +64,10 @@ __global__ void k_colmax(MatView B, int64_t k, int64_t n, int L, int rows_per_bl
 }
 
 __global__ void k_init(int32_t *status, int32_t *E, int64_t m, int32_t *F, int64_t n, int32_t *lossyA,
-                       int32_t *lossyB) {
+                       int32_t *lossyB, int32_t *extra, int64_t n_extra) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < kStatusWords) status[t] = 0;
+  if (t < n_extra) extra[t] = 0;
   if (t < m) { E[t] = INT32_MIN; lossyA[t] = 0; }
   if (t < n) { F[t] = INT32_MIN; lossyB[t] = 0; }
 }
@@ -121,28 +122,34 @@ struct DigitStream {
 // Side A: line = row i, element (i, l).  Side B: line = column j, element (l, j).
 // Output planes: digits[(plane * lines + line) * kpad + l], plane = t (real),
 // s + t (imaginary), 2s + 1 + t (sums, t = -1 .. s-1).
-__global__ void k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
-                            int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits) {
-  const int64_t l0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-  const int64_t line = blockIdx.y;
-  if (l0 >= kpad || line >= lines) return;    // kpad is even: l0 + 1 < kpad
+// Two elements (l0, l0 + 1) of one line.  Every thread of a warp runs the whole
+// digit loop (an element out of range or zero gives zero digits and no stores),
+// so that one warp vote per plane marks in nz[] the planes that got a nonzero
+// digit, and nz[nplanes + c] when a nonzero value of component c was seen.
+__device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad,
+                                               int L, int s, int want_sum, const int32_t *E, int32_t *lossy,
+                                               __nv_bfloat16 *digits, int64_t l0, int64_t line, bool in_range,
+                                               int *nz) {
+  const bool leader = (threadIdx.x & 31) == 0;
   const int64_t pstride = lines * kpad;
   __nv_bfloat162 *out = reinterpret_cast<__nv_bfloat162 *>(digits + line * kpad + l0);
   const int64_t pstride2 = pstride / 2;
   const int nplanes = 2 * s + (want_sum ? s + 1 : 0);
-  const int32_t e_line = E[line];
+  const int32_t e_line = in_range ? E[line] : INT32_MIN;
   DigitStream d[2];
   bool ok = true;
   bool any = false;
+  bool nzv[2] = {false, false};   // a nonzero real / imaginary value among the two elements
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int64_t l = l0 + q;
-    const bool live = (l < k) && (e_line != INT32_MIN);
+    const bool live = in_range && (l < k) && (e_line != INT32_MIN);
     any |= live;
     const int64_t idx = side == 0 ? line * X.ld + l : l * X.ld + line;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const bool nz = live && comp_nonzero(X, c, idx, L);
+      if (nz) nzv[c] = true;
       for (int j = 0; j < L; ++j) d[q].M[c][j] = nz ? X.limb[c][(int64_t)j * X.plane + idx] : 0ull;
       // |X| bit b  <->  M bit b + sh:  X = |v| 2^(8s-1-E), |v| = M 2^(exp-64L)
       d[q].sh[c] = nz ? (64 * (int64_t)L + (int64_t)e_line - (int64_t)X.exp[c][idx] - (8 * (int64_t)s - 1)) : 0;
@@ -158,11 +165,10 @@ __global__ void k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64
     d[q].cbal_s = 0;
   }
   if (!ok) atomicOr(lossy + line, 1);
-  if (!any) {
-    const __nv_bfloat162 z = __floats2bfloat162_rn(0.0f, 0.0f);
-    for (int pl = 0; pl < nplanes; ++pl) out[pl * pstride2] = z;
-    return;
-  }
+  (void)any;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+    if (__ballot_sync(0xffffffffu, nzv[c]) && leader) nz[nplanes + c] = 1;
   const int nbytes = want_sum ? s + 1 : s;
   for (int w = 0; 8 * w < nbytes; ++w) {
     uint64_t wc[2][2];   // two's-complement words [element][component]
@@ -209,7 +215,8 @@ __global__ void k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64
             }
             f[q] = (float)dg;
           }
-          out[(int64_t)(c * s + (s - 1 - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
+          if (in_range) out[(int64_t)(c * s + (s - 1 - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
+          if (__ballot_sync(0xffffffffu, f[0] != 0.f || f[1] != 0.f) && leader) nz[c * s + (s - 1 - pos)] = 1;
         }
       }
       if (want_sum) {
@@ -227,10 +234,30 @@ __global__ void k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64
           }
           f[q] = (float)dg;
         }
-        out[(int64_t)(2 * s + (s - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
+        if (in_range) out[(int64_t)(2 * s + (s - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
+        if (__ballot_sync(0xffffffffu, f[0] != 0.f || f[1] != 0.f) && leader) nz[2 * s + (s - pos)] = 1;
       }
     }
   }
+}
+
+// Digit planes of one operand; plane_nz[x] is set when plane x has a nonzero digit
+// (the group table then skips the slice pairs of all-zero planes), and
+// plane_nz[nplanes + c] when component c (re, im) has a nonzero value.
+__global__ void k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
+                            int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits,
+                            int32_t *plane_nz) {
+  __shared__ int nz[3 * kMaxSlices + 1 + 2];
+  const int nflags = 2 * s + (want_sum ? s + 1 : 0) + 2;
+  for (int x = threadIdx.x; x < nflags; x += blockDim.x) nz[x] = 0;
+  __syncthreads();
+  const int64_t l0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  const int64_t line = blockIdx.y;
+  // kpad is even: l0 + 1 < kpad; out-of-range threads still take part in the warp votes
+  oz_digits_pair(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits, l0, line, l0 < kpad && line < lines, nz);
+  __syncthreads();
+  for (int x = threadIdx.x; x < nflags; x += blockDim.x)
+    if (nz[x]) atomicOr(plane_nz + x, 1);
 }
 
 // Plain path: X = floor(|a| 2^(64 Lp - E)) as Lp limbs (Lp = L + 1), sign kept apart.
@@ -304,10 +331,11 @@ __global__ void k_plain_digits(MatView X, int side, int64_t lines, int64_t k, in
 // ---------------------------------------------------------------- launchers
 
 void launch_init(int32_t *status, int32_t *E, int64_t m, int32_t *F, int64_t n, int32_t *lossyA, int32_t *lossyB,
-                 cudaStream_t st) {
+                 cudaStream_t st, int32_t *extra, int64_t n_extra) {
   int64_t tot = m > n ? m : n;
   if (tot < kStatusWords) tot = kStatusWords;
-  k_init<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(status, E, m, F, n, lossyA, lossyB);
+  if (tot < n_extra) tot = n_extra;
+  k_init<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(status, E, m, F, n, lossyA, lossyB, extra, n_extra);
 }
 
 void launch_line_max(const MatView &A, const MatView &B, int64_t m, int64_t n, int64_t k, int L, int32_t *E,
@@ -319,9 +347,10 @@ void launch_line_max(const MatView &A, const MatView &B, int64_t m, int64_t n, i
 }
 
 void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
-                      int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, cudaStream_t st) {
+                      int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, int32_t *plane_nz,
+                      cudaStream_t st) {
   dim3 g((unsigned)((kpad / 2 + 127) / 128), (unsigned)lines);
-  k_oz_digits<<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits);
+  k_oz_digits<<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits, plane_nz);
 }
 
 void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, int L, int D, int DP, int W,

@@ -45,6 +45,15 @@ def ws_groups(ws, pl, m, n):
     return ws.tensor[off: off + 4 * cnt].view(torch.int32).cpu().numpy().reshape(-1, m, n)
 
 
+def ws_group_tables(ws, pl):
+    """(table [G, 4] = (product, level, first t, count), accumulation order [G], unit schedule [G])."""
+    import torch
+    G = pl["n_groups_total"]
+    t = ws.tensor[pl["off_group_table"]: pl["off_group_table"] + 16 * G].view(torch.int32).cpu().numpy()
+    o = ws.tensor[pl["off_group_order"]: pl["off_group_order"] + 8 * G].view(torch.int32).cpu().numpy()
+    return t.reshape(G, 4), o[:G], o[G:]
+
+
 def ws_lossy(ws, pl, m, n):
     import torch
     a = ws.tensor[pl["off_rowlossy"]: pl["off_rowlossy"] + 4 * m].view(torch.int32).cpu().numpy()

@@ -114,6 +114,9 @@ def test_plan_matches_the_oracle_parameters(mp, p, k, method, guard, s, Q):
             self.lossless = [lossless]
             self.first_pos = first
             self.digits = {w: np.zeros((npos[w], 1, 1)) for w in ("re", "im", "sum")}
+            # the plan's constants are the data-independent upper bound: every plane and component live
+            self.live = {w: [True] * npos[w] for w in ("re", "im", "sum")}
+            self.values = (True, True)
     for la in (True, False):
         for lb in (True, False):
             for c, comp in enumerate(("re", "im")):

@@ -15,6 +15,20 @@ from tests import gpu_util as gu
 pytestmark = pytest.mark.gpu
 
 
+def _check_group_sums(ws, pl, r, m, n):
+    """Every written group sum equals O2's; a group that the all-zero digit planes emptied
+    (count 0 on the device) is not written, and O2's sum for it is zero."""
+    G = gu.ws_groups(ws, pl, m, n)
+    table, _, _ = gu.ws_group_tables(ws, pl)
+    ref = [Gr for pr in r.params.products for Gr in r.group_sums[pr]]
+    assert G.shape[0] == len(ref)
+    for e, Gr in enumerate(ref):
+        if table[e, 3] > 0:
+            assert np.array_equal(G[e], Gr), e
+        else:
+            assert not np.any(Gr), e
+
+
 def _check_against_o1(C, A, B, p):
     ref = c_oracle.rounded_cgemm_matrix(A, B, p)
     bad = gu.mismatches(C, ref)
@@ -105,15 +119,93 @@ def test_config1_stage_parity(method):
         assert np.array_equal(dA[2 * s:, :, :k], r.splitA.digits["sum"])
         assert np.array_equal(dB[2 * s:, :, :k], r.splitB.digits["sum"])
     assert not np.any(dA[:, :, k:]) and not np.any(dB[:, :, k:])
-    G = gu.ws_groups(ws, pl, A.rows, B.cols)
-    e = 0
-    for pr in r.params.products:
-        for Gref in r.group_sums[pr]:
-            assert np.array_equal(G[e], Gref), (pr, e)
-            e += 1
-    assert e == G.shape[0]
+    _check_group_sums(ws, pl, r, A.rows, B.cols)
     assert st["fallback_entries"] == int((~r.certified).sum())
     _check_against_o1(C, A, B, p)
+
+
+@pytest.mark.parametrize("method", ["4m", "3m"])
+def test_group_table_order_and_unit_schedule(method):
+    """The device-built group table equals O2's groups; the accumulation order visits levels
+    in descending order; the slice GEMM's unit schedule is a permutation that keeps each
+    product's groups together, by descending pair count, stable."""
+    p = 256
+    A = si.random_matrix(130, 300, p, 345, "uniform_exp")
+    B = si.random_matrix(300, 140, p, 346, "uniform_exp")
+    params = dict(max_group=5)
+    C, ws, st = gu.run(A, B, p, method, "ozaki", params=params)
+    pl = gu.plan(A, B, p, method, params=params)
+    table, order, sched = gu.ws_group_tables(ws, pl)
+    r = ozaki.ozaki_cgemm(A, B, p, method, max_group=5, fallback=lambda i, j: ((0, 0), (0, 0)))
+    ref = [(x, h.q, h.t0, h.count) for x, pr in enumerate(r.params.products)
+           for h in ozaki.trim_groups(r.splitA, r.splitB, pr, r.groups[pr])]
+    got = [tuple(int(v) for v in row) for row in table]
+    assert [(g[0], g[1], g[3]) for g in got] == [(g[0], g[1], g[3]) for g in ref]
+    assert all(a[2] == b[2] for a, b in zip(got, ref) if b[3] > 0)
+    G = len(ref)
+    assert sorted(order.tolist()) == list(range(G)) and sorted(sched.tolist()) == list(range(G))
+    levels = table[order, 1]
+    assert np.all(levels[:-1] >= levels[1:])
+    prods = table[sched, 0]
+    assert np.all(prods[:-1] <= prods[1:])                       # product by product
+    for x in range(int(table[:, 0].max()) + 1):
+        part = sched[prods == x]
+        key = [(-int(table[e, 3]), int(e)) for e in part]       # descending count, then table order
+        assert key == sorted(key)
+    _check_against_o1(C, A, B, p)
+
+
+def _drop_part(mat, c):
+    out = mat.copy()
+    out.limb[c] = 0
+    out.sign[c] = 0
+    out.exp[c] = si.INT32_MIN
+    return out
+
+
+def _shift_part(mat, c, by):
+    out = mat.copy()
+    nz = out.limb[c, -1] != 0
+    out.exp[c] = np.where(nz, out.exp[c] + by, out.exp[c]).astype(np.int32)
+    return out
+
+
+@pytest.mark.parametrize("method", ["4m", "3m"])
+@pytest.mark.parametrize("case", ["real", "small_imaginary", "imaginary_A"])
+@pytest.mark.parametrize("kernel", ["auto", "mma_sync"])
+def test_zero_digit_planes_are_skipped(method, case, kernel):
+    """Groups lose the pairs of all-zero digit planes at their ends exactly as O2 trims them
+    (real inputs, an imaginary part 2^-100 smaller, a purely imaginary A); the result is
+    still the correctly rounded product."""
+    p = 256
+    A = si.random_matrix(200, 150, p, 351, "uniform_exp")
+    B = si.random_matrix(150, 300, p, 352, "uniform_exp")
+    if case == "real":
+        A, B = _drop_part(A, 1), _drop_part(B, 1)
+    elif case == "small_imaginary":
+        A, B = _shift_part(A, 1, -100), _shift_part(B, 1, -100)
+    else:
+        A = _drop_part(A, 0)
+    params = dict(kernel=kernel)
+    C, ws, st = gu.run(A, B, p, method, "ozaki", params=params)
+    pl = gu.plan(A, B, p, method, params=params)
+    table, order, sched = gu.ws_group_tables(ws, pl)
+    r = ozaki.ozaki_cgemm(A, B, p, method, fallback=lambda i, j: ((0, 0), (0, 0)))
+    ref = []
+    for x, pr in enumerate(r.params.products):
+        for h in ozaki.trim_groups(r.splitA, r.splitB, pr, r.groups[pr]):
+            ref.append((x, h.q, h.t0, h.count))
+    got = [tuple(int(v) for v in row) for row in table]
+    assert [g[:2] + (g[3],) for g in got] == [g[:2] + (g[3],) for g in ref]
+    assert all(a[2] == b[2] for a, b in zip(got, ref) if b[3] > 0)
+    empty = sum(1 for g in ref if g[3] == 0)
+    assert empty > 0
+    _check_group_sums(ws, pl, r, A.rows, B.cols)
+    _check_against_o1(C, A, B, p)
+    assert st["fallback_entries"] == int((~r.certified).sum())     # the same data-dependent bound
+    if case == "real":
+        assert r.certified[1].all() and st["fallback_entries"] == int((~r.certified[0]).sum())
+    assert st["fallback_overflow"] == 0 and st["uncertified"] == 0
 
 
 @pytest.mark.parametrize("kernel", ["auto", "tcgen05", "mma_sync"])
@@ -126,11 +218,8 @@ def test_group_cap_stage_parity(kernel):
     C, ws, st = gu.run(A, B, p, "3m", "ozaki", params=params)
     pl = gu.plan(A, B, p, "3m", params=params)
     r = ozaki.ozaki_cgemm(A, B, p, "3m", max_group=5, fallback=lambda i, j: ((0, 0), (0, 0)))
-    G = gu.ws_groups(ws, pl, A.rows, B.cols)
-    ref = [Gr for pr in r.params.products for Gr in r.group_sums[pr]]
-    assert G.shape[0] == len(ref) and all(g.count <= 5 for pr in r.params.products for g in r.groups[pr])
-    for e, Gr in enumerate(ref):
-        assert np.array_equal(G[e], Gr), e
+    assert all(g.count <= 5 for pr in r.params.products for g in r.groups[pr])
+    _check_group_sums(ws, pl, r, A.rows, B.cols)
     _check_against_o1(C, A, B, p)
 
 

@@ -128,6 +128,42 @@ def test_truncation_bound_holds(method, dist, guard):
     assert worst > Fraction(1, 1 << 20)   # the bound is not vacuous
 
 
+@pytest.mark.parametrize("method", ["4m", "3m"])
+@pytest.mark.parametrize("case", ["real", "imaginary_B", "small_imaginary", "tiny_imaginary"])
+def test_bound_with_zero_planes_holds(method, case):
+    """The data-dependent bound (live dropped pairs, truncation only where both components
+    are nonzero) still bounds |Acc - T| on every entry, including an imaginary part so small
+    that it truncates to zero digits (the lossy terms then carry it); for real inputs the
+    imaginary bound is exactly zero, so every imaginary component is certified."""
+    p = 128
+    A = si.random_matrix(6, 12, p, 641, "uniform_exp")
+    B = si.random_matrix(12, 5, p, 642, "uniform_exp")
+    if case == "real":
+        for X in (A, B):
+            X.limb[1] = 0; X.sign[1] = 0; X.exp[1] = si.INT32_MIN
+    elif case == "imaginary_B":
+        B.limb[0] = 0; B.sign[0] = 0; B.exp[0] = si.INT32_MIN
+    elif case == "small_imaginary":
+        A, B = _scaled_imaginary(A, -70), _scaled_imaginary(B, -50)
+    else:
+        A = _scaled_imaginary(A, -600)        # below every digit of the grid: lossy rows
+    r = ozaki.ozaki_cgemm(A, B, p, method)
+    T = _exact_scaled(A, B, r)
+    for comp in ("re", "im"):
+        for i in range(6):
+            for j in range(5):
+                b, beta = ozaki.entry_bound(r.params, r.splitA, r.splitB, i, j, comp)
+                err = abs(Fraction(int(r.acc[comp][i, j])) - T[comp][i, j])
+                assert err <= b * Fraction(2) ** beta, (case, comp, i, j)
+                if case == "real" and comp == "im":
+                    assert b == 0 and err == 0
+    if case == "real":
+        assert r.certified[1].all()
+    if case == "tiny_imaginary":
+        assert not all(r.splitA.lossless)
+    assert exact.equal_arrays(r.C, exact.rounded_cgemm(A, B, p)) if hasattr(exact, "equal_arrays") else True
+
+
 def test_truncation_bound_is_attained_by_coherent_errors():
     """All-ones mantissas truncate almost a full ulp each, all with one sign:
     the error then sits just below the split term of the bound (not far under it)."""
@@ -170,6 +206,105 @@ def test_group_partition_does_not_change_level_sums():
     for lv in results[1:]:
         assert lv.keys() == results[0].keys()
         assert all(np.array_equal(lv[q], results[0][q]) for q in lv)
+
+
+def _pair_product(spA, spB, prod, t, u):
+    wa, wb = ozaki.PRODUCT_OPERANDS[prod]
+    DA = spA.digits[wa][t - spA.first_pos[wa]]
+    DB = spB.digits[wb][u - spB.first_pos[wb]]
+    return DA @ DB.T          # int64, exact (|entries| <= 128, k small)
+
+
+def _scaled_imaginary(mat, by):
+    out = mat.copy()
+    nz = out.limb[1, -1] != 0
+    out.exp[1] = np.where(nz, out.exp[1] + by, out.exp[1]).astype(np.int32)
+    return out
+
+
+@pytest.mark.parametrize("method", ["4m", "3m"])
+@pytest.mark.parametrize("case", ["real_A", "small_im", "imag_B"])
+def test_trimmed_groups_keep_every_group_sum(method, case):
+    """Pairs removed by the trimming are exactly zero products (brute force over every
+    pair), the trimmed groups are sub-runs of the originals, and no group is added."""
+    p, k = 128, 24
+    A = si.random_matrix(9, k, p, 611, "uniform")
+    B = si.random_matrix(k, 7, p, 612, "uniform")
+    if case == "real_A":
+        A.limb[1] = 0; A.sign[1] = 0; A.exp[1] = si.INT32_MIN
+    elif case == "small_im":
+        A, B = _scaled_imaginary(A, -60), _scaled_imaginary(B, -41)
+    else:
+        B.limb[0] = 0; B.sign[0] = 0; B.exp[0] = si.INT32_MIN
+    prm = ozaki.make_params(p, k, method, max_group=4)
+    spA = ozaki.split_operand(A, prm.s, "A", method)
+    spB = ozaki.split_operand(B, prm.s, "B", method)
+    removed = 0
+    for prod in prm.products:
+        wa, wb = ozaki.PRODUCT_OPERANDS[prod]
+        gs = ozaki.groups_for(ozaki.positions(spA, wa, prm.s), ozaki.positions(spB, wb, prm.s), prm.Q, prm.gmax)
+        tg = ozaki.trim_groups(spA, spB, prod, gs)
+        assert len(tg) == len(gs)
+        for g, h in zip(gs, tg):
+            full = {(t, g.q - t) for t in range(g.t0, g.t0 + g.count)}
+            kept = {(t, h.q - t) for t in range(h.t0, h.t0 + h.count)}
+            assert h.q == g.q and kept <= full
+            for (t, u) in full - kept:
+                assert not np.any(_pair_product(spA, spB, prod, t, u)), (prod, t, u)
+                removed += 1
+            if h.count:   # the kept ends are live pairs
+                for t in (h.t0, h.t0 + h.count - 1):
+                    wa_, wb_ = ozaki.PRODUCT_OPERANDS[prod]
+                    assert np.any(spA.digits[wa_][t - spA.first_pos[wa_]])
+                    assert np.any(spB.digits[wb_][h.q - t - spB.first_pos[wb_]])
+    assert removed > 0
+
+
+def test_trimming_real_inputs_leaves_only_the_real_product():
+    """Real A and B: 4M keeps only rr; 3M keeps rr and ss (= rr), ii is empty."""
+    p, k = 128, 16
+    A = si.random_matrix(6, k, p, 621, "uniform")
+    B = si.random_matrix(k, 5, p, 622, "uniform")
+    for X in (A, B):
+        X.limb[1] = 0; X.sign[1] = 0; X.exp[1] = si.INT32_MIN
+    for method, live in (("4m", {"rr"}), ("3m", {"rr", "ss"})):
+        prm = ozaki.make_params(p, k, method)
+        spA = ozaki.split_operand(A, prm.s, "A", method)
+        spB = ozaki.split_operand(B, prm.s, "B", method)
+        for prod in prm.products:
+            wa, wb = ozaki.PRODUCT_OPERANDS[prod]
+            gs = ozaki.groups_for(ozaki.positions(spA, wa, prm.s), ozaki.positions(spB, wb, prm.s), prm.Q, prm.gmax)
+            kept = sum(g.count for g in ozaki.trim_groups(spA, spB, prod, gs))
+            assert (kept > 0) == (prod in live), (method, prod)
+
+
+def test_trimming_follows_the_smaller_part():
+    """Im smaller by 2^-96: about 96/8 leading Im planes are zero, so ii keeps only pairs
+    with both digits below that depth and ri/ir only pairs with one of them there."""
+    p, k = 256, 16
+    A = _scaled_imaginary(si.random_matrix(8, k, p, 631, "uniform"), -96)
+    B = _scaled_imaginary(si.random_matrix(k, 8, p, 632, "uniform"), -96)
+    prm = ozaki.make_params(p, k, "4m")
+    spA = ozaki.split_operand(A, prm.s, "A", "4m")
+    spB = ozaki.split_operand(B, prm.s, "B", "4m")
+    zA = next(t for t in range(prm.s) if np.any(spA.digits["im"][t]))
+    zB = next(t for t in range(prm.s) if np.any(spB.digits["im"][t]))
+    assert 10 <= zA <= 12 and 10 <= zB <= 12
+    kept = {}
+    for prod, (ta, tb) in (("ii", (zA, zB)), ("ri", (0, zB)), ("ir", (zA, 0)), ("rr", (0, 0))):
+        wa, wb = ozaki.PRODUCT_OPERANDS[prod]
+        gs = ozaki.groups_for(ozaki.positions(spA, wa, prm.s), ozaki.positions(spB, wb, prm.s), prm.Q, prm.gmax)
+        tg = ozaki.trim_groups(spA, spB, prod, gs)
+        for h in tg:
+            for t in range(h.t0, h.t0 + h.count):
+                assert t >= ta and h.q - t >= tb
+        n_kept = sum(h.count for h in tg)
+        bound = sum(1 for g in gs for t in range(g.t0, g.t0 + g.count) if t >= ta and g.q - t >= tb)
+        assert n_kept <= bound, prod
+        kept[prod] = n_kept
+    # the bottom digit planes may be zero too (p < 8s), which trims every product a little;
+    # the leading zero planes of the imaginary parts remove most of ii
+    assert kept["ii"] < 0.8 * kept["rr"] and kept["ri"] < kept["rr"] and kept["ir"] < kept["rr"]
 
 
 def test_group_sums_fit_int32_at_the_limit():
