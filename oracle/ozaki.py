@@ -260,7 +260,18 @@ def groups_for(tA: tuple, tB: tuple, Q: int, gmax: int):
     return gs
 
 
-def trim_groups(spA: Split, spB: Split, prod: str, gs: list) -> list:
+PRODUCT_COMPONENTS = {"4m": {"rr": ("re",), "ii": ("re",), "ri": ("im",), "ir": ("im",)},
+                      "3m": {"rr": ("re", "im"), "ii": ("re", "im"), "ss": ("im",)}}
+
+
+def product_needed(spA: Split, spB: Split, prod: str, method: str) -> bool:
+    """False when every component the product enters vanishes identically (e.g. the 3M
+    sums for real inputs): then all of its groups are emptied."""
+    return any(not component_identically_zero(spA.values, spB.values, c)
+               for c in PRODUCT_COMPONENTS[method][prod])
+
+
+def trim_groups(spA: Split, spB: Split, prod: str, gs: list, method: str = None) -> list:
     """The groups with the pairs at their two ends removed whose A or B digit plane is zero
     everywhere (their products are exactly zero, so every group sum is unchanged).
 
@@ -270,14 +281,18 @@ def trim_groups(spA: Split, spB: Split, prod: str, gs: list) -> list:
     leading digit planes of zeros, and the pairs that use them are skipped.  Trimming only
     at the ends keeps a group one run of consecutive pairs; a group may become empty
     (count 0).  Whole planes are tested, so the result depends on the matrices only.
+    With the method given, a product whose components all vanish identically
+    (``product_needed``) loses every pair.
     """
     wa, wb = PRODUCT_OPERANDS[prod]
     fa, fb = spA.first_pos[wa], spB.first_pos[wb]
     liveA = [bool(np.any(spA.digits[wa][x])) for x in range(spA.digits[wa].shape[0])]
     liveB = [bool(np.any(spB.digits[wb][x])) for x in range(spB.digits[wb].shape[0])]
 
+    needed = method is None or product_needed(spA, spB, prod, method)
+
     def live(t, u):
-        return liveA[t - fa] and liveB[u - fb]
+        return needed and liveA[t - fa] and liveB[u - fb]
     out = []
     for g in gs:
         t0, c = g.t0, g.count

@@ -87,6 +87,12 @@ struct Lazy {
 
 }  // namespace
 
+// Component c of A B vanishes for every entry, given which components (re, im) of A
+// and B have a nonzero value somewhere.
+__device__ __forceinline__ bool component_zero(const int32_t *vA, const int32_t *vB, int c) {
+  return c == 0 ? ((!vA[0] || !vB[0]) && (!vA[1] || !vB[1])) : ((!vA[0] || !vB[1]) && (!vA[1] || !vB[0]));
+}
+
 // digit-set kinds of the two operands of real product `prod`: 0 re, 1 im, 2 sums
 __device__ __forceinline__ void product_kinds(int method, int prod, int &ka, int &kb) {
   if (method == MPC_4M) {
@@ -111,7 +117,9 @@ __device__ __forceinline__ void product_kinds(int method, int prod, int &ka, int
 //                counted only when both operand components of the product have a
 //                nonzero value somewhere (otherwise the product is exactly zero);
 //   lossy_b[c] likewise;
-// all three are zero for a component of A B that vanishes identically.
+// all three are zero for a component of A B that vanishes identically, and
+// zero[c] (bounds[6 + c]) tells the accumulation to add nothing into it: a product
+// needed only there (the 3M sums for real inputs) was emptied.
 __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
   __shared__ uint64_t s_bd[4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -121,8 +129,14 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
       build_groups(warp, pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, a.Q, a.gmax, a.table + pd.group0,
                    pd.n_groups);
     __syncwarp();
+    // a product that enters only components of A B that vanish identically is not needed
+    // (the 3M sums for real or purely imaginary inputs): all its groups are emptied
+    const int32_t *vA = a.flagsA + a.planes_A, *vB = a.flagsB + a.planes_B;
+    bool needed = false;
+    for (int c = 0; c < 2; ++c)
+      if (product_sign(a.method, c, warp) != 0 && !component_zero(vA, vB, c)) needed = true;
     auto live = [&](int t, int u) {
-      return a.flagsA[pd.a_plane0 + t - pd.a_pos0] != 0 && a.flagsB[pd.b_plane0 + u - pd.b_pos0] != 0;
+      return needed && a.flagsA[pd.a_plane0 + t - pd.a_pos0] != 0 && a.flagsB[pd.b_plane0 + u - pd.b_pos0] != 0;
     };
     for (int e = pd.group0 + lane; e < pd.group0 + pd.n_groups; e += 32) {
       GroupEntry g = a.table[e];
@@ -200,11 +214,11 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
     // component c of A B vanishes identically (given which components are nonzero): every
     // product entering it, and the 3M sums, which equal one part digit for digit, cancel
     // exactly, so its accumulator is exactly zero
-    const bool zero = c == 0 ? ((!valA[0] || !valB[0]) && (!valA[1] || !valB[1]))
-                             : ((!valA[0] || !valB[1]) && (!valA[1] || !valB[0]));
+    const bool zero = component_zero(valA, valB, c);
     a.bounds[c] = zero ? 0 : bd;
     a.bounds[2 + c] = zero ? 0 : la;
     a.bounds[4 + c] = zero ? 0 : lb;
+    a.bounds[6 + c] = zero ? 1 : 0;   // the accumulation adds nothing into this component
   }
 }
 
@@ -272,9 +286,10 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
     const GroupEntry g = a.groups[e];
     const bool last = (x + 1 == a.n_entries) || (a.groups[a.order[x + 1]].q != g.q);
     const bool empty = g.count == 0;   // all its pairs were zero: its plane was never written
+    const bool z0 = a.bounds[6] != 0, z1 = a.bounds[7] != 0;   // components that vanish identically
     terms[x] = Term{empty ? -1 : e, (int16_t)(last ? 8 * (a.Q - g.q) : -1),
-                    (int8_t)(empty ? 0 : product_sign(a.method, 0, g.prod)),
-                    (int8_t)(empty ? 0 : product_sign(a.method, 1, g.prod))};
+                    (int8_t)(empty || z0 ? 0 : product_sign(a.method, 0, g.prod)),
+                    (int8_t)(empty || z1 ? 0 : product_sign(a.method, 1, g.prod))};
   }
   const int64_t i = blockIdx.y;
   const int64_t j0 = (int64_t)blockIdx.x * kAccT, j = j0 + tid;

@@ -181,7 +181,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   off = align256(off + (uint64_t)total * sizeof(GroupEntry));
   // accumulation order, the slice GEMM's schedule, the operands' flags, the data-dependent bounds
   P.off_group_order = off;
-  off = align256(off + bounds_offset(total, P.planes_A, P.planes_B) + 6 * 8);
+  off = align256(off + bounds_offset(total, P.planes_A, P.planes_B) + 8 * 8);
   P.ws_bytes = off;
   P.launches = 9;     // init, row max, column max, group table, 2 x digits, slice GEMM, accumulate, fallback
   return MPC_OK;

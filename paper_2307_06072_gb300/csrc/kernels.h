@@ -30,7 +30,7 @@ struct GroupTableArgs {
   const int32_t *flagsA, *flagsB;   // per digit plane: any nonzero digit; then per component: any nonzero value
   GroupEntry *table;
   int32_t *order;                   // accumulation order [G], then the unit schedule [G]
-  uint64_t *bounds;                 // out: drop[2], lossy_a[2], lossy_b[2]
+  uint64_t *bounds;                 // out: drop[2], lossy_a[2], lossy_b[2], zero[2]
 };
 
 // byte offset of the bounds inside the group-order region
@@ -49,7 +49,7 @@ struct AccumArgs {
   const int32_t *E, *F, *lossyA, *lossyB;
   int bound_shift;
   uint64_t bound_drop[2], bound_lossy_a[2], bound_lossy_b[2];   // data-independent (plan)
-  const uint64_t *bounds;       // the call's bounds (drop[2], lossy_a[2], lossy_b[2]), written by k_group_table
+  const uint64_t *bounds;       // the call's bounds (drop[2], lossy_a[2], lossy_b[2], zero[2]), from k_group_table
   int64_t *fallback;            // list of (i*n + j)*2 + c
   int64_t fallback_cap;
   int32_t *status;

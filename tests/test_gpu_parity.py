@@ -17,16 +17,22 @@ pytestmark = pytest.mark.gpu
 
 def _check_group_sums(ws, pl, r, m, n):
     """Every written group sum equals O2's; a group that the all-zero digit planes emptied
-    (count 0 on the device) is not written, and O2's sum for it is zero."""
+    (count 0 on the device) is not written, and O2's sum for it is zero; a product that
+    enters only components vanishing identically has every group emptied."""
     G = gu.ws_groups(ws, pl, m, n)
     table, _, _ = gu.ws_group_tables(ws, pl)
-    ref = [Gr for pr in r.params.products for Gr in r.group_sums[pr]]
-    assert G.shape[0] == len(ref)
-    for e, Gr in enumerate(ref):
-        if table[e, 3] > 0:
-            assert np.array_equal(G[e], Gr), e
-        else:
-            assert not np.any(Gr), e
+    e = 0
+    for pr in r.params.products:
+        needed = ozaki.product_needed(r.splitA, r.splitB, pr, r.params.method)
+        for Gr in r.group_sums[pr]:
+            if not needed:
+                assert table[e, 3] == 0, (pr, e)
+            elif table[e, 3] > 0:
+                assert np.array_equal(G[e], Gr), (pr, e)
+            else:
+                assert not np.any(Gr), (pr, e)
+            e += 1
+    assert e == G.shape[0]
 
 
 def _check_against_o1(C, A, B, p):
@@ -138,7 +144,7 @@ def test_group_table_order_and_unit_schedule(method):
     table, order, sched = gu.ws_group_tables(ws, pl)
     r = ozaki.ozaki_cgemm(A, B, p, method, max_group=5, fallback=lambda i, j: ((0, 0), (0, 0)))
     ref = [(x, h.q, h.t0, h.count) for x, pr in enumerate(r.params.products)
-           for h in ozaki.trim_groups(r.splitA, r.splitB, pr, r.groups[pr])]
+           for h in ozaki.trim_groups(r.splitA, r.splitB, pr, r.groups[pr], method)]
     got = [tuple(int(v) for v in row) for row in table]
     assert [(g[0], g[1], g[3]) for g in got] == [(g[0], g[1], g[3]) for g in ref]
     assert all(a[2] == b[2] for a, b in zip(got, ref) if b[3] > 0)
@@ -193,7 +199,7 @@ def test_zero_digit_planes_are_skipped(method, case, kernel):
     r = ozaki.ozaki_cgemm(A, B, p, method, fallback=lambda i, j: ((0, 0), (0, 0)))
     ref = []
     for x, pr in enumerate(r.params.products):
-        for h in ozaki.trim_groups(r.splitA, r.splitB, pr, r.groups[pr]):
+        for h in ozaki.trim_groups(r.splitA, r.splitB, pr, r.groups[pr], method):
             ref.append((x, h.q, h.t0, h.count))
     got = [tuple(int(v) for v in row) for row in table]
     assert [g[:2] + (g[3],) for g in got] == [g[:2] + (g[3],) for g in ref]

@@ -261,7 +261,8 @@ def test_trimmed_groups_keep_every_group_sum(method, case):
 
 
 def test_trimming_real_inputs_leaves_only_the_real_product():
-    """Real A and B: 4M keeps only rr; 3M keeps rr and ss (= rr), ii is empty."""
+    """Real A and B: by the digit planes alone 4M keeps only rr and 3M keeps rr and ss
+    (= rr); with the method given, ss is not needed either (Im vanishes identically)."""
     p, k = 128, 16
     A = si.random_matrix(6, k, p, 621, "uniform")
     B = si.random_matrix(k, 5, p, 622, "uniform")
@@ -276,6 +277,9 @@ def test_trimming_real_inputs_leaves_only_the_real_product():
             gs = ozaki.groups_for(ozaki.positions(spA, wa, prm.s), ozaki.positions(spB, wb, prm.s), prm.Q, prm.gmax)
             kept = sum(g.count for g in ozaki.trim_groups(spA, spB, prod, gs))
             assert (kept > 0) == (prod in live), (method, prod)
+            kept_m = sum(g.count for g in ozaki.trim_groups(spA, spB, prod, gs, method))
+            assert (kept_m > 0) == (prod == "rr"), (method, prod)
+            assert ozaki.product_needed(spA, spB, prod, method) == (prod in ("rr", "ii"))
 
 
 def test_trimming_follows_the_smaller_part():
