@@ -200,6 +200,25 @@ def run_serving(mp, torch, dev, seed: int = si.SEED_BASE + 5, count: int = 40):
     return out
 
 
+def hbm_stage_rooflines(pl, m, n, k, stages, hbm_gbs, src):
+    """Split and accumulate stages: algorithmic bytes / stage event time.
+
+    split: read every element's limbs, sign and exponent (2 components, 8L + 5 B each) of
+    A and B; write every digit plane (bf16) of both operands.  accumulate: read every
+    group sum (int32) once; write C (2 components, 8L + 5 B each)."""
+    L = pl["limbs"]
+    elem = 2 * (8 * L + 5)
+    split_bytes = (m * k + k * n) * elem + (pl["planes_A"] * m + pl["planes_B"] * n) * pl["kpad"] * 2
+    acc_bytes = pl["n_groups_total"] * m * n * 4 + m * n * elem
+    out = {}
+    for name, nbytes, ms in (("split", split_bytes, stages[0]), ("accumulate_round", acc_bytes, stages[2])):
+        gbs = nbytes / (ms / 1e3) / 1e9
+        out[name] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
+                     "frac": round(gbs / hbm_gbs, 4), "algorithmic_bytes": nbytes, "stage_ms": round(ms, 3),
+                     "peak_source": f"hbm_gbs ({src})"}
+    return out
+
+
 # Plain path roof: 64 IMAD lanes per clock per SM, two lane-operations (low and high
 # word) per 32 x 32 -> 64-bit digit product, 152 SMs at the 2070 MHz maximum SM clock.
 PLAIN_PRODUCTS_PER_CLK_SM = 32
@@ -425,6 +444,8 @@ def run_ours(args):
                 "algorithmic_flops_per_launch": flops, "kernel_ms": round(gemm_ms, 3)}
     if algo == "plain":
         roofline = plain_roofline(mp, m, n, k, p, method, gemm_ms)
+    else:   # the HBM-bound stages around the slice GEMM, against the measured copy bandwidth
+        extras["hbm_stages"] = hbm_stage_rooflines(pl, m, n, k, stages, float(peaks["hbm_gbs"]), peak_src)
 
     # e2e through the public API with host buffers: every step copies its inputs from
     # pinned host memory and its result back, inside the timed region.  Two device

@@ -262,7 +262,7 @@ __device__ __forceinline__ void finish_component(const AccumArgs &a, const OutVi
 // of one group plane (16-byte copies when n is a multiple of 4).  The groups of
 // one level are summed in plain int64 (|sum| < 2^36) and folded into the exact
 // accumulators once per level.
-constexpr int kAccT = 256, kAccBatch = 32;
+constexpr int kAccT = 256, kAccBatch = 16;
 constexpr size_t kAccStageBytes = 2ull * kAccBatch * kAccT * 4;
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
