@@ -88,8 +88,12 @@ typedef struct mpc_mat {
  * Optional tuning of the Ozaki path (Alg. 2's number of divisions d and pair
  * triangle).  Zero-initialise and set what you need; a zeroed struct (or a
  * NULL pointer) means the defaults.
- *   guard_bits  extra fixed-point bits: s = ceil((p + ceil(log2 k) + guard)/8)
+ *   guard_bits  extra fixed-point bits: s = ceil((p + ceil(log2 k) + guard)/w)
  *               slices (0 -> 40).  More guard bits make exact fallbacks rarer.
+ *   digit_bits  w, the bits per slice digit: 9 (balanced base-512 digits,
+ *               |d| <= 256, exact in bf16, fp32-exact for 256 inner elements)
+ *               or 8 (base 256, 960 inner elements); 0 -> 9 when k < 2^15,
+ *               else 8 (a group of one pair must fit int32: k 2^(2w-2) < 2^31).
  *   slices      s itself (0 -> the rule above); 1 <= s <= 160.
  *   cut_level   Q + 1, where pairs (t, u) with t + u <= Q are multiplied
  *               (0 -> Q = s - 1, the paper's triangle alpha + beta <= d + 1).
@@ -106,7 +110,8 @@ typedef struct mpc_oz_params {
     int32_t cut_level;
     int32_t kernel;
     int32_t max_group;
-    int32_t reserved[3];
+    int32_t digit_bits;
+    int32_t reserved[2];
 } mpc_oz_params;
 
 /*
@@ -134,7 +139,7 @@ typedef struct mpc_plan {
     uint64_t off_fix_a, off_fix_b;  /* unused (0) */
     uint64_t ws_bytes;
     int32_t launches;             /* kernel launches one call makes */
-    int32_t reserved;
+    int32_t digit_bits;           /* Ozaki: bits per digit w (8 or 9); plain: 28 */
     uint64_t off_group_order;     /* groups ordered by descending level */
 } mpc_plan;
 

@@ -13,18 +13,19 @@ Algorithm 2 of the paper (Kouya, Sec. III-C) in this library's reading:
    likewise F_j.  Every |a_il| < 2**E_i.
 2. Split (Alg. 2, tau / A_alpha := (A + S_A) - S_A).  The paper cuts each
    row on a grid set by tau into short S-bit floats so that the slice products
-   are exact.  Here the grid is fixed per row: X = sign * floor(|a| 2**(8s-1-E))
-   (truncation of the magnitude) and X is written in s balanced base-256
-   digits d_0 (most significant) .. d_{s-1}, every |d| <= 128, so that
-   a ~= sum_t d_t 2**(E-7-8t).  Digit t plays the role of slice A_{t+1}.
-   Digits are exact in bf16 and their products (|.| <= 2**14) are exact.
+   are exact.  Here the grid is fixed per row: X = sign * floor(|a| 2**(ws-1-E))
+   (truncation of the magnitude) and X is written in s balanced base-2**w
+   digits d_0 (most significant) .. d_{s-1}, every |d| <= 2**(w-1), so that
+   a ~= sum_t d_t 2**(E-(w-1)-wt).  Digit t plays the role of slice A_{t+1}.
+   w = 9 by default (8 selectable): every integer |d| <= 256 is exact in bf16
+   and products (|.| <= 2**(2w-2)) are exact.
 3. Products (Alg. 2, C_ab := A_a B_b for a + b <= d + 1).  Kept pair set
    P = {(t, u): t + u <= Q} (0-based; the paper's triangle is Q = s - 1).
-   Pairs of one level q = t + u have one weight 2**(E+F-14-8q); their
-   products are summed in groups of at most Gmax pairs, Gmax*k*2**14 < 2**31,
-   so every group sum fits an int32.
+   Pairs of one level q = t + u have one weight 2**(E+F-(2w-2)-wq); their
+   products are summed in groups of at most Gmax pairs,
+   Gmax*k*2**(2w-2) < 2**31, so every group sum fits an int32.
 4. Accumulation (Alg. 2, "L-bit FP arithmetic").  Here exact: the integer
-   Acc = sum_q H_q 2**(8(Q-q)), value = Acc * 2**(E_i+F_j-14-8Q).
+   Acc = sum_q H_q 2**(w(Q-q)), value = Acc * 2**(E_i+F_j-(2w-2)-wQ).
 5. 4M / 3M assembly (Eqs. 4m_way, 3m_way) on the exact accumulators:
    4M: Re = rr - ii, Im = ri + ir;  3M: Re = rr - ii, Im = ss - rr - ii, where
    ss is the product of the digit expansions of X_re + X_im (row) and
@@ -45,10 +46,23 @@ import numpy as np
 
 from . import exact as o1
 
-DIGIT_BITS = 8
-DIGIT_MAX = 128                 # every digit d satisfies |d| <= 128
-PROD_LOG2 = 14                  # |d_a * d_b| <= 2**14
+DIGIT_BITS = 9                  # default digit width w (8 is the other supported width)
 INT32_MAX = 2 ** 31 - 1
+
+
+def digit_max(w: int = DIGIT_BITS) -> int:
+    """Largest |d| of a balanced base-2**w digit (the top digit may reach it)."""
+    return 1 << (w - 1)
+
+
+def prod_log2(w: int = DIGIT_BITS) -> int:
+    """|d_a * d_b| <= 2**prod_log2(w)."""
+    return 2 * w - 2
+
+
+def auto_digit_bits(k: int) -> int:
+    """9-bit digits when one pair's sum fits an int32 (k 2**16 < 2**31), else 8."""
+    return 9 if k * (1 << prod_log2(9)) <= INT32_MAX else 8
 DEFAULT_GUARD = 40
 
 PRODUCTS_4M = ("rr", "ii", "ri", "ir")
@@ -71,6 +85,7 @@ class Params:
     gmax: int
     method: str
     guard: int = DEFAULT_GUARD
+    w: int = DIGIT_BITS          # bits per digit
 
     @property
     def products(self):
@@ -78,24 +93,28 @@ class Params:
 
 
 def make_params(p: int, k: int, method: str = "4m", guard: int = DEFAULT_GUARD,
-                s: int | None = None, Q: int | None = None, max_group: int = 0) -> Params:
+                s: int | None = None, Q: int | None = None, max_group: int = 0,
+                w: int | None = None) -> Params:
     """Slice count s, cut level Q and group size.
 
-    s = ceil((p + ceil(log2 k) + guard) / 8) digits; Q = s - 1 (the paper's
+    w = auto_digit_bits(k) unless given (9, or 8 when k >= 2**15);
+    s = ceil((p + ceil(log2 k) + guard) / w) digits; Q = s - 1 (the paper's
     triangle alpha + beta <= d + 1).  Both may be overridden.  Groups hold at
     most Gmax pairs (the int32 limit), or ``max_group`` if smaller; the level
     sums do not depend on the grouping.
     """
+    if w is None:
+        w = auto_digit_bits(k)
     if s is None:
-        s = -(-(p + ceil_log2(k) + guard) // DIGIT_BITS)
+        s = -(-(p + ceil_log2(k) + guard) // w)
     if Q is None:
         Q = s - 1
-    gmax = INT32_MAX // (k << PROD_LOG2) if k > 0 else 1
+    gmax = INT32_MAX // (k << prod_log2(w)) if k > 0 else 1
     if gmax < 1:
         raise ValueError("k too large for int32 group sums")
     if max_group > 0:
         gmax = min(gmax, max_group)
-    return Params(p=p, k=k, s=s, Q=Q, gmax=gmax, method=method, guard=guard)
+    return Params(p=p, k=k, s=s, Q=Q, gmax=gmax, method=method, guard=guard, w=w)
 
 
 # ------------------------------------------------------------- step 1
@@ -124,12 +143,12 @@ def row_exponents(mat, by: str):
 
 # ------------------------------------------------------------- step 2
 
-def fixed_point(v, E: int, s: int):
-    """X = sign * floor(|v| * 2**(8s-1-E)) for v = (N, x); returns (X, lossless)."""
+def fixed_point(v, E: int, s: int, w: int = DIGIT_BITS):
+    """X = sign * floor(|v| * 2**(ws-1-E)) for v = (N, x); returns (X, lossless)."""
     N, x = v
     if N == 0:
         return 0, True
-    sh = x + DIGIT_BITS * s - 1 - E
+    sh = x + w * s - 1 - E
     a = abs(N)
     if sh >= 0:
         X, lossless = a << sh, True
@@ -139,17 +158,18 @@ def fixed_point(v, E: int, s: int):
     return (-X if N < 0 else X), lossless
 
 
-def balanced_digits(X: int, nd: int):
-    """Digits d_0 .. d_{nd-1} (most significant first) with X = sum d_t 256**(nd-1-t).
+def balanced_digits(X: int, nd: int, w: int = DIGIT_BITS):
+    """Digits d_0 .. d_{nd-1} (most significant first) with X = sum d_t R**(nd-1-t), R = 2**w.
 
-    The nd-1 low digits are the residues of X mod 256 taken in [-128, 127];
+    The nd-1 low digits are the residues of X mod R taken in [-R/2, R/2 - 1];
     the top digit is what remains.
     """
+    R, h = 1 << w, 1 << (w - 1)
     out = []
     for _ in range(nd - 1):
-        d = ((X + 128) % 256) - 128
+        d = ((X + h) % R) - h
         out.append(d)
-        X = (X - d) // 256
+        X = (X - d) // R
     out.append(X)
     out.reverse()
     return out
@@ -166,9 +186,9 @@ class Split:
     values: tuple = (True, True)                 # some element has a nonzero real / imaginary part
 
 
-def fixed_point_array(N, x, E_line, s: int):
+def fixed_point_array(N, x, E_line, s: int, w: int = DIGIT_BITS):
     """Vectorised ``fixed_point`` over an object array N (exponent x per element)."""
-    sh = x + DIGIT_BITS * s - 1 - E_line          # int64 array
+    sh = x + w * s - 1 - E_line                   # int64 array
     a = np.abs(N)
     up = a * np.vectorize(lambda t: 1 << int(t) if t >= 0 else 1, otypes=[object])(sh)
     down = np.vectorize(lambda v, t: v >> int(-t) if t < 0 else v, otypes=[object])(a, sh)
@@ -178,18 +198,19 @@ def fixed_point_array(N, x, E_line, s: int):
     return np.where(N < 0, -X, X), lossless
 
 
-def balanced_digits_array(X, nd: int):
+def balanced_digits_array(X, nd: int, w: int = DIGIT_BITS):
     """Vectorised ``balanced_digits``: int64 array [nd, ...], most significant first."""
+    R, h = 1 << w, 1 << (w - 1)
     out = np.zeros((nd,) + X.shape, np.int64)
     for t in range(nd - 1, 0, -1):
-        d = ((X + 128) % 256) - 128
+        d = ((X + h) % R) - h
         out[t] = d.astype(np.int64)
-        X = (X - d) // 256
+        X = (X - d) // R
     out[0] = X.astype(np.int64)
     return out
 
 
-def split_operand(mat, s: int, side: str, method: str) -> Split:
+def split_operand(mat, s: int, side: str, method: str, w: int = DIGIT_BITS) -> Split:
     """Alg. 2's split for A (side='A', lines = rows) or B (side='B', lines = columns).
 
     For B the digit planes are stored K-major: digits[.][u][j][l].
@@ -204,17 +225,17 @@ def split_operand(mat, s: int, side: str, method: str) -> Split:
         Nre, Nim, xre, xim = Nre.T, Nim.T, xre.T, xim.T
     Eline = np.array([0 if e is None else e for e in E], np.int64)[:, None]
     zero_line = np.array([e is None for e in E])[:, None]
-    Xr, okr = fixed_point_array(Nre, xre, Eline, s)
-    Xi, oki = fixed_point_array(Nim, xim, Eline, s)
+    Xr, okr = fixed_point_array(Nre, xre, Eline, s, w)
+    Xi, oki = fixed_point_array(Nim, xim, Eline, s, w)
     Xr = np.where(zero_line, 0, Xr)
     Xi = np.where(zero_line, 0, Xi)
     ok = (okr & oki) | zero_line
     sp = Split(E=E, lossless=[bool(v) for v in ok.all(axis=1)])
-    sp.digits["re"] = balanced_digits_array(Xr, s)
-    sp.digits["im"] = balanced_digits_array(Xi, s)
+    sp.digits["re"] = balanced_digits_array(Xr, s, w)
+    sp.digits["im"] = balanced_digits_array(Xi, s, w)
     sp.first_pos["re"] = sp.first_pos["im"] = 0
     if method == "3m":
-        sp.digits["sum"] = balanced_digits_array(Xr + Xi, s + 1)
+        sp.digits["sum"] = balanced_digits_array(Xr + Xi, s + 1, w)
         sp.first_pos["sum"] = -1
     for which, D in sp.digits.items():
         sp.live[which] = [bool(np.any(D[x])) for x in range(D.shape[0])]
@@ -332,23 +353,24 @@ def group_sums(spA: Split, spB: Split, prod: str, prm: Params):
 
 # ------------------------------------------------------------- step 4
 
-def accumulate(gs, sums, Q: int):
-    """Acc = sum_g G_g * 2**(8(Q - q_g)) as Python ints (object array)."""
+def accumulate(gs, sums, Q: int, w: int = DIGIT_BITS):
+    """Acc = sum_g G_g * 2**(w(Q - q_g)) as Python ints (object array)."""
     shape = sums[0].shape if sums else (0, 0)
     acc = np.zeros(shape, dtype=object)
     for g, G in zip(gs, sums):
-        acc = acc + G.astype(object) * (1 << (DIGIT_BITS * (Q - g.q)))
+        acc = acc + G.astype(object) * (1 << (w * (Q - g.q)))
     return acc
 
 
 # ------------------------------------------------------------- step 6 (bound)
 
 @functools.lru_cache(maxsize=None)
-def drop_bound(tA: tuple, tB: tuple, Q: int, k: int, liveA=None, liveB=None) -> int:
+def drop_bound(tA: tuple, tB: tuple, Q: int, k: int, liveA=None, liveB=None, w: int = DIGIT_BITS) -> int:
     """Integer bound on the dropped pairs of one product, in Acc units.
 
-    Dropped level Q+j contributes at most n_{Q+j} k 2**14 2**(-8j).  The
-    j = 1 term is k*64*n; the rest is below k*max_n/3 (geometric tail).  With
+    Dropped level Q+j contributes at most n_{Q+j} k 2**(2w-2) 2**(-wj).  The
+    j = 1 term is k 2**(w-2) n; the rest is below k*max_n/3 (geometric tail:
+    2**(-2) / (1 - 2**-w) < 1/3).  With
     liveA / liveB (per digit plane, from position tA[0] / tB[0]) only the pairs
     whose two planes both have a nonzero digit are counted: the others are
     exactly zero.
@@ -362,7 +384,7 @@ def drop_bound(tA: tuple, tB: tuple, Q: int, k: int, liveA=None, liveB=None) -> 
     n1 = levels.get(Q + 1, 0)
     rest = [n for q, n in levels.items() if q >= Q + 2]
     nmax = max(rest) if rest else 0
-    return k * (64 * n1 + (-(-nmax // 3)))
+    return k * ((1 << (w - 2)) * n1 + (-(-nmax // 3)))
 
 
 def split_coeffs(prod: str):
@@ -373,8 +395,11 @@ def split_coeffs(prod: str):
 
 
 def bound_exponent(prm: Params) -> int:
-    """beta: the bound is b * 2**beta with beta = max(0, 15 + 8(Q - s))."""
-    return max(0, 15 + DIGIT_BITS * (prm.Q - prm.s))
+    """beta: the bound is b * 2**beta with beta = max(0, 2w - 1 + w(Q - s)).
+
+    One unit of the split grid, 2**(E-(ws-1)), times |b| < 2**F, in Acc units
+    2**(E+F-(2w-2)-wQ), is 2**(2w-1+w(Q-s))."""
+    return max(0, 2 * prm.w - 1 + prm.w * (prm.Q - prm.s))
 
 
 def entry_bound(prm: Params, spA: Split, spB: Split, i: int, j: int, comp: str):
@@ -416,13 +441,13 @@ def product_bound(prm: Params, spA: Split, spB: Split, pr: str):
     have a nonzero value somewhere: otherwise the product and its digit product
     are both exactly zero.  Cached on the splits (it depends on them only).
     """
-    key = ("bound", pr, prm.Q, prm.k, prm.s)
+    key = ("bound", pr, prm.Q, prm.k, prm.s, prm.w)
     cache = spA.__dict__.setdefault("_bound_cache", {})
     hit = cache.get(key)
     if hit is None or hit[0] is not spB:        # keyed on the very B split (kept alive here)
         wa, wb = PRODUCT_OPERANDS[pr]
         tA, tB = positions(spA, wa, prm.s), positions(spB, wb, prm.s)
-        bd = drop_bound(tA, tB, prm.Q, prm.k, tuple(spA.live[wa]), tuple(spB.live[wb]))
+        bd = drop_bound(tA, tB, prm.Q, prm.k, tuple(spA.live[wa]), tuple(spB.live[wb]), prm.w)
         hit = (spB, (bd, value_nonzero(spA, wa) and value_nonzero(spB, wb)))
         cache[key] = hit
     return hit[1]
@@ -454,26 +479,28 @@ class OzakiResult:
     groups: dict          # product -> list[Group]
     group_sums: dict      # product -> list[int64 array m x n]
     acc: dict             # 're'/'im' -> object array of exact combined accumulators
-    scale: np.ndarray     # E_i + F_j - 14 - 8Q (object array)
+    scale: np.ndarray     # E_i + F_j - (2w-2) - wQ (object array)
     certified: np.ndarray  # bool [2, m, n]
     C: object             # MPCMatrix, final rounded output (== O1)
 
 
 def ozaki_cgemm(A, B, p: int, method: str = "4m", guard: int = DEFAULT_GUARD,
-                s: int | None = None, Q: int | None = None, fallback=None, max_group: int = 0) -> OzakiResult:
+                s: int | None = None, Q: int | None = None, fallback=None, max_group: int = 0,
+                w: int | None = None) -> OzakiResult:
     """Emulate the whole Ozaki complex GEMM; ``fallback(i, j) -> (re, im)`` exact values.
 
     Without ``fallback`` the exact O1 triple loop is used for uncertified entries.
     """
     m, k, n = A.rows, A.cols, B.cols
-    prm = make_params(p, k, method, guard, s, Q, max_group)
-    spA = split_operand(A, prm.s, "A", method)
-    spB = split_operand(B, prm.s, "B", method)
+    prm = make_params(p, k, method, guard, s, Q, max_group, w)
+    w = prm.w
+    spA = split_operand(A, prm.s, "A", method, w)
+    spB = split_operand(B, prm.s, "B", method, w)
     groups, sums, acc_p = {}, {}, {}
     for pr in prm.products:
         gs, gsum = group_sums(spA, spB, pr, prm)
         groups[pr], sums[pr] = gs, gsum
-        acc_p[pr] = accumulate(gs, gsum, prm.Q) if gs else np.zeros((m, n), dtype=object)
+        acc_p[pr] = accumulate(gs, gsum, prm.Q, w) if gs else np.zeros((m, n), dtype=object)
     acc_re = acc_p["rr"] - acc_p["ii"]
     acc_im = (acc_p["ri"] + acc_p["ir"]) if method == "4m" else (acc_p["ss"] - acc_p["rr"] - acc_p["ii"])
     scale = np.zeros((m, n), dtype=object)
@@ -484,7 +511,7 @@ def ozaki_cgemm(A, B, p: int, method: str = "4m", guard: int = DEFAULT_GUARD,
         for j in range(n):
             Ei = spA.E[i] if spA.E[i] is not None else 0
             Fj = spB.E[j] if spB.E[j] is not None else 0
-            x = Ei + Fj - PROD_LOG2 - DIGIT_BITS * prm.Q
+            x = Ei + Fj - prod_log2(prm.w) - prm.w * prm.Q
             scale[i, j] = x
             for c, (comp, acc) in enumerate((("re", acc_re), ("im", acc_im))):
                 b, beta = entry_bound(prm, spA, spB, i, j, comp)
@@ -513,7 +540,7 @@ def _exact_entry(A, B, i, j):
 
 
 def exact_accumulators(A, B, spA: Split, spB: Split, prm: Params):
-    """Exact T scaled to Acc units, as rationals: T * 2**-(E+F-14-8Q)."""
+    """Exact T scaled to Acc units, as rationals: T * 2**-(E+F-(2w-2)-wQ)."""
     from fractions import Fraction
     re, im = o1.exact_cgemm(A, B, "4m")
     m, n = A.rows, B.cols
@@ -522,7 +549,7 @@ def exact_accumulators(A, B, spA: Split, spB: Split, prm: Params):
         for j in range(n):
             Ei = spA.E[i] if spA.E[i] is not None else 0
             Fj = spB.E[j] if spB.E[j] is not None else 0
-            x = Ei + Fj - PROD_LOG2 - DIGIT_BITS * prm.Q
+            x = Ei + Fj - prod_log2(prm.w) - prm.w * prm.Q
             for comp, T in (("re", re), ("im", im)):
                 out[comp][i, j] = o1.to_fraction(T[i][j]) / (Fraction(2) ** x)
     return out

@@ -2,12 +2,13 @@
 // Eqs. (4m_way) / (3m_way)), and the exact fallback.
 //
 // k_oz_accum: one thread per output element (i, j).  The group sums of every
-// real product are shifted by 8 (Q - q) and added, with the sign the complex
+// real product are shifted by w (Q - q) and added, with the sign the complex
 // formula gives them, into two exact accumulators (Re, Im):
 //     4M: Re = rr - ii,        Im = ri + ir
 //     3M: Re = rr - ii,        Im = ss - rr - ii
 // Groups are visited in order of increasing shift; each accumulator keeps two
-// running int64 words in registers and emits finished 32-bit words.  Value = Acc * 2^(E_i + F_j - 14 - 8Q).
+// running int64 words in registers and emits finished 32-bit words.
+// Value = Acc * 2^(E_i + F_j - (2w - 2) - wQ).
 // The result is RN_p(Acc) when no rounding midpoint lies within the error
 // bound b * 2^beta of Acc (then it equals RN_p of the exact product);
 // otherwise the component is queued for k_exact_fallback.
@@ -112,7 +113,7 @@ __device__ __forceinline__ void product_kinds(int method, int prod, int &ka, int
 // (descending level, i.e. ascending shift), writes the slice GEMM's unit schedule
 // and the call's error bounds:
 //   drop[c]    = sum over the products of component c of ceil(B_prod / 2^beta),
-//                B_prod = k (64 n_{Q+1} + ceil(max_{j>=2} n_{Q+j} / 3)) over live pairs;
+//                B_prod = k (2^(w-2) n_{Q+1} + ceil(max_{j>=2} n_{Q+j} / 3)) over live pairs;
 //   lossy_a[c] = sum of the products' truncation factors (4 for the 3M sums, else 1),
 //                counted only when both operand components of the product have a
 //                nonzero value somewhere (otherwise the product is exactly zero);
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
       if (q == a.Q + 1) n1 = cnt;
       else if (cnt > nmax) nmax = cnt;
     }
-    if (lane == 0) s_bd[warp] = (uint64_t)a.k * (64 * n1 + (nmax + 2) / 3);
+    if (lane == 0) s_bd[warp] = (uint64_t)a.k * (((uint64_t)1 << (a.w - 2)) * n1 + (nmax + 2) / 3);
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -242,7 +243,7 @@ __device__ __forceinline__ void finish_component(const AccumArgs &a, const OutVi
   if (N == 0 && b == 0) {
     store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
   } else if (N > 0 && certified(mag, a.nslot, N, a.p, b, a.bound_shift)) {
-    const int64_t scale = (int64_t)Ei + (int64_t)Fj - kProdLog2 - 8 * (int64_t)a.Q;
+    const int64_t scale = (int64_t)Ei + (int64_t)Fj - prod_log2(a.w) - (int64_t)a.w * a.Q;
     if (!round_store(mag, a.nslot, N, neg, scale, a.p, a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o,
                      C.plane)) {
       status_set(a.status, kStErange, 1);
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
     const bool last = (x + 1 == a.n_entries) || (a.groups[a.order[x + 1]].q != g.q);
     const bool empty = g.count == 0;   // all its pairs were zero: its plane was never written
     const bool z0 = a.bounds[6] != 0, z1 = a.bounds[7] != 0;   // components that vanish identically
-    terms[x] = Term{empty ? -1 : e, (int16_t)(last ? 8 * (a.Q - g.q) : -1),
+    terms[x] = Term{empty ? -1 : e, (int16_t)(last ? a.w * (a.Q - g.q) : -1),
                     (int8_t)(empty || z0 ? 0 : product_sign(a.method, 0, g.prod)),
                     (int8_t)(empty || z1 ? 0 : product_sign(a.method, 1, g.prod))};
   }

@@ -29,9 +29,9 @@ struct Plan {
   int kernel;
 };
 
-// Integer bound on the pairs a product drops, in Acc units (dropped level
-// Q + j contributes <= n_{Q+j} k 2^14 2^(-8 j)): k (64 n_{Q+1} + ceil(max_{j>=2} n / 3)).
-uint64_t drop_bound(const ProductDesc &pd, int Q, int64_t k) {
+// Integer bound on the pairs a product drops, in Acc units (dropped level Q + j
+// contributes <= n_{Q+j} k 2^(2w-2) 2^(-w j)): k (2^(w-2) n_{Q+1} + ceil(max_{j>=2} n / 3)).
+uint64_t drop_bound(const ProductDesc &pd, int Q, int64_t k, int w) {
   const int qmax = pd.a_pos0 + pd.a_npos - 1 + pd.b_pos0 + pd.b_npos - 1;
   if (Q + 1 > qmax) return 0;
   const uint64_t n1 = (uint64_t)level_pairs(pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, Q + 1);
@@ -40,7 +40,7 @@ uint64_t drop_bound(const ProductDesc &pd, int Q, int64_t k) {
     const uint64_t v = (uint64_t)level_pairs(pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, q);
     if (v > nmax) nmax = v;
   }
-  return (uint64_t)k * (64 * n1 + (nmax + 2) / 3);
+  return (uint64_t)k * (((uint64_t)1 << (w - 2)) * n1 + (nmax + 2) / 3);
 }
 
 int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, const mpc_oz_params *prm,
@@ -82,6 +82,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
     const int DP = (D + 3) & ~3, NLP = plain_limbs(D);
     P.s = D;
     P.kpad = DP;
+    P.digit_bits = kPlainDigitBits;
     P.bound_shift = kPlainDigitBits * D - 2;   // W: bounds are b 2^W in units of 2^(E+F-2W)
     P.n_products = method == MPC_4M ? 4 : 3;
     P.planes_A = P.planes_B = method == MPC_4M ? 2 : 3;
@@ -102,14 +103,18 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
     P.launches = 8;   // init, row max, column max, 2 x digits, plain GEMM, combine, fallback (+1 zero fill when k == 0)
     return MPC_OK;
   }
-  // ---- Ozaki: Alg. 2's number of slices and the kept triangle
+  // ---- Ozaki: the digit width, Alg. 2's number of slices and the kept triangle
+  const int64_t kk = k > 0 ? k : 1;
+  int w = prm ? prm->digit_bits : 0;
+  if (w == 0) w = (kk << prod_log2(9)) <= (int64_t)INT32_MAX ? 9 : 8;   // a pair's sum must fit int32
+  if (w != 8 && w != 9) return MPC_EINVAL;
+  P.digit_bits = w;
   const int guard = (prm && prm->guard_bits > 0) ? prm->guard_bits : kDefaultGuard;
-  int s = (prm && prm->slices > 0) ? prm->slices : (int)((p + ceil_log2(k) + guard + 7) / 8);
+  int s = (prm && prm->slices > 0) ? prm->slices : (int)((p + ceil_log2(k) + guard + w - 1) / w);
   if (s < 1 || s > kMaxSlices) return MPC_EINVAL;
   const int Q = (prm && prm->cut_level > 0) ? prm->cut_level - 1 : s - 1;
   if (Q > 2 * s) return MPC_EINVAL;
-  const int64_t kk = k > 0 ? k : 1;
-  int gmax = (int)(((int64_t)INT32_MAX) / (kk << kProdLog2));
+  int gmax = (int)(((int64_t)INT32_MAX) / (kk << prod_log2(w)));
   if (gmax < 1) return MPC_EINVAL;
   if (prm && prm->max_group < 0) return MPC_EINVAL;
   if (prm && prm->max_group > 0 && prm->max_group < gmax) gmax = prm->max_group;
@@ -149,10 +154,10 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   }
   P.n_groups_total = total;
   if (total > kMaxGroupsTotal) return MPC_EINVAL;   // the accumulate kernel's term table in shared memory
-  P.acc_slots = (8 * (Q - qmin) + 64) / 32 + 3;
+  P.acc_slots = (w * (Q - qmin) + 64) / 32 + 3;
   if (P.acc_slots > 88) return MPC_EINVAL;   // the accumulate kernel's word budget
   // bounds: b = bound_drop[c] + k (lossyA * bound_lossy_a[c] + lossyB * bound_lossy_b[c]), times 2^beta
-  const int beta = 15 + 8 * (Q - s) > 0 ? 15 + 8 * (Q - s) : 0;
+  const int beta = 2 * w - 1 + w * (Q - s) > 0 ? 2 * w - 1 + w * (Q - s) : 0;
   P.bound_shift = beta;
   for (int c = 0; c < 2; ++c) {
     int prods[3], np = 0;
@@ -162,7 +167,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
     uint64_t bd = 0, la = 0, lb = 0;
     for (int x = 0; x < np; ++x) {
       const ProductDesc &d = out->prod[prods[x]];
-      bd += ceil_shift(drop_bound(d, Q, k), beta);
+      bd += ceil_shift(drop_bound(d, Q, k, w), beta);
       const uint64_t cf = (d.a_pos0 < 0) ? 2 : 1;   // sums: 2 ulps truncation, |.| < 2^(E+1)
       la += cf * cf;
       lb += cf * cf;
@@ -295,9 +300,9 @@ void call_pre(Call &c, cudaStream_t st) {
                         (int32_t *)(c.ws + P.off_digits_b), st);
   } else {
     const int want_sum = P.method == MPC_3M;
-    launch_oz_digits(c.A, 0, c.m, c.k, P.kpad, L, P.s, want_sum, c.E, c.lossyA,
+    launch_oz_digits(c.A, 0, c.m, c.k, P.kpad, L, P.s, P.digit_bits, want_sum, c.E, c.lossyA,
                      (__nv_bfloat16 *)(c.ws + P.off_digits_a), plane_nz, st);
-    launch_oz_digits(c.B, 1, c.n, c.k, P.kpad, L, P.s, want_sum, c.F, c.lossyB,
+    launch_oz_digits(c.B, 1, c.n, c.k, P.kpad, L, P.s, P.digit_bits, want_sum, c.F, c.lossyB,
                      (__nv_bfloat16 *)(c.ws + P.off_digits_b), plane_nz + flagsA, st);
     GroupTableArgs ga{};
     for (int x = 0; x < 4; ++x) ga.prod[x] = c.pl.prod[x];
@@ -306,6 +311,7 @@ void call_pre(Call &c, cudaStream_t st) {
     ga.Q = P.Q;
     ga.gmax = P.gmax;
     ga.beta = P.bound_shift;
+    ga.w = P.digit_bits;
     ga.k = c.k;
     ga.planes_A = P.planes_A;
     ga.planes_B = P.planes_B;
@@ -326,6 +332,7 @@ SliceGemmArgs slice_args(const Call &c) {
   sa.m = c.m;
   sa.n = c.n;
   sa.kpad = P.kpad;
+  sa.chunk_kb = chunk_kblocks(P.digit_bits);
   sa.groups = (const GroupEntry *)(c.ws + P.off_group_table);
   sa.sched = (const int32_t *)(c.ws + P.off_group_order) + P.n_groups_total;
   sa.n_entries = P.n_groups_total;
@@ -404,6 +411,7 @@ void call_accum(Call &c, cudaStream_t st) {
   aa.lossyA = c.lossyA;
   aa.lossyB = c.lossyB;
   aa.bound_shift = P.bound_shift;
+  aa.w = P.digit_bits;
   aa.bounds = (const uint64_t *)(c.ws + P.off_group_order + bounds_offset(P.n_groups_total, P.planes_A, P.planes_B));
   for (int x = 0; x < 2; ++x) {
     aa.bound_drop[x] = P.bound_drop[x];

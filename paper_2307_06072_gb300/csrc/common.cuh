@@ -12,9 +12,11 @@
 
 namespace mpc {
 
-constexpr int kDigitBits = 8;          // balanced base-256 digits, |d| <= 128
-constexpr int kProdLog2 = 14;          // |d_a d_b| <= 2^14
-constexpr int kChunk = 960;            // K elements per fp32 drain: 960 * 2^14 < 2^24
+// Ozaki digits of w bits (9, or 8 for k >= 2^15): balanced base-2^w, |d| <= 2^(w-1),
+// |d_a d_b| <= 2^(2w-2); the fp32 tensor-core sum of a chunk of inner products stays an
+// exact integer below 2^24 (w = 8: 960 elements, 960 2^14 < 2^24; w = 9: 256, <= 2^24).
+__host__ __device__ constexpr int prod_log2(int w) { return 2 * w - 2; }
+__host__ __device__ constexpr int chunk_kblocks(int w) { return w == 9 ? 4 : 15; }   // 64-element k-blocks
 constexpr int kKBlock = 64;            // digit-plane row padding (one 128-byte bf16 row)
 constexpr int kMaxSlices = 160;
 constexpr int kMaxLimbs = 16;          // p <= 1024

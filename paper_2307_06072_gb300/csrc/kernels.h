@@ -12,6 +12,7 @@ struct SliceGemmArgs {
   const __nv_bfloat16 *dA;      // digit planes of A: [plane][m][kpad]
   const __nv_bfloat16 *dB;      // digit planes of B: [plane][n][kpad]
   int64_t m, n, kpad;
+  int chunk_kb;                 // k-blocks of 64 per exact fp32 chunk (digit width)
   const GroupEntry *groups;     // group table (n_entries)
   const int32_t *sched;         // order in which the groups' units are handed out (null: table order)
   int32_t n_entries;
@@ -24,7 +25,7 @@ struct SliceGemmArgs {
 // bounds of one Ozaki call (k_group_table, after the digits).
 struct GroupTableArgs {
   ProductDesc prod[4];
-  int n_products, method, Q, gmax, beta;
+  int n_products, method, Q, gmax, beta, w;
   int64_t k;
   int planes_A, planes_B;
   const int32_t *flagsA, *flagsB;   // per digit plane: any nonzero digit; then per component: any nonzero value
@@ -47,7 +48,7 @@ struct AccumArgs {
   int64_t m, n, k;
   int p, L, Q, nslot, method;
   const int32_t *E, *F, *lossyA, *lossyB;
-  int bound_shift;
+  int bound_shift, w;          // bounds are b 2^beta; w bits per digit
   uint64_t bound_drop[2], bound_lossy_a[2], bound_lossy_b[2];   // data-independent (plan)
   const uint64_t *bounds;       // the call's bounds (drop[2], lossy_a[2], lossy_b[2], zero[2]), from k_group_table
   int64_t *fallback;            // list of (i*n + j)*2 + c
@@ -95,7 +96,7 @@ void launch_init(int32_t *status, int32_t *E, int64_t m, int32_t *F, int64_t n, 
                  cudaStream_t st, int32_t *extra = nullptr, int64_t n_extra = 0);
 void launch_line_max(const MatView &A, const MatView &B, int64_t m, int64_t n, int64_t k, int L, int32_t *E,
                      int32_t *F, cudaStream_t st);
-void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
+void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s, int wd,
                       int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, int32_t *plane_nz,
                       cudaStream_t st);
 void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, int L, int D, int DP, int W,

@@ -4,11 +4,11 @@
 // One CTA computes one 128 x 128 tile of one group sum
 //     G_g = sum_{(t,u) in g} D^A_t (D^B_u)^T,
 // i.e. one GEMM over the concatenated inner dimension K' = count * kpad.
-// Operands are integer digits |d| <= 128 carried in bf16; products (<= 2^14)
-// are exact and the fp32 accumulators stay exact while fewer than 1024
-// products are summed, so every kChunk = 960 inner elements the fp32 tile is
-// converted to int32 and added to int32 registers (the group bound keeps
-// every partial sum below 2^31).  This kernel is kept as an independent
+// Operands are integer digits |d| <= 2^(w-1) (w = 9 or 8) carried in bf16;
+// products (<= 2^(2w-2)) are exact and the fp32 accumulators stay exact over a
+// chunk of inner elements (256 for w = 9, 960 for w = 8), after which the fp32
+// tile is converted to int32 and added to int32 registers (the group bound
+// keeps every partial sum below 2^31).  This kernel is kept as an independent
 // second implementation of the tcgen05 kernel's contract.
 #include <cuda_bf16.h>
 
@@ -19,8 +19,7 @@ namespace mpc {
 
 namespace {
 constexpr int MT = 128, NT = 128, KT = 32, LDS = 40;   // LDS: smem row stride (bf16), 80 B
-constexpr int kStepsPerChunk = kChunk / KT;             // 30
-static_assert(kChunk % KT == 0, "chunk must be a multiple of the k step");
+static_assert((64 % KT) == 0, "a k-block must be whole k steps");
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
   uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
@@ -60,6 +59,7 @@ __global__ void __launch_bounds__(256) k_slicegemm_mma(SliceGemmArgs a, int tile
   const ProductDesc pd = a.prod[g.prod];
   const int64_t planeA = a.m * a.kpad, planeB = a.n * a.kpad;
   const int steps_per_pair = (int)(a.kpad / KT);
+  const int steps_per_chunk = a.chunk_kb * (64 / KT);   // exact fp32 chunk (digit width)
   const int total_steps = g.count * steps_per_pair;
 
   auto load_stage = [&](int stage, int step) {
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_slicegemm_mma(SliceGemmArgs a, int tile
         for (int nt = 0; nt < 4; ++nt) mma_bf16_16816(accf[mt][nt], af[mt], bfr[nt][0], bfr[nt][1]);
     }
     __syncthreads();
-    if ((step + 1) % kStepsPerChunk == 0 || step + 1 == total_steps) {
+    if ((step + 1) % steps_per_chunk == 0 || step + 1 == total_steps) {
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll

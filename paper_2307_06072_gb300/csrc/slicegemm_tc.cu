@@ -18,9 +18,9 @@
 //   warp 1      TMEM owner (alloc 512 columns) and, on one lane, the MMA
 //               issuer: tcgen05.mma.cta_group::1.kind::f16, bf16 x bf16 ->
 //               fp32 into one of two 128 x 256 TMEM accumulators.
-//   warps 2..9  epilogue: every kChunk = 960 inner elements (15 k-blocks) the
-//               accumulator holds an exact integer < 2^24 (digits |d| <= 128,
-//               |d_a d_b| <= 2^14, 960 * 2^14 < 2^24); it is read with
+//   warps 2..9  epilogue: every chunk of inner elements (4 k-blocks for 9-bit
+//               digits: 256 2^16 <= 2^24; 15 for 8-bit: 960 2^14 < 2^24) the
+//               accumulator holds an exact integer; it is read with
 //               tcgen05.ld, converted exactly to int32 and added to int32
 //               registers (the group bound keeps every sum below 2^31).
 //               The two TMEM buffers let the MMA fill one while the other
@@ -42,14 +42,12 @@ namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int KB_PER_CHUNK = kChunk / BK;       // 15
 constexpr int NUM_THREADS = 320, EPI_WARPS = 8;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long kTimeoutCycles = 4000000000ll;   // ~2 s at 2 GHz
 constexpr int URING = 4;                               // unit-index ring slots
 constexpr int kMaxBatch = 48;                          // problems per launch (kernel parameter space)
 constexpr int kStUnitCounter = 8;                      // status word used as the unit counter
-static_assert(kChunk % BK == 0, "chunk must be whole k-blocks");
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
 
 // One launch serves a set of up to kMaxBatch independent problems (a single
@@ -59,7 +57,8 @@ struct TcProblem {
   int64_t m, n;
   int64_t unit0;       // first unit of this problem
   int kbpp;            // k-blocks per pair (kpad / 64)
-  int tiles_m, tiles_n, pad_;
+  int tiles_m, tiles_n;
+  int chunk_kb;        // k-blocks per exact fp32 chunk (4 for 9-bit digits, 15 for 8-bit)
   const GroupEntry *groups;
   const int32_t *sched;   // unit order over the groups (null: table order)
   int32_t *out;
@@ -418,8 +417,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (++slot == URING) { slot = 0; uphase ^= 1; }
         if (u < 0) break;
         const Unit x = decode<CL>(P, u, rank);
-        for (int c0 = 0; c0 < x.nkb && ok; c0 += KB_PER_CHUNK) {
-          const int cend = min(x.nkb, c0 + KB_PER_CHUNK);
+        const int ck = P.prob[x.prob].chunk_kb;
+        for (int c0 = 0; c0 < x.nkb && ok; c0 += ck) {
+          const int cend = min(x.nkb, c0 + ck);
           if (!mbar_wait(&tempty[buf], tphase ^ 1, abort, P.status)) { ok = false; break; }
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
@@ -465,7 +465,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (++slot == URING) { slot = 0; uphase ^= 1; }
       if (u < 0) break;
       const Unit x = decode<CL>(P, u, rank);
-      for (int c0 = 0; c0 < x.nkb; c0 += KB_PER_CHUNK) {
+      const int ck = P.prob[x.prob].chunk_kb;
+      for (int c0 = 0; c0 < x.nkb; c0 += ck) {
         if (!mbar_wait(&tfull[buf], tphase, abort, P.status)) { ok = false; break; }
         tc_fence_after();
         const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + half * 128);
@@ -578,6 +579,7 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
     t.kbpp = (int)(a.kpad / BK);
     t.tiles_m = (int)((a.m + BM - 1) / BM);
     t.tiles_n = (int)((a.n + BN - 1) / BN);
+    t.chunk_kb = a.chunk_kb;
     t.unit0 = units;
     t.groups = a.groups;
     t.sched = a.sched;

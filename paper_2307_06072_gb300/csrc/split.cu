@@ -6,9 +6,10 @@
 //    column j of B.  Every |a_il| < 2^E_i.
 //  * k_oz_digits: the split itself.  Alg. 2 cuts A on a grid set by tau into
 //    short floats whose products are exact.  Here the grid is fixed per row:
-//    X = sign * floor(|a| 2^(8s-1-E)) and X is written in s balanced base-256
-//    digits (|d| <= 128, exact in bf16, products exact), most significant
-//    first; digit t stands for slice A_{t+1}.  For the 3M form (Eq. 3m_way)
+//    X = sign * floor(|a| 2^(ws-1-E)) and X is written in s balanced base-2^w
+//    digits (w = 9 or 8: |d| <= 2^(w-1) <= 256, exact in bf16, products
+//    exact), most significant first; digit t stands for slice A_{t+1}.  For
+//    the 3M form (Eq. 3m_way)
 //    the digits of X_re + X_im are produced as well (s+1 digits).  B is split
 //    by columns and stored transposed (K-major), as the tensor cores read it.
 //  * k_plain_digits: the plain path's fixed-point operands as signed
@@ -127,7 +128,7 @@ struct DigitStream {
 // so that one warp vote per plane marks in nz[] the planes that got a nonzero
 // digit, and nz[nplanes + c] when a nonzero value of component c was seen.
 __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad,
-                                               int L, int s, int want_sum, const int32_t *E, int32_t *lossy,
+                                               int L, int s, int wd, int want_sum, const int32_t *E, int32_t *lossy,
                                                __nv_bfloat16 *digits, int64_t l0, int64_t line, bool in_range,
                                                int *nz) {
   const bool leader = (threadIdx.x & 31) == 0;
@@ -152,7 +153,7 @@ __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64
       if (nz) nzv[c] = true;
       for (int j = 0; j < L; ++j) d[q].M[c][j] = nz ? X.limb[c][(int64_t)j * X.plane + idx] : 0ull;
       // |X| bit b  <->  M bit b + sh:  X = |v| 2^(8s-1-E), |v| = M 2^(exp-64L)
-      d[q].sh[c] = nz ? (64 * (int64_t)L + (int64_t)e_line - (int64_t)X.exp[c][idx] - (8 * (int64_t)s - 1)) : 0;
+      d[q].sh[c] = nz ? (64 * (int64_t)L + (int64_t)e_line - (int64_t)X.exp[c][idx] - ((int64_t)wd * s - 1)) : 0;
       d[q].neg[c] = nz ? X.sign[c][idx] : 0;
       d[q].cneg[c] = 1;
       d[q].cbal[c] = 0;
@@ -169,74 +170,97 @@ __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64
 #pragma unroll
   for (int c = 0; c < 2; ++c)
     if (__ballot_sync(0xffffffffu, nzv[c]) && leader) nz[nplanes + c] = 1;
-  const int nbytes = want_sum ? s + 1 : s;
-  for (int w = 0; 8 * w < nbytes; ++w) {
-    uint64_t wc[2][2];   // two's-complement words [element][component]
+  // Digits, least significant first, from LSB-first bit streams of the two's-complement
+  // words of X_re, X_im (wd*s bits) and X_re + X_im: every stream keeps a 128-bit buffer
+  // (lo, hi) holding `nbuf` bits; all streams advance in step (wd bits per digit).
+  const int ndig = want_sum ? s + 1 : s;
+  const int64_t xbits = (int64_t)wd * s;                 // |X| < 2^(xbits - 1)
+  const uint32_t fmask = (1u << wd) - 1u;
+  const int half = 1 << (wd - 1), full = 1 << wd;
+  uint64_t blo[2][3], bhi[2][3];                         // [element][re, im, sum]
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) blo[q][c] = bhi[q][c] = 0;
+  int nbuf = 0, wnext = 0;
+  for (int pos = 0; pos < ndig; ++pos) {
+    if (nbuf < wd) {   // append word `wnext` of every stream above the bits still buffered
+      uint64_t wc[2][3];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          uint64_t x = word_at_bit(d[q].M[c], L, 64 * (int64_t)wnext + d[q].sh[c]);
+          const int64_t top = xbits - 64 * (int64_t)wnext;   // bits of |X| in this word
+          if (top < 64) x &= top <= 0 ? 0ull : ((1ull << top) - 1ull);
+          if (d[q].neg[c]) {
+            const uint64_t t = ~x + d[q].cneg[c];
+            d[q].cneg[c] = (d[q].cneg[c] && t == 0) ? 1ull : 0ull;
+            x = t;
+          }
+          wc[q][c] = x;
+        }
+        const uint64_t a0 = wc[q][0] + wc[q][1];
+        const uint64_t c1 = a0 < wc[q][0];
+        const uint64_t a1 = a0 + d[q].csum;
+        const uint64_t c2 = a1 < a0;
+        wc[q][2] = a1;
+        d[q].csum = c1 | c2;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          blo[q][c] |= wc[q][c] << nbuf;
+          bhi[q][c] = nbuf ? (wc[q][c] >> (64 - nbuf)) : 0ull;
+        }
+      }
+      nbuf += 64;
+      ++wnext;
+    }
+    int fld[2][3];
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        fld[q][c] = (int)(blo[q][c] & fmask);
+        blo[q][c] = (blo[q][c] >> wd) | (bhi[q][c] << (64 - wd));
+        bhi[q][c] >>= wd;
+      }
+    nbuf -= wd;
+    if (pos < s) {
+#pragma unroll
       for (int c = 0; c < 2; ++c) {
-        uint64_t x = word_at_bit(d[q].M[c], L, 64 * (int64_t)w + d[q].sh[c]);
-        if (8 * w + 8 > s) x &= (s - 8 * w >= 8) ? ~0ull : ((1ull << (8 * (s - 8 * w))) - 1ull);   // |X| has 8s bits
-        if (d[q].neg[c]) {
-          const uint64_t t = ~x + d[q].cneg[c];
-          d[q].cneg[c] = (d[q].cneg[c] && t == 0) ? 1ull : 0ull;
-          x = t;
-        }
-        wc[q][c] = x;
-      }
-    uint64_t ws_[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const uint64_t a = wc[q][0] + wc[q][1];
-      const uint64_t c1 = a < wc[q][0];
-      const uint64_t b = a + d[q].csum;
-      const uint64_t c2 = b < a;
-      ws_[q] = b;
-      d[q].csum = c1 | c2;
-    }
-    for (int by = 0; by < 8; ++by) {
-      const int pos = 8 * w + by;
-      if (pos > s || (pos == s && !want_sum)) break;
-      if (pos < s) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          float f[2];
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int b = (int)((wc[q][c] >> (8 * by)) & 0xFF);
-            int dg;
-            if (pos == s - 1) {
-              dg = (int)(int8_t)(uint8_t)b + d[q].cbal[c];   // top digit: signed byte + carry
-            } else {
-              dg = b + d[q].cbal[c];
-              d[q].cbal[c] = dg >= 128;
-              if (dg >= 128) dg -= 256;
-            }
-            f[q] = (float)dg;
-          }
-          if (in_range) out[(int64_t)(c * s + (s - 1 - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
-          if (__ballot_sync(0xffffffffu, f[0] != 0.f || f[1] != 0.f) && leader) nz[c * s + (s - 1 - pos)] = 1;
-        }
-      }
-      if (want_sum) {
         float f[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const int S = (int)((ws_[q] >> (8 * by)) & 0xFF);
           int dg;
-          if (pos == s) {
-            dg = (int)(int8_t)(uint8_t)S + d[q].cbal_s;
+          if (pos == s - 1) {   // top digit: the signed field plus the carry
+            dg = (fld[q][c] >= half ? fld[q][c] - full : fld[q][c]) + d[q].cbal[c];
           } else {
-            dg = S + d[q].cbal_s;
-            d[q].cbal_s = dg >= 128;
-            if (dg >= 128) dg -= 256;
+            dg = fld[q][c] + d[q].cbal[c];
+            d[q].cbal[c] = dg >= half;
+            if (dg >= half) dg -= full;
           }
           f[q] = (float)dg;
         }
-        if (in_range) out[(int64_t)(2 * s + (s - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
-        if (__ballot_sync(0xffffffffu, f[0] != 0.f || f[1] != 0.f) && leader) nz[2 * s + (s - pos)] = 1;
+        if (in_range) out[(int64_t)(c * s + (s - 1 - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
+        if (__ballot_sync(0xffffffffu, f[0] != 0.f || f[1] != 0.f) && leader) nz[c * s + (s - 1 - pos)] = 1;
       }
+    }
+    if (want_sum) {
+      float f[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        int dg;
+        if (pos == s) {
+          dg = (fld[q][2] >= half ? fld[q][2] - full : fld[q][2]) + d[q].cbal_s;
+        } else {
+          dg = fld[q][2] + d[q].cbal_s;
+          d[q].cbal_s = dg >= half;
+          if (dg >= half) dg -= full;
+        }
+        f[q] = (float)dg;
+      }
+      if (in_range) out[(int64_t)(2 * s + (s - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
+      if (__ballot_sync(0xffffffffu, f[0] != 0.f || f[1] != 0.f) && leader) nz[2 * s + (s - pos)] = 1;
     }
   }
 }
@@ -245,7 +269,7 @@ __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64
 // (the group table then skips the slice pairs of all-zero planes), and
 // plane_nz[nplanes + c] when component c (re, im) has a nonzero value.
 __global__ void k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
-                            int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits,
+                            int wd, int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits,
                             int32_t *plane_nz) {
   __shared__ int nz[3 * kMaxSlices + 1 + 2];
   const int nflags = 2 * s + (want_sum ? s + 1 : 0) + 2;
@@ -254,7 +278,8 @@ __global__ void k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64
   const int64_t l0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
   const int64_t line = blockIdx.y;
   // kpad is even: l0 + 1 < kpad; out-of-range threads still take part in the warp votes
-  oz_digits_pair(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits, l0, line, l0 < kpad && line < lines, nz);
+  oz_digits_pair(X, side, lines, k, kpad, L, s, wd, want_sum, E, lossy, digits, l0, line, l0 < kpad && line < lines,
+                 nz);
   __syncthreads();
   for (int x = threadIdx.x; x < nflags; x += blockDim.x)
     if (nz[x]) atomicOr(plane_nz + x, 1);
@@ -346,11 +371,11 @@ void launch_line_max(const MatView &A, const MatView &B, int64_t m, int64_t n, i
   k_colmax<<<g, 128, 0, st>>>(B, k, n, L, rpb, F);
 }
 
-void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
+void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s, int wd,
                       int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, int32_t *plane_nz,
                       cudaStream_t st) {
   dim3 g((unsigned)((kpad / 2 + 127) / 128), (unsigned)lines);
-  k_oz_digits<<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits, plane_nz);
+  k_oz_digits<<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, wd, want_sum, E, lossy, digits, plane_nz);
 }
 
 void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, int L, int D, int DP, int W,

@@ -87,18 +87,23 @@ def test_shape_mismatch_and_workspace_checks(mp):
                        ctypes.c_void_p(0x100000), need, None) == 0
 
 
-@pytest.mark.parametrize("p,k,method,guard,s,Q", [
-    (128, 32, "4m", None, None, None), (256, 256, "4m", None, None, None), (256, 256, "3m", None, None, None),
-    (1024, 2048, "3m", None, None, None), (512, 1024, "4m", 8, None, None), (128, 9, "3m", 0, None, 3),
-    (128, 8, "4m", None, 10, 18), (192, 2048, "3m", None, 30, 33)])
-def test_plan_matches_the_oracle_parameters(mp, p, k, method, guard, s, Q):
-    """s, Q, group counts and bound constants of the C plan equal O2's."""
-    prm = ozaki.make_params(p, k, method, guard if guard is not None else ozaki.DEFAULT_GUARD, s, Q)
-    params = dict(guard_bits=guard or 0, slices=s or 0, cut_level=(Q + 1) if Q is not None else 0)
+@pytest.mark.parametrize("p,k,method,guard,s,Q,w", [
+    (128, 32, "4m", None, None, None, None), (256, 256, "4m", None, None, None, None),
+    (256, 256, "3m", None, None, None, None), (1024, 2048, "3m", None, None, None, None),
+    (1024, 2048, "3m", None, None, None, 8), (512, 1024, "4m", 8, None, None, None),
+    (128, 9, "3m", 0, None, 3, None), (128, 8, "4m", None, 10, 18, None), (192, 2048, "3m", None, 30, 33, 8),
+    (256, 40000, "4m", None, None, None, None)])
+def test_plan_matches_the_oracle_parameters(mp, p, k, method, guard, s, Q, w):
+    """Digit width, s, Q, group counts and bound constants of the C plan equal O2's
+    (w = 9 by default, 8 when k >= 2^15 or when asked for)."""
+    prm = ozaki.make_params(p, k, method, guard if guard is not None else ozaki.DEFAULT_GUARD, s, Q, w=w)
+    params = dict(guard_bits=guard or 0, slices=s or 0, cut_level=(Q + 1) if Q is not None else 0,
+                  digit_bits=w or 0)
     if guard == 0:
         params["guard_bits"] = 0
-        prm = ozaki.make_params(p, k, method, ozaki.DEFAULT_GUARD, s, Q)   # 0 means default in the ABI
+        prm = ozaki.make_params(p, k, method, ozaki.DEFAULT_GUARD, s, Q, w=w)   # 0 means default in the ABI
     pl = mp.plan(64, 48, k, p, method, "ozaki", params)
+    assert pl["digit_bits"] == prm.w == (w or (9 if k < 32768 else 8))
     assert (pl["s"], pl["Q"], pl["gmax"]) == (prm.s, prm.Q, prm.gmax)
     first = {"re": 0, "im": 0, "sum": -1}
     npos = {"re": prm.s, "im": prm.s, "sum": prm.s + 1}

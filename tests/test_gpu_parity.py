@@ -108,12 +108,16 @@ def test_plain_long_k_largest_sums(method):
 
 
 @pytest.mark.parametrize("method", ["4m", "3m"])
-def test_config1_stage_parity(method):
-    """256^3, p = 256: digits and every group sum equal O2; output equals O1."""
+@pytest.mark.parametrize("w", [9, 8])
+def test_config1_stage_parity(method, w):
+    """256^3, p = 256: digits and every group sum equal O2; output equals O1 (9- and
+    8-bit digits)."""
     A, B, p = si.make_config("c1_ozaki_256_p256")
-    C, ws, st = gu.run(A, B, p, method, "ozaki")
-    pl = gu.plan(A, B, p, method)
-    r = ozaki.ozaki_cgemm(A, B, p, method, fallback=lambda i, j: ((0, 0), (0, 0)))
+    params = dict(digit_bits=w)
+    C, ws, st = gu.run(A, B, p, method, "ozaki", params=params)
+    pl = gu.plan(A, B, p, method, params=params)
+    assert pl["digit_bits"] == w
+    r = ozaki.ozaki_cgemm(A, B, p, method, fallback=lambda i, j: ((0, 0), (0, 0)), w=w)
     s, kp, k = r.params.s, pl["kpad"], A.cols
     dA = gu.ws_digits(ws, pl, "A", A.rows)
     dB = gu.ws_digits(ws, pl, "B", B.cols)
@@ -212,6 +216,42 @@ def test_zero_digit_planes_are_skipped(method, case, kernel):
     if case == "real":
         assert r.certified[1].all() and st["fallback_entries"] == int((~r.certified[0]).sum())
     assert st["fallback_overflow"] == 0 and st["uncertified"] == 0
+
+
+def _digit_pattern_mantissa(top, low, s, w, L):
+    """Mantissa (exponent 0) whose w-bit balanced digits are top, then low repeated."""
+    R = 1 << w
+    X = top * R ** (s - 1) + sum(low * R ** (s - 1 - t) for t in range(1, s))
+    assert (1 << (w * s - 2)) <= X < (1 << (w * s - 1))    # the row maximum has exponent 0
+    assert ozaki.balanced_digits(X, s, w) == [top] + [low] * (s - 1)
+    sh = 64 * L + 1 - w * s                                  # a = X 2^(1 - ws) = M 2^(-64L)
+    M = X << sh if sh >= 0 else X >> (-sh)
+    assert (M << (-sh) if sh < 0 else M >> sh) == X and M >> (64 * L - 1) == 1
+    return [(M >> (64 * j)) & 0xFFFFFFFFFFFFFFFF for j in range(L)]
+
+
+@pytest.mark.parametrize("kernel", ["auto", "mma_sync"])
+@pytest.mark.parametrize("method", ["4m", "3m"])
+def test_largest_digits_fill_the_fp32_chunk_exactly(kernel, method):
+    """9-bit digits all -256 (top digit 200), equal signs, k = 512: every 256-element fp32
+    chunk of the tensor cores sums to exactly 2^24; group sums equal O2, output equals O1."""
+    p, k, s_ = 256, 512, 29
+    L = si.limbs_for(p)
+    limbs = _digit_pattern_mantissa(200, -256, s_, 9, L)
+    A = si.random_matrix(6, k, p, 361)
+    B = si.random_matrix(k, 5, p, 362)
+    for X in (A, B):
+        for j in range(L):
+            X.limb[:, j] = np.uint64(limbs[j])
+        X.sign[:] = 0
+        X.exp[:] = 0
+    B.sign[1] = 1
+    params = dict(kernel=kernel, slices=s_, digit_bits=9)
+    C, ws, st = gu.run(A, B, p, method, "ozaki", params=params)
+    pl = gu.plan(A, B, p, method, params=params)
+    r = ozaki.ozaki_cgemm(A, B, p, method, s=s_, w=9, fallback=lambda i, j: ((0, 0), (0, 0)))
+    _check_group_sums(ws, pl, r, A.rows, B.cols)
+    _check_against_o1(C, A, B, p)
 
 
 @pytest.mark.parametrize("kernel", ["auto", "tcgen05", "mma_sync"])

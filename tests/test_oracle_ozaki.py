@@ -17,27 +17,30 @@ from oracle import exact, ozaki
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def test_balanced_digits_reassemble():
+@pytest.mark.parametrize("w", [8, 9])
+def test_balanced_digits_reassemble(w):
+    R, h = 1 << w, 1 << (w - 1)
     rng = np.random.default_rng(3)
     for _ in range(2000):
         nd = int(rng.integers(1, 40))
-        lim = 1 << (8 * nd - 1)
-        X = int(rng.integers(-2**62, 2**62)) * (1 << int(rng.integers(0, max(1, 8 * nd - 63)))) % lim
+        lim = 1 << (w * nd - 1)
+        X = int(rng.integers(-2**62, 2**62)) * (1 << int(rng.integers(0, max(1, w * nd - 63)))) % lim
         X = X if rng.random() < 0.5 else -X
-        d = ozaki.balanced_digits(X, nd)
-        assert sum(v * 256 ** (nd - 1 - t) for t, v in enumerate(d)) == X
-        assert all(-128 <= v <= 127 for v in d[1:])
-        assert -128 <= d[0] <= 128
+        d = ozaki.balanced_digits(X, nd, w)
+        assert sum(v * R ** (nd - 1 - t) for t, v in enumerate(d)) == X
+        assert all(-h <= v <= h - 1 for v in d[1:])
+        assert -h <= d[0] <= h
     # extremes
-    for X in (2 ** 23 - 1, -(2 ** 23 - 1), 0, 1, -1, 128, -128, 127):
-        d = ozaki.balanced_digits(X, 3)
-        assert sum(v * 256 ** (2 - t) for t, v in enumerate(d)) == X
-    d = ozaki.balanced_digits(2 ** 23 - 1, 3)
-    assert d[0] == 128   # the top digit may reach +-128
+    for X in ((1 << (3 * w - 1)) - 1, -((1 << (3 * w - 1)) - 1), 0, 1, -1, h, -h, h - 1):
+        d = ozaki.balanced_digits(X, 3, w)
+        assert sum(v * R ** (2 - t) for t, v in enumerate(d)) == X
+    d = ozaki.balanced_digits((1 << (3 * w - 1)) - 1, 3, w)
+    assert d[0] == h   # the top digit may reach +-2^(w-1) (still exact in bf16 for w <= 9)
 
 
-def test_fixed_point_truncation():
-    """0 <= |a| 2^(8s-1-E) - |X| < 1 and |X| < 2^(8s-1) for |a| < 2^E."""
+@pytest.mark.parametrize("w", [8, 9])
+def test_fixed_point_truncation(w):
+    """0 <= |a| 2^(ws-1-E) - |X| < 1 and |X| < 2^(ws-1) for |a| < 2^E."""
     p = 256
     A = si.random_matrix(8, 12, p, 5, "uniform_exp")
     s = 20
@@ -48,10 +51,10 @@ def test_fixed_point_truncation():
                 v = exact.component(A, c, i, l)
                 a = abs(exact.to_fraction(v))
                 assert a < Fraction(2) ** E[i]
-                X, lossless = ozaki.fixed_point(v, E[i], s)
-                scaled = a * Fraction(2) ** (8 * s - 1 - E[i])
+                X, lossless = ozaki.fixed_point(v, E[i], s, w)
+                scaled = a * Fraction(2) ** (w * s - 1 - E[i])
                 assert 0 <= scaled - abs(X) < 1
-                assert abs(X) < 2 ** (8 * s - 1)
+                assert abs(X) < 2 ** (w * s - 1)
                 assert lossless == (scaled == abs(X))
                 assert (X < 0) == (v[0] < 0) or X == 0
 
@@ -90,13 +93,14 @@ def _exact_scaled(A, B, r):
 
 
 @pytest.mark.parametrize("method", ["4m", "3m"])
-def test_all_pairs_and_lossless_split_give_the_exact_product(method):
+@pytest.mark.parametrize("w", [8, 9])
+def test_all_pairs_and_lossless_split_give_the_exact_product(method, w):
     """Special case: P = every pair and no digit dropped -> Acc * 2^scale == T exactly."""
     p = 128
     A = si.random_matrix(5, 8, p, 12, "uniform_exp")
     B = si.random_matrix(8, 4, p, 13, "uniform_exp", zero_frac=0.1)
-    prm = ozaki.make_params(p, 8, method, guard=60)
-    r = ozaki.ozaki_cgemm(A, B, p, method, guard=60, Q=2 * prm.s + 2)
+    prm = ozaki.make_params(p, 8, method, guard=60, w=w)
+    r = ozaki.ozaki_cgemm(A, B, p, method, guard=60, Q=2 * prm.s + 2, w=w)
     assert all(r.splitA.lossless) and all(r.splitB.lossless)
     T = _exact_scaled(A, B, r)
     for comp in ("re", "im"):
@@ -110,12 +114,13 @@ def test_all_pairs_and_lossless_split_give_the_exact_product(method):
 
 @pytest.mark.parametrize("method,dist,guard", [("4m", "uniform", 8), ("3m", "uniform", 8),
                                                 ("4m", "uniform_exp", 0), ("3m", "uniform_exp", 4)])
-def test_truncation_bound_holds(method, dist, guard):
+@pytest.mark.parametrize("w", [8, 9])
+def test_truncation_bound_holds(method, dist, guard, w):
     """|Acc - T| <= b 2^beta for the paper's triangle, lossy split included."""
     p = 128
     A = si.random_matrix(6, 10, p, 14, dist)
     B = si.random_matrix(10, 5, p, 15, dist)
-    r = ozaki.ozaki_cgemm(A, B, p, method, guard=guard)
+    r = ozaki.ozaki_cgemm(A, B, p, method, guard=guard, w=w)
     T = _exact_scaled(A, B, r)
     worst = Fraction(0)
     for comp in ("re", "im"):
@@ -164,7 +169,8 @@ def test_bound_with_zero_planes_holds(method, case):
     assert exact.equal_arrays(r.C, exact.rounded_cgemm(A, B, p)) if hasattr(exact, "equal_arrays") else True
 
 
-def test_truncation_bound_is_attained_by_coherent_errors():
+@pytest.mark.parametrize("w", [8, 9])
+def test_truncation_bound_is_attained_by_coherent_errors(w):
     """All-ones mantissas truncate almost a full ulp each, all with one sign:
     the error then sits just below the split term of the bound (not far under it)."""
     p, k = 128, 16
@@ -178,7 +184,7 @@ def test_truncation_bound_is_attained_by_coherent_errors():
     B.exp[:, :, 0] = -2                 # both truncation errors with one sign
     B.sign[1, :, 0] = 1
     s_ = 10
-    r = ozaki.ozaki_cgemm(A, B, p, "4m", s=s_, Q=2 * s_ - 2)   # every pair kept: no dropped term
+    r = ozaki.ozaki_cgemm(A, B, p, "4m", s=s_, Q=2 * s_ - 2, w=w)   # every pair kept: no dropped term
     assert not r.splitA.lossless[0] and not r.splitB.lossless[0]
     T = _exact_scaled(A, B, r)
     b, beta = ozaki.entry_bound(r.params, r.splitA, r.splitB, 0, 0, "re")
@@ -312,24 +318,30 @@ def test_trimming_follows_the_smaller_part():
 
 
 def test_group_sums_fit_int32_at_the_limit():
-    """Gmax * k * 2^14 <= 2^31 - 1 for the largest supported k; worst-case digits."""
-    for k in (1, 7, 256, 2048, 131071):
+    """Gmax * k * 2^(2w-2) <= 2^31 - 1 for the largest supported k; worst-case digits
+    |d| = 2^(w-1).  9-bit digits up to k = 2^15 - 1, then 8-bit digits."""
+    for k in (1, 7, 256, 2048, 32767, 32768, 131071):
         prm = ozaki.make_params(256, k)
-        assert prm.gmax * k * (128 * 128) <= 2 ** 31 - 1
-        assert (prm.gmax + 1) * k * (128 * 128) > 2 ** 31 - 1 or prm.gmax == 2 ** 31 // (k << 14)
+        assert prm.w == (9 if k <= 32767 else 8)
+        big = (1 << (prm.w - 1)) ** 2
+        assert prm.gmax * k * big <= 2 ** 31 - 1
+        assert (prm.gmax + 1) * k * big > 2 ** 31 - 1
     with pytest.raises(ValueError):
         ozaki.make_params(256, 131072)
+    with pytest.raises(ValueError):
+        ozaki.make_params(256, 32768, w=9)
 
 
 @pytest.mark.parametrize("method", ["4m", "3m"])
 @pytest.mark.parametrize("dist,guard,zf", [("uniform", 40, 0.0), ("uniform_exp", 40, 0.1),
                                            ("uniform", 0, 0.0), ("uniform_exp", 2, 0.2)])
-def test_final_output_equals_o1(method, dist, guard, zf):
+@pytest.mark.parametrize("w", [8, 9])
+def test_final_output_equals_o1(method, dist, guard, zf, w):
     """Certified entries round Acc; the rest fall back to the exact value -> == O1."""
     p = 128
     A = si.random_matrix(7, 9, p, 18, dist, zero_frac=zf)
     B = si.random_matrix(9, 6, p, 19, dist, zero_frac=zf)
-    r = ozaki.ozaki_cgemm(A, B, p, method, guard=guard)
+    r = ozaki.ozaki_cgemm(A, B, p, method, guard=guard, w=w)
     assert exact.equal_arrays(r.C, exact.rounded_cgemm(A, B, p))
     if guard >= 40 and dist == "uniform":
         assert r.certified.all()
@@ -376,15 +388,16 @@ def test_table1_real_products_per_method():
 def _pins_pass(monkeypatch_ctx):
     """Run a compact version of the pins; True if all hold."""
     try:
-        test_balanced_digits_reassemble()
-        test_fixed_point_truncation()
+        for w in (8, 9):
+            test_balanced_digits_reassemble(w)
+            test_fixed_point_truncation(w)
         for method in ("4m", "3m"):
-            test_all_pairs_and_lossless_split_give_the_exact_product(method)
-            test_final_output_equals_o1(method, "uniform", 40, 0.0)
-            test_final_output_equals_o1(method, "uniform_exp", 0, 0.1)
-        test_truncation_bound_holds("3m", "uniform_exp", 4)
-        test_truncation_bound_holds("4m", "uniform", 8)
-        test_truncation_bound_is_attained_by_coherent_errors()
+            test_all_pairs_and_lossless_split_give_the_exact_product(method, 9)
+            test_final_output_equals_o1(method, "uniform", 40, 0.0, 9)
+            test_final_output_equals_o1(method, "uniform_exp", 0, 0.1, 9)
+        test_truncation_bound_holds("3m", "uniform_exp", 4, 9)
+        test_truncation_bound_holds("4m", "uniform", 8, 9)
+        test_truncation_bound_is_attained_by_coherent_errors(9)
     except AssertionError:
         return False
     return True
@@ -399,19 +412,19 @@ def _mutants():
     orig_bexp = ozaki.bound_exponent
 
     def digit_order(m):      # digits stored least significant first
-        m.setattr(ozaki, "balanced_digits", lambda X, nd: list(reversed(orig_bd(X, nd))))
-        m.setattr(ozaki, "balanced_digits_array", lambda X, nd: orig_bda(X, nd)[::-1].copy())
+        m.setattr(ozaki, "balanced_digits", lambda X, nd, w=9: list(reversed(orig_bd(X, nd, w))))
+        m.setattr(ozaki, "balanced_digits_array", lambda X, nd, w=9: orig_bda(X, nd, w)[::-1].copy())
 
     def level_shift(m):      # level weight off by one digit
-        m.setattr(ozaki, "accumulate", lambda gs, sums, Q: orig_acc(gs, sums, Q + 1))
+        m.setattr(ozaki, "accumulate", lambda gs, sums, Q, w=9: orig_acc(gs, sums, Q + 1, w))
 
     def split_rounding(m):   # magnitude rounded up instead of truncated
-        def fp(v, E, s):
-            X, ok = orig_fp(v, E, s)
+        def fp(v, E, s, w=9):
+            X, ok = orig_fp(v, E, s, w)
             return (X + (1 if X > 0 else -1 if X < 0 else 0)), ok
 
-        def fpa(N, x, E, s):
-            X, ok = orig_fpa(N, x, E, s)
+        def fpa(N, x, E, s, w=9):
+            X, ok = orig_fpa(N, x, E, s, w)
             return np.where(X > 0, X + 1, np.where(X < 0, X - 1, X)), ok
         m.setattr(ozaki, "fixed_point", fp)
         m.setattr(ozaki, "fixed_point_array", fpa)
@@ -420,7 +433,7 @@ def _mutants():
         m.setattr(ozaki, "drop_bound", lambda *a: 0)
 
     def bound_scale(m):      # bound expressed in the wrong unit (one digit too coarse)
-        m.setattr(ozaki, "bound_exponent", lambda prm: max(0, orig_bexp(prm) - 8))
+        m.setattr(ozaki, "bound_exponent", lambda prm: max(0, orig_bexp(prm) - prm.w))
 
     def im_sign(m):          # 3M imaginary part: + rr instead of - rr
         orig = ozaki.ozaki_cgemm
@@ -431,8 +444,8 @@ def _mutants():
         orig_acc2 = ozaki.accumulate
         state = {"n": 0}
 
-        def acc(gs, sums, Q):
-            v = orig_acc2(gs, sums, Q)
+        def acc(gs, sums, Q, w=9):
+            v = orig_acc2(gs, sums, Q, w)
             state["n"] += 1
             # products arrive in the order rr, ii, (ri, ir | ss); flip rr's sign
             return -v if state["n"] % (4 if False else 3) == 1 else v
