@@ -225,11 +225,12 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
 
 // One accumulation term per group, in order of descending level: plane index,
 // the two signs, and -- on the last group of a level -- the level's shift.
-struct Term {
+struct Term {        // packed in 8 bytes (the accumulation reads it as one 64-bit word)
   int32_t plane;
-  int16_t shift;    // 8 (Q - q) on the last group of level q, else -1
+  int16_t shift;    // w (Q - q) on the last group of level q, else -1
   int8_t s0, s1;
 };
+static_assert(sizeof(Term) == 8, "Term is read as one 64-bit word");
 
 // Round (or queue for the exact fallback) one component of one output element.
 __device__ __forceinline__ void finish_component(const AccumArgs &a, const OutView &C, Lazy &acc, uint32_t *words,
@@ -341,14 +342,17 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
     __syncthreads();
     if (active) {
       const int nb = a.n_entries - x0 < kAccBatch ? a.n_entries - x0 : kAccBatch;
+      const uint64_t *tw = reinterpret_cast<const uint64_t *>(terms) + x0;   // packed Term (8 bytes)
+#pragma unroll 4
       for (int u = 0; u < nb; ++u) {
-        const Term t = terms[x0 + u];   // block-uniform: the branches below do not diverge
-        const int64_t v = stage[buf][u][tid];
-        if (t.s0 > 0) sum0 += v; else if (t.s0 < 0) sum0 -= v;
-        if (t.s1 > 0) sum1 += v; else if (t.s1 < 0) sum1 -= v;
-        if (t.shift >= 0) {
-          acc[0].add(words[0], sum0, t.shift);
-          acc[1].add(words[1], sum1, t.shift);
+        const uint64_t t = tw[u];                  // block-uniform
+        const int32_t v = stage[buf][u][tid];     // |v| < 2^31: v * (+-1 | 0) fits int32
+        sum0 += (int64_t)(v * (int32_t)(int8_t)(t >> 48));
+        sum1 += (int64_t)(v * (int32_t)(int8_t)(t >> 56));
+        const int shift = (int)(int16_t)(t >> 32);
+        if (shift >= 0) {   // the last group of a level
+          acc[0].add(words[0], sum0, shift);
+          acc[1].add(words[1], sum1, shift);
           sum0 = sum1 = 0;
         }
       }
