@@ -71,7 +71,8 @@ extern "C" {
 /* ---- algorithm selection --------------------------------------------- */
 enum { MPC_4M = 0, MPC_3M = 1 };          /* Eq. (4m_way) / Eq. (3m_way) */
 enum { MPC_PLAIN = 0, MPC_OZAKI = 1 };    /* Eq. (simple_triple_loop) / Alg. 2 */
-enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2, MPC_KERNEL_TCGEN05_PAIR = 3 };
+enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2, MPC_KERNEL_TCGEN05_PAIR = 3,
+       MPC_KERNEL_TCGEN05_2SM = 4 };
 
 /* Largest supported precision and inner size. */
 #define MPC_MAX_P_BITS 1024
@@ -101,8 +102,10 @@ typedef struct mpc_mat {
  *               G_max); smaller groups make more, shorter work units.
  *   kernel      MPC_KERNEL_*: which slice-GEMM kernel (auto = tcgen05, in CTA pairs
  *               when m > 128; TCGEN05_PAIR always runs CTA pairs that share the B
- *               tile by TMA multicast, TCGEN05 single CTAs; the mma.sync
- *               kernel is a second, independent implementation of the same sums).
+ *               tile by TMA multicast, TCGEN05 single CTAs, TCGEN05_2SM CTA pairs
+ *               that run one 256-row MMA across both SMs, each holding half of B;
+ *               the mma.sync kernel is a second, independent implementation of the
+ *               same sums).
  */
 typedef struct mpc_oz_params {
     int32_t guard_bits;

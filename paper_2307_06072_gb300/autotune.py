@@ -1,10 +1,12 @@
 """Autotuner for the slice-GEMM configuration of a (batched) complex GEMM.
 
 The tunable parts are the work-unit shape and size: the tcgen05 kernel in
-single CTAs (128 x 256 output tiles) or in CTA pairs (256 x 256 tiles, the B
-tile shared by multicast), and the cap on slice pairs per group (smaller groups
-give more, shorter units, which balances small problems better; the int32
-limit is the largest).  The k-block (64 bf16 = one 128-byte swizzled row) is
+single CTAs (128 x 256 output tiles), in CTA pairs (256 x 256 tiles, the B
+tile shared by multicast) or in CTA pairs running one cta_group::2 MMA (each
+SM holds half of B; pays off with the longer fp32 chunks of 8-bit digits),
+the digit width, and the cap on slice pairs per group (smaller groups give
+more, shorter units, which balances small problems better; the int32 limit
+is the largest).  The k-block (64 bf16 = one 128-byte swizzled row) is
 fixed by the kernel.  Every candidate computes the same exact result, so the
 tuner simply times each one on the caller's data once and caches the winner
 per problem signature.
@@ -20,7 +22,8 @@ CANDIDATES = (
     {"kernel": "tcgen05"},
     {"kernel": "tcgen05_pair"},
     {"kernel": "auto", "max_group": 16},
-    {"kernel": "auto", "max_group": 4},
+    {"kernel": "tcgen05_2sm"},
+    {"kernel": "tcgen05_2sm", "digit_bits": 8},
 )
 
 

@@ -56,7 +56,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   P.p_bits = p;
   P.limbs = L;
   out->kernel = prm ? prm->kernel : MPC_KERNEL_AUTO;
-  if (out->kernel < MPC_KERNEL_AUTO || out->kernel > MPC_KERNEL_TCGEN05_PAIR) return MPC_EINVAL;
+  if (out->kernel < MPC_KERNEL_AUTO || out->kernel > MPC_KERNEL_TCGEN05_2SM) return MPC_EINVAL;
   uint64_t off = 0;
   P.off_status = off;
   off = align256(off + kStatusWords * 4);
@@ -485,7 +485,7 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_
         launch_slicegemm_mma(sa, st);
       } else {   // auto: the tcgen05 kernel, in CTA pairs when there are at least two row tiles
         const int pair = c.pl.kernel == MPC_KERNEL_TCGEN05_PAIR || (c.pl.kernel == MPC_KERNEL_AUTO && c.m > 128);
-        const cudaError_t e = launch_slicegemm_tc(sa, st, pair ? 2 : 1);
+        const cudaError_t e = launch_slicegemm_tc(sa, st, c.pl.kernel == MPC_KERNEL_TCGEN05_2SM ? 3 : pair ? 2 : 1);
         if (e == cudaErrorNotSupported && c.pl.kernel == MPC_KERNEL_AUTO) launch_slicegemm_mma(sa, st);
         else if (e != cudaSuccess) return e == cudaErrorNotSupported ? MPC_ENOTSUP : cuda_code(e);
       }
@@ -554,7 +554,8 @@ int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *pa
   }
   if (!slices.empty()) {   // one persistent launch for every Ozaki problem (48 per launch)
     const int pair = kernel == MPC_KERNEL_TCGEN05_PAIR || (kernel == MPC_KERNEL_AUTO && any_tall);
-    const cudaError_t e = launch_slicegemm_tc_batch(slices.data(), (int)slices.size(), st, pair ? 2 : 1);
+    const cudaError_t e = launch_slicegemm_tc_batch(slices.data(), (int)slices.size(), st,
+                                                    kernel == MPC_KERNEL_TCGEN05_2SM ? 3 : pair ? 2 : 1);
     if (e == cudaErrorNotSupported && kernel == MPC_KERNEL_AUTO) {
       for (const SliceGemmArgs &sa : slices) launch_slicegemm_mma(sa, st);
     } else if (e != cudaSuccess) {

@@ -40,15 +40,28 @@ namespace mpc {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int BM = 128, BN = 256, BK = 64;
+
+// Per variant: CL = 1 single CTAs; CL = 2 CTA pairs with cta_group::1 MMAs (each CTA
+// holds the whole 256-row B tile, half of it multicast by the peer); CL = 3 CTA pairs
+// with one cta_group::2 MMA of M = 256 (each CTA holds only its half of B: the tensor
+// cores read the other half from the peer's shared memory).
+template <int CL>
+struct TcCfg {
+  static constexpr bool kTwoSm = CL == 3;
+  static constexpr int kPair = CL == 1 ? 1 : 2;              // CTAs per unit
+  static constexpr int STAGES = kTwoSm ? 6 : 4;
+  static constexpr int B_ROWS = kTwoSm ? BN / 2 : BN;        // B rows in this CTA's shared memory
+  static constexpr int A_BYTES = BM * BK * 2, B_BYTES = B_ROWS * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int PAD = kTwoSm ? 16384 : 0;             // slack behind the last B stage
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + PAD + 512;
+};
 constexpr int NUM_THREADS = 320, EPI_WARPS = 8;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long kTimeoutCycles = 4000000000ll;   // ~2 s at 2 GHz
 constexpr int URING = 4;                               // unit-index ring slots
 constexpr int kMaxBatch = 48;                          // problems per launch (kernel parameter space)
 constexpr int kStUnitCounter = 8;                      // status word used as the unit counter
-constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256;
 
 // One launch serves a set of up to kMaxBatch independent problems (a single
 // GEMM is a set of one): their units are numbered consecutively and each
@@ -184,6 +197,17 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity
   return true;
 }
 
+// TMA load into this CTA's shared memory whose completion is signalled on a barrier that
+// may sit in the peer CTA of the pair (shared::cluster address)
+__device__ __forceinline__ void tma_load_3d_pair(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                                 uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
 // TMA load multicast to the CTAs in `mask`: same shared-memory offset and barrier offset in each
 __device__ __forceinline__ void tma_load_3d_mc(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
                                                uint64_t *bar, uint16_t mask) {
@@ -215,6 +239,27 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+// The same for a CTA pair: M = 256 rows, the leader's 128 in its TMEM, the peer's 128 in
+// the peer's TMEM at the same address; A and B are read from both CTAs' shared memory.
+constexpr uint32_t kIdesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                             ((uint32_t)((2 * BM) >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16_2sm(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc2), "r"(accumulate));
+}
+
+// arrive on the barrier at this offset in every CTA of `mask` once the pair's MMAs complete
+__device__ __forceinline__ void mma_commit_2sm_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -254,20 +299,21 @@ struct Unit {
   int prob;
 };
 
-// unit u -> (group, tile); with CL = 2 a unit is a pair of row tiles, CTA `rank` takes one
+// unit u -> (group, tile); for CTA pairs a unit is a pair of row tiles, CTA `rank` takes one
 template <int CL>
 __device__ __forceinline__ Unit decode(const TcParams &P, int64_t u, uint32_t rank) {
+  constexpr int CP = TcCfg<CL>::kPair;
   Unit x;
   int pi = 0;
   while (pi + 1 < P.count && P.prob[pi + 1].unit0 <= u) ++pi;
   const TcProblem &q = P.prob[pi];
   const int64_t r = u - q.unit0;
-  const int tiles_mu = (q.tiles_m + CL - 1) / CL;
+  const int tiles_mu = (q.tiles_m + CP - 1) / CP;
   const int tiles = tiles_mu * q.tiles_n;
   x.prob = pi;
   x.e = q.sched ? q.sched[r / tiles] : (int)(r / tiles);
   const int t = (int)(r % tiles);
-  x.tm = (t / q.tiles_n) * CL + (int)rank;
+  x.tm = (t / q.tiles_n) * CP + (int)rank;
   x.tn = t % q.tiles_n;
   x.g = q.groups[x.e];
   x.pd = q.prod[x.g.prod];
@@ -282,7 +328,7 @@ __device__ __forceinline__ bool unit_empty(const TcParams &P, int64_t u) {
   while (pi + 1 < P.count && P.prob[pi + 1].unit0 <= u) ++pi;
   const TcProblem &q = P.prob[pi];
   const int64_t r = u - q.unit0;
-  const int tiles = ((q.tiles_m + CL - 1) / CL) * q.tiles_n;
+  const int tiles = ((q.tiles_m + TcCfg<CL>::kPair - 1) / TcCfg<CL>::kPair) * q.tiles_n;
   const int e = q.sched ? q.sched[r / tiles] : (int)(r / tiles);
   return q.groups[e].count == 0;
 }
@@ -299,11 +345,13 @@ __device__ __forceinline__ bool unit_empty(const TcParams &P, int64_t u) {
 template <int CL>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_slicegemm_tc(const __grid_constant__ TcMaps maps, const __grid_constant__ TcParams P) {
+  using C = TcCfg<CL>;
+  constexpr int STAGES = C::STAGES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   uint8_t *sA = smem;
   uint8_t *sB = smem + STAGES * A_BYTES;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES + C::PAD);
   uint64_t *empty = full + STAGES;
   uint64_t *tfull = empty + STAGES;
   uint64_t *tempty = tfull + 2;
@@ -314,19 +362,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   volatile int *uring = reinterpret_cast<volatile int *>(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = CL == 2 ? cluster_rank() : 0u;
+  const uint32_t rank = CL >= 2 ? cluster_rank() : 0u;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CL);
+      mbar_init(&empty[s], CL == 2 ? 2 : 1);   // CL = 2: both CTAs' MMAs; else one (multicast) commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], EPI_WARPS);
+      mbar_init(&tempty[b], CL == 3 ? 2 * EPI_WARPS : EPI_WARPS);   // CL = 3: both CTAs drain the leader's MMA
     }
     for (int r = 0; r < URING; ++r) {
       mbar_init(&ufull[r], 1);
-      mbar_init(&uempty[r], CL == 2 ? 2 * (1 + EPI_WARPS) + 1 : 1 + EPI_WARPS);
+      mbar_init(&uempty[r], CL >= 2 ? 2 * (1 + EPI_WARPS) + 1 : 1 + EPI_WARPS);
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -336,18 +384,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if (CL == 3) {   // one warp of each CTA of the pair allocates, collectively
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
-  if (CL == 2) cluster_sync();   // every barrier of both CTAs initialised before any remote use
+  if (CL >= 2) cluster_sync();   // every barrier of both CTAs initialised before any remote use
   else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // the unit ring is filled by the leader (rank 0); everyone releases slots on the leader's barrier
-  const uint32_t uempty_leader = CL == 2 ? mapa(smem_u32(uempty), 0) : smem_u32(uempty);
+  const uint32_t uempty_leader = CL >= 2 ? mapa(smem_u32(uempty), 0) : smem_u32(uempty);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -365,7 +420,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           u = v >= P.units ? -1 : (int)v;
           uring[slot] = u;
           mbar_arrive(&ufull[slot]);
-          if (CL == 2) {
+          if (CL >= 2) {
             st_cluster_u32(mapa(smem_u32((const void *)&uring[slot]), 1), (uint32_t)u);
             mbar_arrive_cluster(mapa(smem_u32(&ufull[slot]), 1));
           }
@@ -386,6 +441,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const int planeA = x.pd.a_plane0 + t - x.pd.a_pos0;
           const int planeB = x.pd.b_plane0 + uu - x.pd.b_pos0;
           if (!mbar_wait(&empty[stage], phase ^ 1, abort, P.status)) { ok = false; break; }
+          if (CL == 3) {   // both CTAs' copies complete on the leader's stage barrier
+            const uint32_t fb = mapa(smem_u32(&full[stage]), 0);
+            if (rank == 0) mbar_expect_tx(&full[stage], 2 * STAGE_BYTES);
+            tma_load_3d_pair(sA + stage * A_BYTES, tmA, k0, x.tm * BM, planeA, fb);
+            tma_load_3d_pair(sB + stage * B_BYTES, tmB, k0, x.tn * BN + (int)rank * (BN / 2), planeB, fb);
+            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+            continue;
+          }
           mbar_expect_tx(&full[stage], STAGE_BYTES);
           tma_load_3d(sA + stage * A_BYTES, tmA, k0, x.tm * BM, planeA, &full[stage]);
           if (CL == 1) {
@@ -402,6 +465,60 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           mbar_drain(&full[s], 0);
           mbar_drain(&full[s], 1);
         }
+      }
+    }
+  } else if (warp == 1 && CL == 3) {
+    if (lane == 0 && rank == 0) {
+      // ---------------- MMA issuer of the pair (leader): M = 256 across both CTAs
+      int stage = 0, buf = 0, slot = 0;
+      uint32_t phase = 0, tphase = 0, uphase = 0;
+      bool ok = true;
+      while (ok) {
+        if (!mbar_wait_cluster(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
+        const int u = uring[slot];
+        mbar_arrive_cluster(uempty_leader + 8u * (uint32_t)slot);
+        if (++slot == URING) { slot = 0; uphase ^= 1; }
+        if (u < 0) break;
+        const Unit x = decode<CL>(P, u, rank);
+        const int ck = P.prob[x.prob].chunk_kb;
+        for (int c0 = 0; c0 < x.nkb && ok; c0 += ck) {
+          const int cend = min(x.nkb, c0 + ck);
+          // both CTAs' epilogues have drained this accumulator
+          if (!mbar_wait_cluster(&tempty[buf], tphase ^ 1, abort, P.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+          for (int kb = c0; kb < cend; ++kb) {
+            // both CTAs' halves of the stage have landed (the peer's copies signal here too)
+            if (!mbar_wait_cluster(&full[stage], phase, abort, P.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t ad = smem_desc(sA + stage * A_BYTES);
+            const uint64_t bd = smem_desc(sB + stage * B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              mma_f16_2sm(d_tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb > c0 || kk > 0) ? 1u : 0u);
+            mma_commit_2sm_mc(&empty[stage], (uint16_t)0x3);   // both producers may refill the stage
+            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          mma_commit_2sm_mc(&tfull[buf], (uint16_t)0x3);       // both epilogues may drain
+          buf ^= 1;
+          if (buf == 0) tphase ^= 1;
+        }
+      }
+      if (!ok) {   // wait for the MMAs already issued before TMEM is freed
+        mma_commit_2sm_mc(&tfull[buf], (uint16_t)0x3);
+        mbar_drain(&tfull[buf], tphase);
+      }
+    } else if (lane == 0) {
+      // ---------------- peer: no MMA to issue; only takes its turn on the unit ring
+      int slot = 0;
+      uint32_t uphase = 0;
+      while (true) {
+        if (!mbar_wait_cluster(&ufull[slot], uphase, abort, P.status)) break;
+        const int u = uring[slot];
+        mbar_arrive_cluster(uempty_leader + 8u * (uint32_t)slot);
+        if (++slot == URING) { slot = 0; uphase ^= 1; }
+        if (u < 0) break;
       }
     }
   } else if (warp == 1) {
@@ -479,7 +596,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[buf]);
+        if (lane == 0) {   // CL = 3: the peer's warps release the buffer on the leader's barrier
+          if (CL == 3 && rank == 1) mbar_arrive_cluster(mapa(smem_u32(&tempty[buf]), 0));
+          else mbar_arrive(&tempty[buf]);
+        }
         buf ^= 1;
         if (buf == 0) tphase ^= 1;
       }
@@ -506,13 +626,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if (CL == 3) cluster_sync();   // the leader's MMAs into the peer's TMEM are all drained
   if (warp == 1) {
     tc_fence_after();
     __syncwarp();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
-                 : "memory");
+    if (CL == 3)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                   : "memory");
   }
-  if (CL == 2) cluster_sync();   // neither CTA leaves while its peer may still signal it
+  if (CL >= 2) cluster_sync();   // neither CTA leaves while its peer may still signal it
 }
 
 // ------------------------------------------------------------------ host side
@@ -562,6 +687,7 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
   static TcMaps maps;    // host staging of the kernel parameters (copied at launch)
   static TcParams P;
   std::memset(&P, 0, sizeof(P));
+  const int pair = cluster == 1 ? 1 : 2;   // CTAs per unit
   int64_t units = 0;
   for (int q = 0; q < count; ++q) {
     const SliceGemmArgs &a = list[q];
@@ -571,7 +697,7 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
       if (a.prod[x].b_plane0 + a.prod[x].b_npos > planes_b) planes_b = a.prod[x].b_plane0 + a.prod[x].b_npos;
     }
     if (!make_map(&maps.a[q], a.dA, a.m, a.kpad, planes_a, BM) ||
-        !make_map(&maps.b[q], a.dB, a.n, a.kpad, planes_b, cluster == 2 ? BN / 2 : BN))
+        !make_map(&maps.b[q], a.dB, a.n, a.kpad, planes_b, cluster == 1 ? BN : BN / 2))
       return cudaErrorNotSupported;
     TcProblem &t = P.prob[q];
     t.m = a.m;
@@ -585,26 +711,27 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
     t.sched = a.sched;
     t.out = a.out;
     for (int x = 0; x < 4; ++x) t.prod[x] = a.prod[x];
-    units += (int64_t)a.n_entries * ((t.tiles_m + cluster - 1) / cluster) * t.tiles_n;
+    units += (int64_t)a.n_entries * ((t.tiles_m + pair - 1) / pair) * t.tiles_n;
   }
   P.count = count;
   P.units = units;
   P.status = list[0].status;
   if (units == 0) return cudaSuccess;
-  static bool attr[3] = {false, false, false};
-  auto kfn = cluster == 2 ? k_slicegemm_tc<2> : k_slicegemm_tc<1>;
+  static bool attr[4] = {false, false, false, false};
+  auto kfn = cluster == 3 ? k_slicegemm_tc<3> : cluster == 2 ? k_slicegemm_tc<2> : k_slicegemm_tc<1>;
+  const size_t smem = cluster == 3 ? TcCfg<3>::SMEM : cluster == 2 ? TcCfg<2>::SMEM : TcCfg<1>::SMEM;
   if (!attr[cluster]) {
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr[cluster] = true;
   }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute la[1];
   cfg.blockDim = dim3(NUM_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   int ctas = num_sms();
-  if (cluster == 2) {
+  if (pair == 2) {
     la[0].id = cudaLaunchAttributeClusterDimension;
     la[0].val.clusterDim.x = 2;
     la[0].val.clusterDim.y = 1;
@@ -612,12 +739,13 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
     cfg.attrs = la;
     cfg.numAttrs = 1;
     cfg.gridDim = dim3((unsigned)ctas, 1, 1);
-    static int clusters = 0;      // queried once (also keeps the call free of queries under graph capture)
-    if (clusters == 0 && (cudaOccupancyMaxActiveClusters(&clusters, kfn, &cfg) != cudaSuccess || clusters < 1))
-      clusters = ctas / 2;
-    ctas = 2 * clusters;
+    static int clusters[4] = {0, 0, 0, 0};   // queried once per variant (also keeps graph capture query-free)
+    if (clusters[cluster] == 0 &&
+        (cudaOccupancyMaxActiveClusters(&clusters[cluster], kfn, &cfg) != cudaSuccess || clusters[cluster] < 1))
+      clusters[cluster] = ctas / 2;
+    ctas = 2 * clusters[cluster];
   }
-  const int64_t need = units * cluster;
+  const int64_t need = units * pair;
   if (need < ctas) ctas = (int)need;
   cfg.gridDim = dim3((unsigned)ctas, 1, 1);
   return cudaLaunchKernelEx(&cfg, kfn, maps, P);
@@ -629,7 +757,7 @@ cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cuda
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   if (major != 10 || minor != 3) return cudaErrorNotSupported;   // built for sm_103a only
-  if (cluster != 1 && cluster != 2) return cudaErrorInvalidValue;
+  if (cluster < 1 || cluster > 3) return cudaErrorInvalidValue;
   static std::mutex mu;            // the parameter staging below is shared
   std::lock_guard<std::mutex> lock(mu);
   for (int q0 = 0; q0 < count; q0 += kMaxBatch) {
