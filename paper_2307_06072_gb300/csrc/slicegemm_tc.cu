@@ -50,11 +50,10 @@ template <int CL>
 struct TcCfg {
   static constexpr bool kTwoSm = CL == 3;
   static constexpr int kPair = CL == 1 ? 1 : 2;              // CTAs per unit
-  static constexpr int STAGES = kTwoSm ? 6 : 4;
+  static constexpr int STAGES = kTwoSm ? 7 : 4;
   static constexpr int B_ROWS = kTwoSm ? BN / 2 : BN;        // B rows in this CTA's shared memory
   static constexpr int A_BYTES = BM * BK * 2, B_BYTES = B_ROWS * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int PAD = kTwoSm ? 16384 : 0;             // slack behind the last B stage
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + PAD + 512;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 512;   // 7 x 32 KB + barriers <= 227 KB
 };
 constexpr int NUM_THREADS = 320, EPI_WARPS = 8;
 constexpr uint32_t TMEM_COLS = 512;
@@ -165,6 +164,14 @@ __device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
 
 __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// Arrive without release semantics: only for a signal that publishes no memory writes
+// (the peer's epilogue handing back a TMEM buffer whose reads tcgen05.wait::ld has
+// already completed).  The release form waits on the order of a thousand cycles per
+// call, longer than the epilogue spends draining a chunk.
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
@@ -351,7 +358,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   uint8_t *sA = smem;
   uint8_t *sB = smem + STAGES * A_BYTES;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES + C::PAD);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
   uint64_t *empty = full + STAGES;
   uint64_t *tfull = empty + STAGES;
   uint64_t *tempty = tfull + 2;
@@ -597,7 +604,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {   // CL = 3: the peer's warps release the buffer on the leader's barrier
-          if (CL == 3 && rank == 1) mbar_arrive_cluster(mapa(smem_u32(&tempty[buf]), 0));
+          if (CL == 3 && rank == 1) mbar_arrive_cluster_relaxed(mapa(smem_u32(&tempty[buf]), 0));
           else mbar_arrive(&tempty[buf]);
         }
         buf ^= 1;
