@@ -225,12 +225,19 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
 
 // One accumulation term per group, in order of descending level: plane index,
 // the two signs, and -- on the last group of a level -- the level's shift.
-struct Term {        // packed in 8 bytes (the accumulation reads it as one 64-bit word)
+struct __align__(16) Term {   // 16 bytes: the accumulation reads it as one int4
   int32_t plane;
-  int16_t shift;    // w (Q - q) on the last group of level q, else -1
-  int8_t s0, s1;
+  int32_t shift;    // w (Q - q) on the last group of level q, else -1
+  int32_t s0, s1;   // the group's sign in the real / imaginary part: -1, 0 or 1
 };
-static_assert(sizeof(Term) == 8, "Term is read as one 64-bit word");
+static_assert(sizeof(Term) == 16, "Term is read as one int4");
+
+// acc + (int64) v * s in one instruction
+__device__ __forceinline__ int64_t mad_wide(int32_t v, int32_t s, int64_t acc) {
+  int64_t r;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(r) : "r"(v), "r"(s), "l"(acc));
+  return r;
+}
 
 // Round (or queue for the exact fallback) one component of one output element.
 __device__ __forceinline__ void finish_component(const AccumArgs &a, const OutView &C, Lazy &acc, uint32_t *words,
@@ -289,9 +296,8 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
     const bool last = (x + 1 == a.n_entries) || (a.groups[a.order[x + 1]].q != g.q);
     const bool empty = g.count == 0;   // all its pairs were zero: its plane was never written
     const bool z0 = a.bounds[6] != 0, z1 = a.bounds[7] != 0;   // components that vanish identically
-    terms[x] = Term{empty ? -1 : e, (int16_t)(last ? a.w * (a.Q - g.q) : -1),
-                    (int8_t)(empty || z0 ? 0 : product_sign(a.method, 0, g.prod)),
-                    (int8_t)(empty || z1 ? 0 : product_sign(a.method, 1, g.prod))};
+    terms[x] = Term{empty ? -1 : e, last ? a.w * (a.Q - g.q) : -1, empty || z0 ? 0 : product_sign(a.method, 0, g.prod),
+                    empty || z1 ? 0 : product_sign(a.method, 1, g.prod)};
   }
   const int64_t i = blockIdx.y;
   const int64_t j0 = (int64_t)blockIdx.x * kAccT, j = j0 + tid;
@@ -342,17 +348,16 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
     __syncthreads();
     if (active) {
       const int nb = a.n_entries - x0 < kAccBatch ? a.n_entries - x0 : kAccBatch;
-      const uint64_t *tw = reinterpret_cast<const uint64_t *>(terms) + x0;   // packed Term (8 bytes)
+      const int4 *tv = reinterpret_cast<const int4 *>(terms) + x0;   // Term as (plane, shift, s0, s1)
 #pragma unroll 4
       for (int u = 0; u < nb; ++u) {
-        const uint64_t t = tw[u];                  // block-uniform
-        const int32_t v = stage[buf][u][tid];     // |v| < 2^31: v * (+-1 | 0) fits int32
-        sum0 += (int64_t)(v * (int32_t)(int8_t)(t >> 48));
-        sum1 += (int64_t)(v * (int32_t)(int8_t)(t >> 56));
-        const int shift = (int)(int16_t)(t >> 32);
-        if (shift >= 0) {   // the last group of a level
-          acc[0].add(words[0], sum0, shift);
-          acc[1].add(words[1], sum1, shift);
+        const int4 t = tv[u];                      // block-uniform
+        const int32_t v = stage[buf][u][tid];
+        sum0 = mad_wide(v, t.z, sum0);
+        sum1 = mad_wide(v, t.w, sum1);
+        if (t.y >= 0) {   // the last group of a level
+          acc[0].add(words[0], sum0, t.y);
+          acc[1].add(words[1], sum1, t.y);
           sum0 = sum1 = 0;
         }
       }
