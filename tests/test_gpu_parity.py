@@ -386,6 +386,24 @@ def test_config2_2048_p1024_3m_sampled():
 
 
 @pytest.mark.parametrize("method", ["4m", "3m"])
+def test_long_k_switches_to_8bit_digits(method):
+    """k >= 2^15: one 9-bit slice pair could reach k 2^16 > 2^31, so the plan takes
+    8-bit digits (groups of 3 pairs at k = 40000, 15-k-block chunks); every entry is
+    checked against the exact C oracle."""
+    k, p = 40000, 128
+    A = si.random_matrix(8, k, p, 371, "uniform_exp")
+    B = si.random_matrix(k, 6, p, 372, "uniform_exp")
+    pl = gu.plan(A, B, p, method)
+    assert pl["digit_bits"] == 8 and pl["gmax"] == 3
+    C, ws, st = gu.run(A, B, p, method, "ozaki")
+    assert st["uncertified"] == 0 and st["fallback_overflow"] == 0 and st["device_timeout"] == 0
+    ent = np.array([(i, j) for i in range(A.rows) for j in range(B.cols)])
+    sg, ex, li = c_oracle.rounded_cgemm(A, B, p, ent)
+    gs, ge, gl = gu.take_entries(C, ent)
+    assert np.array_equal(gs, sg) and np.array_equal(ge, ex) and np.array_equal(gl, li)
+
+
+@pytest.mark.parametrize("method", ["4m", "3m"])
 def test_plain_1024_p512_sampled(method):
     A, B, p = si.make_config("c2_1024_p512")
     C, ws, st = gu.run(A, B, p, method, "plain")
