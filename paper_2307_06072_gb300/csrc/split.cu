@@ -107,26 +107,41 @@ __device__ __forceinline__ uint64_t word_at_bit(const uint64_t *M, int L, int64_
   return off ? ((lo >> off) | (hi << (64 - off))) : lo;
 }
 
-// Per element: the shifted magnitude |X| = M >> sh, read 64 bits at a time
-// as a two's-complement word stream of X = sign |X|, and turned into balanced
-// base-256 digits (and, for 3M, the digits of X_re + X_im).
-struct DigitStream {
-  uint64_t M[2][kMaxLimbs];
-  int64_t sh[2];
-  int neg[2];
-  uint64_t cneg[2];      // +1 carry of the two's complement
-  uint64_t csum;         // carry of X_re + X_im
-  int cbal[2], cbal_s;   // balanced-digit carries
+// Per element and component: the shifted magnitude |X| = M >> sh (M the L-limb
+// mantissa, sh may be negative), read 64 bits at a time, least significant first,
+// straight from the input limbs: word w of |X| is bits [64 w + sh, 64 w + sh + 64)
+// of M, i.e. limbs w + floor(sh / 64) and the next one; the next one is kept for
+// the following word, so every limb is loaded once and nothing is held in memory
+// indexed at run time.
+struct LimbStream {
+  const uint64_t *p;   // limb 0 of the element (limb j at p[j * stride])
+  int64_t j;           // index of the limb in `cur`
+  uint64_t cur;
+  int off;             // sh mod 64
+  bool live;
+  __device__ __forceinline__ uint64_t limb(int64_t jj, int64_t stride, int L) const {
+    return (live && jj >= 0 && jj < L) ? p[jj * stride] : 0ull;
+  }
+  __device__ __forceinline__ void start(const uint64_t *base, bool nz, int64_t sh, int64_t stride, int L) {
+    p = base;
+    live = nz;
+    off = (int)(sh & 63);
+    j = sh >> 6;   // floor
+    cur = limb(j, stride, L);
+  }
+  __device__ __forceinline__ uint64_t next(int64_t stride, int L) {
+    const uint64_t hi = limb(j + 1, stride, L);
+    const uint64_t x = off ? ((cur >> off) | (hi << (64 - off))) : cur;
+    cur = hi;
+    ++j;
+    return x;
+  }
 };
 
 // One thread per (line, l, l+1): digits of two adjacent elements of a line.
 // Side A: line = row i, element (i, l).  Side B: line = column j, element (l, j).
 // Output planes: digits[(plane * lines + line) * kpad + l], plane = t (real),
 // s + t (imaginary), 2s + 1 + t (sums, t = -1 .. s-1).
-// Two elements (l0, l0 + 1) of one line.  Every thread of a warp runs the whole
-// digit loop (an element out of range or zero gives zero digits and no stores),
-// so that one warp vote per plane marks in nz[] the planes that got a nonzero
-// digit, and nz[nplanes + c] when a nonzero value of component c was seen.
 __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad,
                                                int L, int s, int wd, int want_sum, const int32_t *E, int32_t *lossy,
                                                __nv_bfloat16 *digits, int64_t l0, int64_t line, bool in_range,
@@ -137,36 +152,44 @@ __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64
   const int64_t pstride2 = pstride / 2;
   const int nplanes = 2 * s + (want_sum ? s + 1 : 0);
   const int32_t e_line = in_range ? E[line] : INT32_MIN;
-  DigitStream d[2];
+  const int64_t xbits = (int64_t)wd * s;                 // |X| < 2^(xbits - 1)
+  LimbStream m[2][2];                                    // [element][re, im]
+  bool neg[2][2];
+  uint64_t cneg[2][2], csum[2];                          // two's-complement and X_re + X_im carries
+  int cbal[2][2], cbal_s[2];                             // balanced-digit carries
   bool ok = true;
-  bool any = false;
   bool nzv[2] = {false, false};   // a nonzero real / imaginary value among the two elements
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int64_t l = l0 + q;
     const bool live = in_range && (l < k) && (e_line != INT32_MIN);
-    any |= live;
     const int64_t idx = side == 0 ? line * X.ld + l : l * X.ld + line;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      const bool nz = live && comp_nonzero(X, c, idx, L);
-      if (nz) nzv[c] = true;
-      for (int j = 0; j < L; ++j) d[q].M[c][j] = nz ? X.limb[c][(int64_t)j * X.plane + idx] : 0ull;
-      // |X| bit b  <->  M bit b + sh:  X = |v| 2^(8s-1-E), |v| = M 2^(exp-64L)
-      d[q].sh[c] = nz ? (64 * (int64_t)L + (int64_t)e_line - (int64_t)X.exp[c][idx] - ((int64_t)wd * s - 1)) : 0;
-      d[q].neg[c] = nz ? X.sign[c][idx] : 0;
-      d[q].cneg[c] = 1;
-      d[q].cbal[c] = 0;
-      if (nz) {
-        if (d[q].sh[c] >= 64 * (int64_t)L) ok = false;                  // every bit dropped (M != 0)
-        else if (!low_bits_zero(d[q].M[c], L, d[q].sh[c])) ok = false;  // some low bits dropped
+      const bool nzc = live && comp_nonzero(X, c, idx, L);
+      if (nzc) nzv[c] = true;
+      // |X| bit b  <->  M bit b + sh:  X = |v| 2^(ws-1-E), |v| = M 2^(exp-64L)
+      const int64_t sh = nzc ? (64 * (int64_t)L + (int64_t)e_line - (int64_t)X.exp[c][idx] - (xbits - 1)) : 0;
+      m[q][c].start(X.limb[c] + idx, nzc, sh, X.plane, L);
+      neg[q][c] = nzc && X.sign[c][idx];
+      cneg[q][c] = 1;
+      cbal[q][c] = 0;
+      if (nzc && sh > 0) {   // the bits of M below sh are dropped: the line is lossy unless they are zero
+        if (sh >= 64 * (int64_t)L) {
+          ok = false;
+        } else {
+          for (int jj = 0; jj < L && 64 * (int64_t)jj < sh; ++jj) {
+            const int64_t take = sh - 64 * (int64_t)jj;
+            const uint64_t mask = take >= 64 ? ~0ull : ((1ull << take) - 1ull);
+            if (X.limb[c][(int64_t)jj * X.plane + idx] & mask) ok = false;
+          }
+        }
       }
     }
-    d[q].csum = 0;
-    d[q].cbal_s = 0;
+    csum[q] = 0;
+    cbal_s[q] = 0;
   }
   if (!ok) atomicOr(lossy + line, 1);
-  (void)any;
 #pragma unroll
   for (int c = 0; c < 2; ++c)
     if (__ballot_sync(0xffffffffu, nzv[c]) && leader) nz[nplanes + c] = 1;
@@ -174,7 +197,6 @@ __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64
   // words of X_re, X_im (wd*s bits) and X_re + X_im: every stream keeps a 128-bit buffer
   // (lo, hi) holding `nbuf` bits; all streams advance in step (wd bits per digit).
   const int ndig = want_sum ? s + 1 : s;
-  const int64_t xbits = (int64_t)wd * s;                 // |X| < 2^(xbits - 1)
   const uint32_t fmask = (1u << wd) - 1u;
   const int half = 1 << (wd - 1), full = 1 << wd;
   uint64_t blo[2][3], bhi[2][3];                         // [element][re, im, sum]
@@ -186,26 +208,26 @@ __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64
   for (int pos = 0; pos < ndig; ++pos) {
     if (nbuf < wd) {   // append word `wnext` of every stream above the bits still buffered
       uint64_t wc[2][3];
+      const int64_t top = xbits - 64 * (int64_t)wnext;   // bits of |X| in this word
+      const uint64_t tmask = top >= 64 ? ~0ull : (top <= 0 ? 0ull : ((1ull << top) - 1ull));
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          uint64_t x = word_at_bit(d[q].M[c], L, 64 * (int64_t)wnext + d[q].sh[c]);
-          const int64_t top = xbits - 64 * (int64_t)wnext;   // bits of |X| in this word
-          if (top < 64) x &= top <= 0 ? 0ull : ((1ull << top) - 1ull);
-          if (d[q].neg[c]) {
-            const uint64_t t = ~x + d[q].cneg[c];
-            d[q].cneg[c] = (d[q].cneg[c] && t == 0) ? 1ull : 0ull;
+          uint64_t x = m[q][c].next(X.plane, L) & tmask;
+          if (neg[q][c]) {
+            const uint64_t t = ~x + cneg[q][c];
+            cneg[q][c] = (cneg[q][c] && t == 0) ? 1ull : 0ull;
             x = t;
           }
           wc[q][c] = x;
         }
         const uint64_t a0 = wc[q][0] + wc[q][1];
         const uint64_t c1 = a0 < wc[q][0];
-        const uint64_t a1 = a0 + d[q].csum;
+        const uint64_t a1 = a0 + csum[q];
         const uint64_t c2 = a1 < a0;
         wc[q][2] = a1;
-        d[q].csum = c1 | c2;
+        csum[q] = c1 | c2;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           blo[q][c] |= wc[q][c] << nbuf;
@@ -233,10 +255,10 @@ __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64
         for (int q = 0; q < 2; ++q) {
           int dg;
           if (pos == s - 1) {   // top digit: the signed field plus the carry
-            dg = (fld[q][c] >= half ? fld[q][c] - full : fld[q][c]) + d[q].cbal[c];
+            dg = (fld[q][c] >= half ? fld[q][c] - full : fld[q][c]) + cbal[q][c];
           } else {
-            dg = fld[q][c] + d[q].cbal[c];
-            d[q].cbal[c] = dg >= half;
+            dg = fld[q][c] + cbal[q][c];
+            cbal[q][c] = dg >= half;
             if (dg >= half) dg -= full;
           }
           f[q] = (float)dg;
@@ -251,10 +273,10 @@ __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64
       for (int q = 0; q < 2; ++q) {
         int dg;
         if (pos == s) {
-          dg = (fld[q][2] >= half ? fld[q][2] - full : fld[q][2]) + d[q].cbal_s;
+          dg = (fld[q][2] >= half ? fld[q][2] - full : fld[q][2]) + cbal_s[q];
         } else {
-          dg = fld[q][2] + d[q].cbal_s;
-          d[q].cbal_s = dg >= half;
+          dg = fld[q][2] + cbal_s[q];
+          cbal_s[q] = dg >= half;
           if (dg >= half) dg -= full;
         }
         f[q] = (float)dg;
