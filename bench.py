@@ -47,7 +47,7 @@ WORKLOADS = {
 BATCH_WORKLOAD = "c3_batch64"
 PROFILE = os.path.join(ROOT, "profiles", "oz_slicegemm_c2_2048_p1024.md")
 # the slice GEMM kernel and the group table / unit schedule it runs over
-SLICEGEMM_SRC = [os.path.join(ROOT, "paper_2307_06072_gb300", "csrc", f) for f in ("slicegemm_tc.cu", "accum.cu")]
+SLICEGEMM_SRC = [os.path.join(ROOT, "paper_2307_06072_gb300", "csrc", f) for f in ("slicegemm_tc.cu", "grouptable.cu")]
 
 
 def sources_hash(paths) -> str:

@@ -270,4 +270,14 @@ __device__ __forceinline__ void store_zero(int L, uint8_t *sign_out, int32_t *ex
 
 #endif  // __CUDACC__
 
+// sign with which product `prod` enters component c
+__host__ __device__ inline int product_sign(int method, int c, int prod) {
+  if (method == MPC_4M) {
+    if (c == 0) return prod == 0 ? 1 : (prod == 1 ? -1 : 0);
+    return (prod == 2 || prod == 3) ? 1 : 0;
+  }
+  if (c == 0) return prod == 0 ? 1 : (prod == 1 ? -1 : 0);
+  return prod == 2 ? 1 : -1;
+}
+
 }  // namespace mpc

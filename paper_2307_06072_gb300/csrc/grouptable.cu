@@ -1,0 +1,152 @@
+// The group table of one Ozaki call (Alg. 2's product loop, as grouped here):
+// which slice pairs (t, q - t) of which real product are summed together into one
+// int32 plane, in what order the accumulation visits them, in what order the slice
+// GEMM hands out its units, and the call's error bounds.  It runs once per call,
+// after the digit kernels, because it trims the pairs of all-zero digit planes.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mpc {
+
+// Component c of A B vanishes for every entry, given which components (re, im) of A
+// and B have a nonzero value somewhere.
+__device__ __forceinline__ bool component_zero(const int32_t *vA, const int32_t *vB, int c) {
+  return c == 0 ? ((!vA[0] || !vB[0]) && (!vA[1] || !vB[1])) : ((!vA[0] || !vB[1]) && (!vA[1] || !vB[0]));
+}
+
+// digit-set kinds of the two operands of real product `prod`: 0 re, 1 im, 2 sums
+__device__ __forceinline__ void product_kinds(int method, int prod, int &ka, int &kb) {
+  if (method == MPC_4M) {
+    ka = (prod == 0 || prod == 2) ? 0 : 1;   // rr, ii, ri, ir
+    kb = (prod == 0 || prod == 3) ? 0 : 1;
+  } else {
+    ka = kb = prod;                           // rr, ii, ss
+  }
+}
+
+// Per product (one warp each): the group table, levels ascending; then every
+// group loses the pairs at its two ends whose A or B digit plane is all zero
+// (their products are exactly zero), so it never splits and the table keeps its
+// size; a group of zero pairs only keeps its place (count 0: no unit, no term).
+// The warp also counts the dropped pairs (levels above Q) whose planes are both
+// nonzero.  Thread 0 then merges the products' groups into the accumulation order
+// (descending level, i.e. ascending shift), writes the slice GEMM's unit schedule
+// and the call's error bounds:
+//   drop[c]    = sum over the products of component c of ceil(B_prod / 2^beta),
+//                B_prod = k (2^(w-2) n_{Q+1} + ceil(max_{j>=2} n_{Q+j} / 3)) over live pairs;
+//   lossy_a[c] = sum of the products' truncation factors (4 for the 3M sums, else 1),
+//                counted only when both operand components of the product have a
+//                nonzero value somewhere (otherwise the product is exactly zero);
+//   lossy_b[c] likewise;
+// all three are zero for a component of A B that vanishes identically, and
+// zero[c] (bounds[6 + c]) tells the accumulation to add nothing into it: a product
+// needed only there (the 3M sums for real inputs) was emptied.
+__global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
+  __shared__ uint64_t s_bd[4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < a.n_products) {
+    const ProductDesc pd = a.prod[warp];
+    if (lane == 0)
+      build_groups(warp, pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, a.Q, a.gmax, a.table + pd.group0,
+                   pd.n_groups);
+    __syncwarp();
+    // a product that enters only components of A B that vanish identically is not needed
+    // (the 3M sums for real or purely imaginary inputs): all its groups are emptied
+    const int32_t *vA = a.flagsA + a.planes_A, *vB = a.flagsB + a.planes_B;
+    bool needed = false;
+    for (int c = 0; c < 2; ++c)
+      if (product_sign(a.method, c, warp) != 0 && !component_zero(vA, vB, c)) needed = true;
+    auto live = [&](int t, int u) {
+      return needed && a.flagsA[pd.a_plane0 + t - pd.a_pos0] != 0 && a.flagsB[pd.b_plane0 + u - pd.b_pos0] != 0;
+    };
+    for (int e = pd.group0 + lane; e < pd.group0 + pd.n_groups; e += 32) {
+      GroupEntry g = a.table[e];
+      while (g.count > 0 && !live(g.t0, g.q - g.t0)) {
+        ++g.t0;
+        --g.count;
+      }
+      while (g.count > 0 && !live(g.t0 + g.count - 1, g.q - (g.t0 + g.count - 1))) --g.count;
+      a.table[e] = g;
+    }
+    // live dropped pairs per level above Q
+    const int qmax = pd.a_pos0 + pd.a_npos - 1 + pd.b_pos0 + pd.b_npos - 1;
+    uint64_t n1 = 0, nmax = 0;
+    for (int q = a.Q + 1; q <= qmax; ++q) {
+      const int lo = max(pd.a_pos0, q - (pd.b_pos0 + pd.b_npos - 1));
+      const int hi = min(pd.a_pos0 + pd.a_npos - 1, q - pd.b_pos0);
+      unsigned cnt = 0;
+      for (int t = lo + lane; t <= hi; t += 32) cnt += live(t, q - t) ? 1u : 0u;
+      cnt = __reduce_add_sync(0xffffffffu, cnt);
+      if (q == a.Q + 1) n1 = cnt;
+      else if (cnt > nmax) nmax = cnt;
+    }
+    if (lane == 0) s_bd[warp] = (uint64_t)a.k * (((uint64_t)1 << (a.w - 2)) * n1 + (nmax + 2) / 3);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const ProductDesc *pds = a.prod;
+  const int n_products = a.n_products;
+  const GroupEntry *table = a.table;
+  int32_t *order = a.order;
+  // merge the per-product lists (each ascending in q) from their ends
+  int next[4];
+  for (int x = 0; x < 4; ++x) next[x] = x < n_products ? pds[x].group0 + pds[x].n_groups - 1 : -1;
+  int n = 0;
+  while (true) {
+    int best = -1;
+    for (int x = 0; x < n_products; ++x)
+      if (next[x] >= pds[x].group0 && (best < 0 || table[next[x]].q > table[next[best]].q)) best = x;
+    if (best < 0) break;
+    order[n++] = next[best]--;
+  }
+  // the slice GEMM's schedule: product by product, groups by descending pair
+  // count (stable), so that consecutive units take nearly equally long and the
+  // groups of adjacent levels, which share digit planes, stay next to each other
+  // (counting sort per product; count <= kMaxSlices + 1)
+  int32_t *sched = order + n;
+  int out = 0;
+  for (int x = 0; x < n_products; ++x) {
+    const int g0 = pds[x].group0, g1 = g0 + pds[x].n_groups;
+    int start[kMaxSlices + 3];
+    for (int c = 0; c < kMaxSlices + 3; ++c) start[c] = 0;
+    for (int e = g0; e < g1; ++e) ++start[kMaxSlices + 1 - table[e].count + 1];
+    start[0] = out;
+    for (int c = 1; c < kMaxSlices + 3; ++c) start[c] += start[c - 1];
+    for (int e = g0; e < g1; ++e) sched[start[kMaxSlices + 1 - table[e].count]++] = e;
+    out += g1 - g0;
+  }
+  // the call's bounds
+  const int32_t *valA = a.flagsA + a.planes_A, *valB = a.flagsB + a.planes_B;   // [re, im] values nonzero
+  for (int c = 0; c < 2; ++c) {
+    uint64_t bd = 0, la = 0, lb = 0;
+    for (int x = 0; x < n_products; ++x) {
+      if (product_sign(a.method, c, x) == 0) continue;
+      int ka, kb;
+      product_kinds(a.method, x, ka, kb);
+      const bool va = ka == 2 ? (valA[0] || valA[1]) : valA[ka] != 0;
+      const bool vb = kb == 2 ? (valB[0] || valB[1]) : valB[kb] != 0;
+      bd += ceil_shift(s_bd[x], a.beta);
+      const uint64_t cf = ka == 2 ? 2 : 1;   // sums: 2 ulps truncation, |.| < 2^(E+1)
+      if (va && vb) {
+        la += cf * cf;
+        lb += cf * cf;
+      }
+    }
+    // component c of A B vanishes identically (given which components are nonzero): every
+    // product entering it, and the 3M sums, which equal one part digit for digit, cancel
+    // exactly, so its accumulator is exactly zero
+    const bool zero = component_zero(valA, valB, c);
+    a.bounds[c] = zero ? 0 : bd;
+    a.bounds[2 + c] = zero ? 0 : la;
+    a.bounds[4 + c] = zero ? 0 : lb;
+    a.bounds[6 + c] = zero ? 1 : 0;   // the accumulation adds nothing into this component
+  }
+}
+
+// ---------------------------------------------------------------- launcher
+
+void launch_group_table(const GroupTableArgs &a, cudaStream_t st) {
+  k_group_table<<<1, 128, 0, st>>>(a);
+}
+
+}  // namespace mpc
