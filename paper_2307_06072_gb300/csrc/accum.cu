@@ -6,8 +6,9 @@
 // formula gives them, into two exact accumulators (Re, Im):
 //     4M: Re = rr - ii,        Im = ri + ir
 //     3M: Re = rr - ii,        Im = ss - rr - ii
-// Groups are visited in order of increasing shift; each accumulator keeps two
-// running int64 words in registers and emits finished 32-bit words.
+// Groups are visited in order of increasing shift; the groups of one level are
+// summed in int64, and each accumulator takes one level sum per step, keeping a
+// running carry in registers and emitting finished 32-bit words.
 // Value = Acc * 2^(E_i + F_j - (2w - 2) - wQ).
 // The result is RN_p(Acc) when no rounding midpoint lies within the error
 // bound b * 2^beta of Acc (then it equals RN_p of the exact product);
@@ -39,43 +40,53 @@ struct LimbAcc {   // 32-bit words of a little-endian uint64 array
   }
 };
 
-// Exact signed integer built from terms v * 2^shift with nondecreasing shifts:
-// `lo` holds the current 32-bit word (index `cur`) plus pending carries, `hi`
-// the next; finished words are emitted to `out`.  Any int64 term is split into
-// 32-bit halves first, so no intermediate exceeds 2^56 in magnitude.
-struct Lazy {
-  int64_t lo = 0, hi = 0;
-  int cur = 0;
-  __device__ __forceinline__ void emit(uint32_t *out) {
-    out[cur++] = (uint32_t)lo;
-    lo = (lo >> 32) + hi;
-    hi = 0;
+// Exact signed integer built from one term per level, at shifts 0, w, 2w, ...
+// (a skipped level counts as a zero term): after each level the low w bits of the
+// running signed carry are final, go to a bit buffer and leave the carry, so every
+// shift is by a constant w.  A level sum has at most 3 x 160 int32 groups (|h| < 2^40),
+// so |carry + h| < 2^41.
+struct DigitAcc {
+  int64_t c = 0;      // value not yet emitted, in units of 2^(bits emitted)
+  uint64_t bb = 0;    // emitted bits not yet written to `out` (nb of them, nb < 32)
+  int nb = 0, cur = 0, next = 0;   // next: shift of the next level
+  __device__ __forceinline__ void step(uint32_t *out, int64_t h, int w) {
+    c += h;
+    bb |= (uint64_t)(c & ((1ll << w) - 1)) << nb;
+    c >>= w;   // floor
+    nb += w;
+    next += w;
+    if (nb >= 32) {
+      out[cur++] = (uint32_t)bb;
+      bb >>= 32;
+      nb -= 32;
+    }
   }
-  __device__ __forceinline__ void add(uint32_t *out, int64_t v, int shift) {
-    const int w = shift >> 5, r = shift & 31;
-    while (cur < w) emit(out);
-    // v 2^r = vl 2^r + vh 2^(32+r) with vl = v mod 2^32, vh = floor(v / 2^32)
-    const uint64_t xl = (uint64_t)(uint32_t)v << r;        // < 2^56
-    const int64_t vh = v >> 32;                            // |vh| < 2^31
-    lo += (int64_t)(xl & 0xFFFFFFFFull);
-    hi += (int64_t)(xl >> 32) + vh * ((int64_t)1 << r);
+  __device__ __forceinline__ void add(uint32_t *out, int64_t h, int shift, int w) {
+    while (next < shift) step(out, 0, w);
+    step(out, h, w);
   }
   // emit the remaining words; returns the sign (magnitude left in out[0, nw))
   __device__ __forceinline__ bool finish(uint32_t *out, int nw) {
-    while (cur < nw) emit(out);
-    const bool neg = lo < 0;
+    if (cur < nw) {   // the buffered bits below the carry's bits (no carry between them)
+      out[cur++] = (uint32_t)(bb | ((uint64_t)c << nb));
+      c >>= (32 - nb);
+    }
+    while (cur < nw) {
+      out[cur++] = (uint32_t)c;
+      c >>= 32;
+    }
+    const bool neg = c < 0;
     if (neg) {
-      uint64_t c = 1;
+      uint64_t k = 1;
       for (int i = 0; i < nw; ++i) {
-        const uint64_t t = (uint64_t)(uint32_t)~out[i] + c;
+        const uint64_t t = (uint64_t)(uint32_t)~out[i] + k;
         out[i] = (uint32_t)t;
-        c = t >> 32;
+        k = t >> 32;
       }
     }
     return neg;
   }
 };
-
 }  // namespace
 
 // One accumulation term per group, in order of descending level: plane index,
@@ -95,7 +106,7 @@ __device__ __forceinline__ int64_t mad_wide(int32_t v, int32_t s, int64_t acc) {
 }
 
 // Round (or queue for the exact fallback) one component of one output element.
-__device__ __forceinline__ void finish_component(const AccumArgs &a, const OutView &C, Lazy &acc, uint32_t *words,
+__device__ __forceinline__ void finish_component(const AccumArgs &a, const OutView &C, DigitAcc &acc, uint32_t *words,
                                                  int c, int64_t i, int64_t j, int32_t Ei, int32_t Fj) {
   const int64_t o = i * C.ld + j;
   const bool neg = acc.finish(words, a.nslot);
@@ -193,7 +204,7 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
     cp_async_commit();
   };
   uint32_t words[2][kMaxWords];
-  Lazy acc[2];
+  DigitAcc acc[2];
   int64_t sum0 = 0, sum1 = 0;
   issue(0, 0);
   for (int x0 = 0, buf = 0; x0 < a.n_entries; x0 += kAccBatch, buf ^= 1) {
@@ -211,8 +222,8 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
         sum0 = mad_wide(v, t.z, sum0);
         sum1 = mad_wide(v, t.w, sum1);
         if (t.y >= 0) {   // the last group of a level
-          acc[0].add(words[0], sum0, t.y);
-          acc[1].add(words[1], sum1, t.y);
+          acc[0].add(words[0], sum0, t.y, a.w);
+          acc[1].add(words[1], sum1, t.y, a.w);
           sum0 = sum1 = 0;
         }
       }
