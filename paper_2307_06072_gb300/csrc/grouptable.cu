@@ -43,6 +43,8 @@ __device__ __forceinline__ void product_kinds(int method, int prod, int &ka, int
 // needed only there (the 3M sums for real inputs) was emptied.
 __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
   __shared__ uint64_t s_bd[4];
+  __shared__ int32_t s_qc[kMaxGroupsTotal];   // per group: (q + 8) << 16 | count, for the serial passes below
+  __shared__ int s_start[kMaxSlices + 3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp < a.n_products) {
     const ProductDesc pd = a.prod[warp];
@@ -82,11 +84,17 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
     }
     if (lane == 0) s_bd[warp] = (uint64_t)a.k * (((uint64_t)1 << (a.w - 2)) * n1 + (nmax + 2) / 3);
   }
+  __syncthreads();   // the trimmed table is complete
+  int n_groups = 0;
+  for (int x = 0; x < a.n_products; ++x) n_groups = max(n_groups, a.prod[x].group0 + a.prod[x].n_groups);
+  for (int e = threadIdx.x; e < n_groups; e += blockDim.x) {
+    const GroupEntry g = a.table[e];
+    s_qc[e] = ((g.q + 8) << 16) | g.count;   // q >= -2, count <= kMaxSlices + 1
+  }
   __syncthreads();
   if (threadIdx.x != 0) return;
   const ProductDesc *pds = a.prod;
   const int n_products = a.n_products;
-  const GroupEntry *table = a.table;
   int32_t *order = a.order;
   // merge the per-product lists (each ascending in q) from their ends
   int next[4];
@@ -95,7 +103,7 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
   while (true) {
     int best = -1;
     for (int x = 0; x < n_products; ++x)
-      if (next[x] >= pds[x].group0 && (best < 0 || table[next[x]].q > table[next[best]].q)) best = x;
+      if (next[x] >= pds[x].group0 && (best < 0 || (s_qc[next[x]] >> 16) > (s_qc[next[best]] >> 16))) best = x;
     if (best < 0) break;
     order[n++] = next[best]--;
   }
@@ -107,12 +115,12 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
   int out = 0;
   for (int x = 0; x < n_products; ++x) {
     const int g0 = pds[x].group0, g1 = g0 + pds[x].n_groups;
-    int start[kMaxSlices + 3];
+    int *start = s_start;
     for (int c = 0; c < kMaxSlices + 3; ++c) start[c] = 0;
-    for (int e = g0; e < g1; ++e) ++start[kMaxSlices + 1 - table[e].count + 1];
+    for (int e = g0; e < g1; ++e) ++start[kMaxSlices + 1 - (s_qc[e] & 0xFFFF) + 1];
     start[0] = out;
     for (int c = 1; c < kMaxSlices + 3; ++c) start[c] += start[c - 1];
-    for (int e = g0; e < g1; ++e) sched[start[kMaxSlices + 1 - table[e].count]++] = e;
+    for (int e = g0; e < g1; ++e) sched[start[kMaxSlices + 1 - (s_qc[e] & 0xFFFF)]++] = e;
     out += g1 - g0;
   }
   // the call's bounds
