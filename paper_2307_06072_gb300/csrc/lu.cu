@@ -227,47 +227,58 @@ __global__ void k_sub_block(MatRW A, int64_t r0, int64_t c0, int64_t rows, int64
   if (!ok) atomicOr(reinterpret_cast<int *>(status) + kStErange, 1);
 }
 
-// Solve with the factors for one right-hand side column (block per column).
-__global__ void __launch_bounds__(1024) k_lu_solve(MatRW LU, int64_t n, const int32_t *ipiv, MatRW Bm, int p, int L,
-                                                   int32_t *status) {
-  const int64_t col = blockIdx.x;
-  if (status[kStSingular]) return;
-  if (threadIdx.x == 0) {   // apply the row interchanges in order
-    for (int64_t j = 0; j < n; ++j) {
-      const int64_t r = ipiv[j];
-      if (r == j) continue;
-      for (int c = 0; c < 2; ++c) {
-        const int64_t a = j * Bm.ld + col, b = r * Bm.ld + col;
-        uint8_t s = Bm.sign[c][a];
-        Bm.sign[c][a] = Bm.sign[c][b];
-        Bm.sign[c][b] = s;
-        int32_t e = Bm.exp[c][a];
-        Bm.exp[c][a] = Bm.exp[c][b];
-        Bm.exp[c][b] = e;
-        for (int u = 0; u < L; ++u) {
-          uint64_t v = Bm.limb[c][(int64_t)u * Bm.plane + a];
-          Bm.limb[c][(int64_t)u * Bm.plane + a] = Bm.limb[c][(int64_t)u * Bm.plane + b];
-          Bm.limb[c][(int64_t)u * Bm.plane + b] = v;
-        }
+// Solve with the factors, one launch per step so that every step spreads over the
+// whole GPU (right-hand side column col0 + blockIdx.y).
+// b := P b: the row interchanges in order, one thread per right-hand side column.
+__global__ void k_solve_perm(MatRW Bm, int64_t n, int64_t nrhs, const int32_t *ipiv, int L, int32_t *status) {
+  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nrhs || status[kStSingular]) return;
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t r = ipiv[j];
+    if (r == j) continue;
+    for (int c = 0; c < 2; ++c) {
+      const int64_t a = j * Bm.ld + col, b = r * Bm.ld + col;
+      uint8_t sg = Bm.sign[c][a];
+      Bm.sign[c][a] = Bm.sign[c][b];
+      Bm.sign[c][b] = sg;
+      int32_t e = Bm.exp[c][a];
+      Bm.exp[c][a] = Bm.exp[c][b];
+      Bm.exp[c][b] = e;
+      for (int u = 0; u < L; ++u) {
+        uint64_t v = Bm.limb[c][(int64_t)u * Bm.plane + a];
+        Bm.limb[c][(int64_t)u * Bm.plane + a] = Bm.limb[c][(int64_t)u * Bm.plane + b];
+        Bm.limb[c][(int64_t)u * Bm.plane + b] = v;
       }
     }
   }
-  __syncthreads();
-  for (int64_t j = 0; j < n; ++j) {   // forward: unit lower L
-    for (int64_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
-      cfma_store(Bm, i, col, Bm.ref(0, i, col), Bm.ref(1, i, col), LU.ref(0, i, j), LU.ref(1, i, j),
-                 Bm.ref(0, j, col), Bm.ref(1, j, col), p, L, status);
-    __syncthreads();
-  }
-  for (int64_t j = n - 1; j >= 0; --j) {   // backward: upper U
-    if (threadIdx.x == 0)
-      cdiv_store(Bm, j, col, Bm.ref(0, j, col), Bm.ref(1, j, col), LU.ref(0, j, j), LU.ref(1, j, j), p, L, status);
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < j; i += blockDim.x)
-      cfma_store(Bm, i, col, Bm.ref(0, i, col), Bm.ref(1, i, col), LU.ref(0, i, j), LU.ref(1, i, j),
-                 Bm.ref(0, j, col), Bm.ref(1, j, col), p, L, status);
-    __syncthreads();
-  }
+}
+
+// forward step j (unit lower L): y_i = RN(y_i - l_ij y_j) for j < i < n
+__global__ void k_solve_fwd(MatRW LU, int64_t n, int64_t j, MatRW Bm, int64_t col0, int p, int L, int32_t *status) {
+  const int64_t col = col0 + blockIdx.y;
+  const int64_t i = j + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || status[kStSingular]) return;
+  cfma_store(Bm, i, col, Bm.ref(0, i, col), Bm.ref(1, i, col), LU.ref(0, i, j), LU.ref(1, i, j), Bm.ref(0, j, col),
+             Bm.ref(1, j, col), p, L, status);
+}
+
+// x_j = RN(y_j / u_jj) for the last row (the first backward step)
+__global__ void k_solve_last(MatRW LU, int64_t j, MatRW Bm, int64_t nrhs, int p, int L, int32_t *status) {
+  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nrhs || status[kStSingular]) return;
+  cdiv_store(Bm, j, col, Bm.ref(0, j, col), Bm.ref(1, j, col), LU.ref(0, j, j), LU.ref(1, j, j), p, L, status);
+}
+
+// backward step j (upper U, x_j already in row j): y_i = RN(y_i - u_ij x_j) for i < j;
+// the thread of row j - 1 then forms x_{j-1} = RN(y_{j-1} / u_{j-1,j-1}) for the next step
+__global__ void k_solve_bwd(MatRW LU, int64_t j, MatRW Bm, int64_t col0, int p, int L, int32_t *status) {
+  const int64_t col = col0 + blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= j || status[kStSingular]) return;
+  cfma_store(Bm, i, col, Bm.ref(0, i, col), Bm.ref(1, i, col), LU.ref(0, i, j), LU.ref(1, i, j), Bm.ref(0, j, col),
+             Bm.ref(1, j, col), p, L, status);
+  if (i == j - 1)
+    cdiv_store(Bm, i, col, Bm.ref(0, i, col), Bm.ref(1, i, col), LU.ref(0, i, i), LU.ref(1, i, i), p, L, status);
 }
 
 }  // namespace mpc
@@ -408,7 +419,23 @@ extern "C" int mpcgesv(int64_t n, int32_t p_bits, mpc_mat *A, int32_t *ipiv, mpc
       k_sub_block<<<blocks_for(rest * rest, 64), 64, 0, st>>>(Am, kend, kend, rest, rest, Pm, p_bits, L, status);
     }
   }
-  k_lu_solve<<<(unsigned)B->cols, 1024, 0, st>>>(Am, n, ipiv, Bm, p_bits, L, status);
+  // solve: forward then backward substitution, every element's operations in the same
+  // order as the column-oriented loops (bit-identical results), one launch per step
+  const int64_t nrhs = B->cols;
+  if (n > 0 && nrhs > 0) {
+    constexpr int64_t kMaxGridY = 65535;
+    constexpr int kT = 64;
+    k_solve_perm<<<blocks_for(nrhs, kT), kT, 0, st>>>(Bm, n, nrhs, ipiv, L, status);
+    for (int64_t j = 0; j + 1 < n; ++j)
+      for (int64_t c0 = 0; c0 < nrhs; c0 += kMaxGridY)
+        k_solve_fwd<<<dim3(blocks_for(n - j - 1, kT), (unsigned)std::min(kMaxGridY, nrhs - c0)), kT, 0, st>>>(
+            Am, n, j, Bm, c0, p_bits, L, status);
+    k_solve_last<<<blocks_for(nrhs, kT), kT, 0, st>>>(Am, n - 1, Bm, nrhs, p_bits, L, status);
+    for (int64_t j = n - 1; j >= 1; --j)
+      for (int64_t c0 = 0; c0 < nrhs; c0 += kMaxGridY)
+        k_solve_bwd<<<dim3(blocks_for(j, kT), (unsigned)std::min(kMaxGridY, nrhs - c0)), kT, 0, st>>>(
+            Am, j, Bm, c0, p_bits, L, status);
+  }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MPC_OK : MPC_ECUDA - (int)e;
 }
