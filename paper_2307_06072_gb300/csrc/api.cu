@@ -2,7 +2,9 @@
 // parameters and the workspace layout) and the launch sequence on the
 // caller's stream.  See include/mpcgemm.h for the contract.
 #include <cstdio>
+#include <atomic>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -515,6 +517,60 @@ int mpcgemm_batched_workspace(int count, const mpc_problem *probs, const mpc_oz_
   return MPC_OK;
 }
 
+namespace {
+
+// Side streams of a batched call: the small per-problem kernels (split, group table,
+// accumulation) of different problems are independent, so they are spread over a
+// fixed pool of streams forked from and joined back into the caller's stream (under
+// stream capture this becomes parallel branches of the graph).  The pool is created
+// once per device; the mutex keeps the fork / join events of concurrent calls apart
+// while they are enqueued.
+constexpr int kSideStreams = 8;
+constexpr int kMaxDevices = 64;
+struct SidePool {
+  std::once_flag once;
+  bool ok = false;
+  std::atomic<bool> ready{false};
+  cudaStream_t s[kSideStreams];
+  cudaEvent_t fork, join[kSideStreams];
+  std::mutex mu;
+};
+SidePool g_side[kMaxDevices];
+
+// nullptr: run on the caller's stream (the pool is never created while `st` is being
+// captured, since creating streams and events there could invalidate the capture)
+SidePool *side_pool(cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  SidePool &sp = g_side[dev];
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return nullptr;
+  if (cs != cudaStreamCaptureStatusNone) return sp.ready.load() ? &sp : nullptr;
+  std::call_once(sp.once, [&sp] {
+    bool ok = cudaEventCreateWithFlags(&sp.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int x = 0; x < kSideStreams && ok; ++x)
+      ok = cudaStreamCreateWithFlags(&sp.s[x], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&sp.join[x], cudaEventDisableTiming) == cudaSuccess;
+    sp.ok = ok;
+    sp.ready.store(ok);
+  });
+  return sp.ok ? &sp : nullptr;
+}
+
+void side_fork(SidePool *sp, cudaStream_t st) {
+  cudaEventRecord(sp->fork, st);
+  for (int x = 0; x < kSideStreams; ++x) cudaStreamWaitEvent(sp->s[x], sp->fork, 0);
+}
+
+void side_join(SidePool *sp, cudaStream_t st) {
+  for (int x = 0; x < kSideStreams; ++x) {
+    cudaEventRecord(sp->join[x], sp->s[x]);
+    cudaStreamWaitEvent(st, sp->join[x], 0);
+  }
+}
+
+}  // namespace
+
 int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *params, void *workspace,
                     size_t ws_bytes, void *stream) {
   if (count < 0 || (count > 0 && !probs)) return MPC_EINVAL;
@@ -532,10 +588,18 @@ int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *pa
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaGetLastError();
-  for (int x = 0; x < count; ++x) {
-    if (!calls[x].empty) call_pre(calls[x], st);
-    else if (calls[x].status) cudaMemsetAsync(calls[x].status, 0, kStatusWords * 4, st);
+  SidePool *sp = count > 1 ? side_pool(st) : nullptr;
+  std::unique_lock<std::mutex> lock;
+  if (sp) {
+    lock = std::unique_lock<std::mutex>(sp->mu);
+    side_fork(sp, st);
   }
+  auto lane = [&](int x) { return sp ? sp->s[x % kSideStreams] : st; };
+  for (int x = 0; x < count; ++x) {
+    if (!calls[x].empty) call_pre(calls[x], lane(x));
+    else if (calls[x].status) cudaMemsetAsync(calls[x].status, 0, kStatusWords * 4, lane(x));
+  }
+  if (sp) side_join(sp, st);
   thread_local std::vector<SliceGemmArgs> slices;
   slices.clear();
   bool any_tall = false;
@@ -562,10 +626,13 @@ int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *pa
       return e == cudaErrorNotSupported ? MPC_ENOTSUP : cuda_code(e);
     }
   }
+  if (sp) side_fork(sp, st);
   for (int x = 0; x < count; ++x)
-    if (!calls[x].empty && calls[x].k > 0) call_accum(calls[x], st);
-  for (int x = 0; x < count; ++x)
-    if (!calls[x].empty && calls[x].k > 0) call_fallback(calls[x], st);
+    if (!calls[x].empty && calls[x].k > 0) {
+      call_accum(calls[x], lane(x));
+      call_fallback(calls[x], lane(x));
+    }
+  if (sp) side_join(sp, st);
   return cuda_code(cudaGetLastError());
 }
 
