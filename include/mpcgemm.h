@@ -205,12 +205,14 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits,
  * precisions and methods, in one call.  The Ozaki problems share ONE persistent
  * tcgen05 slice-GEMM launch (48 problems per launch), so small problems fill
  * the GPU together; the split, accumulation and fallback kernels run per
- * problem, spread over 8 library-owned side streams that are forked from and
+ * problem; in batches of 16 problems or more they are spread over 8
+ * library-owned side streams that are forked from and
  * joined back into `stream` (under capture: parallel branches of the graph),
- * so the call stays ordered on `stream` like any other.  The side streams
- * and their events are created by the first batched call on a device made
- * outside stream capture (until then, everything runs on `stream`); concurrent
- * batched calls from several host threads enqueue one after the other.  The
+ * so the call stays ordered on `stream` like any other.  Each caller stream
+ * (up to 64 per process) has side streams of its own, created by its first
+ * batched call made outside stream capture; until then, and beyond 64 caller
+ * streams, everything runs on `stream`.  Concurrent batched calls on the same
+ * stream from several host threads enqueue one after the other.  The
  * call is asynchronous and allocates no memory, so it can be captured in a
  * CUDA graph and replayed.  Each problem uses its own region of
  * the workspace, at offsets[i] from mpcgemm_batched_workspace(); its device

@@ -128,7 +128,16 @@ def lu_solve(A, Bm, p: int, K: int):
                     pr, pi = rn(sr, p), rn(si, p)
                     ar, ai = a[i][c]
                     a[i][c] = (rn(o1.add(ar, o1.neg(pr)), p), rn(o1.add(ai, o1.neg(pi)), p))
-    # solve
+    return a, ipiv, substitute(a, ipiv, b, p)
+
+
+def substitute(a, ipiv, b, p: int):
+    """The solve with given factors (Sec. IV-C): b := P b by the interchanges in order,
+    forward substitution with the unit lower triangle of `a`, backward substitution
+    with its upper triangle; every operation rounded once (RN_p), column-oriented.
+    `a` is n x n and `b` n x nrhs, both lists of rows of (re, im) exact values; `b`
+    is overwritten and returned."""
+    n, nrhs = len(a), (len(b[0]) if b else 0)
     for j in range(n):
         r = ipiv[j]
         b[j], b[r] = b[r], b[j]
@@ -140,7 +149,7 @@ def lu_solve(A, Bm, p: int, K: int):
             b[j][c] = cdiv(b[j][c], a[j][j], p)
             for i in range(j):
                 b[i][c] = cfma(b[i][c], a[i][j], b[j][c], p)
-    return a, ipiv, b
+    return b
 
 
 def pack_values(rows, p):

@@ -2,7 +2,6 @@
 // parameters and the workspace layout) and the launch sequence on the
 // caller's stream.  See include/mpcgemm.h for the contract.
 #include <cstdio>
-#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -520,41 +519,51 @@ int mpcgemm_batched_workspace(int count, const mpc_problem *probs, const mpc_oz_
 namespace {
 
 // Side streams of a batched call: the small per-problem kernels (split, group table,
-// accumulation) of different problems are independent, so they are spread over a
-// fixed pool of streams forked from and joined back into the caller's stream (under
-// stream capture this becomes parallel branches of the graph).  The pool is created
-// once per device; the mutex keeps the fork / join events of concurrent calls apart
-// while they are enqueued.
+// accumulation) of different problems are independent, so they are spread over a pool
+// of streams forked from and joined back into the caller's stream (under stream capture
+// this becomes parallel branches of the graph).  Every caller stream gets a pool of its
+// own, so that batched calls on independent streams stay independent; a pool is created
+// the first time its stream makes a batched call outside capture, and its mutex keeps
+// the fork / join events of concurrent calls on that stream apart while they are
+// enqueued.  Past kMaxPools caller streams, calls run on the caller's stream alone.
+// Only batches of at least kSideMinBatch problems use side streams: the GPU has few
+// hardware work queues (8 by default), and the streams of many small concurrent calls
+// (a serving loop's slots) would share them with each other's long slice-GEMM launches.
 constexpr int kSideStreams = 8;
-constexpr int kMaxDevices = 64;
+constexpr int kSideMinBatch = 16;
+constexpr int kMaxPools = 64;
 struct SidePool {
-  std::once_flag once;
+  int dev = -1;
+  cudaStream_t caller = nullptr;
   bool ok = false;
-  std::atomic<bool> ready{false};
   cudaStream_t s[kSideStreams];
   cudaEvent_t fork, join[kSideStreams];
   std::mutex mu;
 };
-SidePool g_side[kMaxDevices];
+SidePool g_pools[kMaxPools];
+int g_npools = 0;
+std::mutex g_pools_mu;
 
-// nullptr: run on the caller's stream (the pool is never created while `st` is being
-// captured, since creating streams and events there could invalidate the capture)
+// nullptr: run on the caller's stream (no pool is created while `st` is being captured,
+// since creating streams and events there could invalidate the capture)
 SidePool *side_pool(cudaStream_t st) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-  SidePool &sp = g_side[dev];
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return nullptr;
-  if (cs != cudaStreamCaptureStatusNone) return sp.ready.load() ? &sp : nullptr;
-  std::call_once(sp.once, [&sp] {
-    bool ok = cudaEventCreateWithFlags(&sp.fork, cudaEventDisableTiming) == cudaSuccess;
-    for (int x = 0; x < kSideStreams && ok; ++x)
-      ok = cudaStreamCreateWithFlags(&sp.s[x], cudaStreamNonBlocking) == cudaSuccess &&
-           cudaEventCreateWithFlags(&sp.join[x], cudaEventDisableTiming) == cudaSuccess;
-    sp.ok = ok;
-    sp.ready.store(ok);
-  });
-  return sp.ok ? &sp : nullptr;
+  std::lock_guard<std::mutex> lk(g_pools_mu);
+  for (int x = 0; x < g_npools; ++x)
+    if (g_pools[x].dev == dev && g_pools[x].caller == st) return g_pools[x].ok ? &g_pools[x] : nullptr;
+  if (cs != cudaStreamCaptureStatusNone || g_npools == kMaxPools) return nullptr;
+  SidePool &sp = g_pools[g_npools++];
+  sp.dev = dev;
+  sp.caller = st;
+  bool ok = cudaEventCreateWithFlags(&sp.fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int x = 0; x < kSideStreams && ok; ++x)
+    ok = cudaStreamCreateWithFlags(&sp.s[x], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&sp.join[x], cudaEventDisableTiming) == cudaSuccess;
+  sp.ok = ok;
+  return ok ? &sp : nullptr;
 }
 
 void side_fork(SidePool *sp, cudaStream_t st) {
@@ -588,7 +597,7 @@ int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *pa
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaGetLastError();
-  SidePool *sp = count > 1 ? side_pool(st) : nullptr;
+  SidePool *sp = count >= kSideMinBatch ? side_pool(st) : nullptr;
   std::unique_lock<std::mutex> lock;
   if (sp) {
     lock = std::unique_lock<std::mutex>(sp->mu);

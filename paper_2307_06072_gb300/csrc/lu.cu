@@ -227,7 +227,52 @@ __global__ void k_sub_block(MatRW A, int64_t r0, int64_t c0, int64_t rows, int64
   if (!ok) atomicOr(reinterpret_cast<int *>(status) + kStErange, 1);
 }
 
-// Solve with the factors, one launch per step so that every step spreads over the
+// Solve with the factors for one right-hand side column per block (blockIdx.x), every
+// step inside the block: for n up to the block size every row has a thread of its own,
+// and a single launch costs less than 2n of them.
+__global__ void __launch_bounds__(1024) k_lu_solve(MatRW LU, int64_t n, const int32_t *ipiv, MatRW Bm, int p, int L,
+                                                   int32_t *status) {
+  const int64_t col = blockIdx.x;
+  if (status[kStSingular]) return;
+  if (threadIdx.x == 0) {   // apply the row interchanges in order
+    for (int64_t j = 0; j < n; ++j) {
+      const int64_t r = ipiv[j];
+      if (r == j) continue;
+      for (int c = 0; c < 2; ++c) {
+        const int64_t a = j * Bm.ld + col, b = r * Bm.ld + col;
+        uint8_t sg = Bm.sign[c][a];
+        Bm.sign[c][a] = Bm.sign[c][b];
+        Bm.sign[c][b] = sg;
+        int32_t e = Bm.exp[c][a];
+        Bm.exp[c][a] = Bm.exp[c][b];
+        Bm.exp[c][b] = e;
+        for (int u = 0; u < L; ++u) {
+          uint64_t v = Bm.limb[c][(int64_t)u * Bm.plane + a];
+          Bm.limb[c][(int64_t)u * Bm.plane + a] = Bm.limb[c][(int64_t)u * Bm.plane + b];
+          Bm.limb[c][(int64_t)u * Bm.plane + b] = v;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int64_t j = 0; j < n; ++j) {   // forward: unit lower L
+    for (int64_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
+      cfma_store(Bm, i, col, Bm.ref(0, i, col), Bm.ref(1, i, col), LU.ref(0, i, j), LU.ref(1, i, j),
+                 Bm.ref(0, j, col), Bm.ref(1, j, col), p, L, status);
+    __syncthreads();
+  }
+  for (int64_t j = n - 1; j >= 0; --j) {   // backward: upper U
+    if (threadIdx.x == 0)
+      cdiv_store(Bm, j, col, Bm.ref(0, j, col), Bm.ref(1, j, col), LU.ref(0, j, j), LU.ref(1, j, j), p, L, status);
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < j; i += blockDim.x)
+      cfma_store(Bm, i, col, Bm.ref(0, i, col), Bm.ref(1, i, col), LU.ref(0, i, j), LU.ref(1, i, j),
+                 Bm.ref(0, j, col), Bm.ref(1, j, col), p, L, status);
+    __syncthreads();
+  }
+}
+
+// Larger systems: one launch per step, so that every step spreads over the
 // whole GPU (right-hand side column col0 + blockIdx.y).
 // b := P b: the row interchanges in order, one thread per right-hand side column.
 __global__ void k_solve_perm(MatRW Bm, int64_t n, int64_t nrhs, const int32_t *ipiv, int L, int32_t *status) {
@@ -422,7 +467,10 @@ extern "C" int mpcgesv(int64_t n, int32_t p_bits, mpc_mat *A, int32_t *ipiv, mpc
   // solve: forward then backward substitution, every element's operations in the same
   // order as the column-oriented loops (bit-identical results), one launch per step
   const int64_t nrhs = B->cols;
-  if (n > 0 && nrhs > 0) {
+  constexpr int64_t kSolveBlock = 1024;
+  if (n > 0 && nrhs > 0 && n <= kSolveBlock) {
+    k_lu_solve<<<(unsigned)nrhs, (unsigned)kSolveBlock, 0, st>>>(Am, n, ipiv, Bm, p_bits, L, status);
+  } else if (n > 0 && nrhs > 0) {
     constexpr int64_t kMaxGridY = 65535;
     constexpr int kT = 64;
     k_solve_perm<<<blocks_for(nrhs, kT), kT, 0, st>>>(Bm, n, nrhs, ipiv, L, status);

@@ -42,6 +42,22 @@ def test_lu_matches_oracle_bit_for_bit(n, K, p, method, nrhs):
     assert gu.same(X, lu.pack_values(x, p))
 
 
+def test_large_solve_matches_the_oracle_substitution():
+    """n > 1024: the solve runs as one launch per substitution step (smaller systems use
+    one block per right-hand side).  With the GPU's own factors and interchanges, the
+    oracle's column-oriented substitution must give the same X bit for bit."""
+    from oracle import exact as o1
+    n, K, p = 1100, 128, 128
+    A = si.shifted_diagonal_matrix(n, p, 970)
+    B = si.random_matrix(n, 1, p, 971, "uniform")
+    LU, ipiv, X, st, sing = _gpu_lu(A, B, p, K, "3m")
+    assert sing == 0 and st["erange"] == 0 and st["uncertified"] == 0
+    lv, bv = o1.matrix_values(LU), o1.matrix_values(B)
+    a = [[(lv[0][i][j], lv[1][i][j]) for j in range(n)] for i in range(n)]
+    b = [[(bv[0][i][0], bv[1][i][0])] for i in range(n)]
+    assert gu.same(X, lu.pack_values(lu.substitute(a, ipiv, b, p), p))
+
+
 def test_singular_matrix_is_reported():
     n, p = 12, 128
     A = si.random_matrix(n, n, p, 950)
