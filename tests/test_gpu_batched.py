@@ -89,6 +89,31 @@ def test_batched_call_replays_from_a_cuda_graph():
             assert gu.same(_result(dC, p), c_oracle.rounded_cgemm_matrix(A, B, p))
 
 
+def test_large_batch_graph_with_and_without_side_streams():
+    """16 problems or more run their per-problem kernels on side streams of the caller's
+    stream (graph branches under capture) once that stream has made a batched call
+    outside capture; a stream that never did runs everything itself.  Both graphs must
+    replay to the exact products."""
+    import torch
+    M = gu.mp()
+    specs = [(20 + 3 * x, 40, 18 + x, 128 + 64 * (x % 3), "3m" if x % 2 else "4m", "ozaki") for x in range(20)]
+    probs, host = _make(specs, 4700)
+    warm, fresh = torch.cuda.Stream(), torch.cuda.Stream()
+    ws = M.mpcgemm_batched(probs, stream=warm)          # creates the side streams of `warm`
+    torch.cuda.synchronize()
+    for s in (warm, fresh):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                M.mpcgemm_batched(probs, workspace=ws, stream=s)
+        for (_, _, dC, _, _, _) in probs:
+            dC.limb.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for (dA, dB, dC, p, method, algo), (A, B) in zip(probs, host):
+            assert gu.same(_result(dC, p), c_oracle.rounded_cgemm_matrix(A, B, p))
+
+
 def test_autotuner_picks_a_working_configuration():
     import torch
     M = gu.mp()
