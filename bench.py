@@ -70,6 +70,17 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(v: float, ws: int, device) -> float:
+    """The largest of every rank's v (the job's time is its slowest rank's)."""
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_inputs(workload: str, rank: int):
     m, n, k, p, dist, idx = WORKLOADS[workload]
     A = si.random_matrix(m, k, p, si.SEED_BASE + idx + 7919 * rank, dist)
@@ -400,11 +411,7 @@ def run_ours(args):
         return ms, stages
 
     def max_over_ranks(v: float) -> float:
-        if ws_ == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, ws_, dev)
 
     units = 8.0 * m * n * k
     with ClockSampler(dev.index or 0) as clocks:
@@ -589,7 +596,7 @@ def cpu_baseline_batch(problems, seconds: float):
 def run_reference_batch(args, ws_):
     specs = batch_specs()
     problems = batch_host_problems(specs)
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = min(max(2.0, 60.0 / max(1, args.steps + args.warmup)), args.cpu_seconds)
     for _ in range(args.warmup):
         cpu_baseline_batch(problems, min(per_step, 5.0))
     vals, cb = [], None
@@ -621,7 +628,7 @@ def run_reference(args):
         return
     m, n, k, p, dist, _ = WORKLOADS[args.workload]
     A, B, p = make_inputs(args.workload, 0)
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = min(max(2.0, 60.0 / max(1, args.steps + args.warmup)), args.cpu_seconds)
     for _ in range(args.warmup):
         cpu_baseline(A, B, p, min(per_step, 5.0))
     vals = []
@@ -659,7 +666,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the 4M / plain side measurements")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="CPU oracle sample per measurement: the cpu_baseline leg, and the cap of each step of --impl reference")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("note: warm-up raised to the minimum of 3 steps")
