@@ -124,3 +124,60 @@ def test_identity_and_singular():
     S.limb[:, :, :, 2] = 0          # a zero column
     with pytest.raises(lu.SingularMatrix):
         lu.lu_solve(S, b, p, 2)
+
+
+def test_substitution_solves_an_exact_triangular_system():
+    """The solve with given factors, pinned by the residual: L and U hold small complex
+    integers with unit or power-of-two diagonals, so at p = 64 no operation rounds and
+    the returned x must satisfy (L U) x = P b exactly (checked in Fractions, by matrix
+    products rather than by substitution)."""
+    rnd = random.Random(11)
+    n, p = 7, 64
+
+    def cval(re, im):
+        return ((re, 0), (im, 0))
+
+    a = [[None] * n for _ in range(n)]
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                a[i][j] = rnd.choice([cval(1, 0), cval(-2, 0), cval(0, 1), cval(4, 0), cval(0, -2)])
+            else:
+                a[i][j] = cval(rnd.randint(-3, 3), rnd.randint(-3, 3))
+    ipiv = [rnd.randint(j, n - 1) for j in range(n)]
+    b = [[cval(rnd.randint(-5, 5), rnd.randint(-5, 5))] for _ in range(n)]
+    x = lu.substitute(a, ipiv, [row[:] for row in b], p)
+
+    def cf(v):
+        return complex_frac(exact.to_fraction(v[0]), exact.to_fraction(v[1]))
+
+    def complex_frac(re, im):
+        return (re, im)
+
+    def cmul(u, v):
+        return (u[0] * v[0] - u[1] * v[1], u[0] * v[1] + u[1] * v[0])
+
+    def cadd(u, v):
+        return (u[0] + v[0], u[1] + v[1])
+
+    zero = (Fraction(0), Fraction(0))
+    Lm = [[cf(a[i][j]) if i > j else ((Fraction(1), Fraction(0)) if i == j else zero) for j in range(n)]
+          for i in range(n)]
+    Um = [[cf(a[i][j]) if i <= j else zero for j in range(n)] for i in range(n)]
+    LU = [[zero] * n for _ in range(n)]
+    for i in range(n):
+        for j in range(n):
+            s = zero
+            for t in range(n):
+                s = cadd(s, cmul(Lm[i][t], Um[t][j]))
+            LU[i][j] = s
+    pb = [cf(row[0]) for row in b]
+    for j in range(n):                     # P b: the interchanges in order
+        r = ipiv[j]
+        pb[j], pb[r] = pb[r], pb[j]
+    xs = [cf(row[0]) for row in x]
+    for i in range(n):
+        s = zero
+        for j in range(n):
+            s = cadd(s, cmul(LU[i][j], xs[j]))
+        assert s == pb[i], i
