@@ -92,7 +92,8 @@ def test_shape_mismatch_and_workspace_checks(mp):
     (256, 256, "3m", None, None, None, None), (1024, 2048, "3m", None, None, None, None),
     (1024, 2048, "3m", None, None, None, 8), (512, 1024, "4m", 8, None, None, None),
     (128, 9, "3m", 0, None, 3, None), (128, 8, "4m", None, 10, 18, None), (192, 2048, "3m", None, 30, 33, 8),
-    (256, 40000, "4m", None, None, None, None)])
+    (256, 40000, "4m", None, None, None, None),
+    (128, 131071, "3m", None, None, None, None)])   # the largest k: 8-bit digits, one pair per group
 def test_plan_matches_the_oracle_parameters(mp, p, k, method, guard, s, Q, w):
     """Digit width, s, Q, group counts and bound constants of the C plan equal O2's
     (w = 9 by default, 8 when k >= 2^15 or when asked for)."""
