@@ -130,3 +130,56 @@ def test_plan_matches_the_oracle_parameters(mp, p, k, method, guard, s, Q, w):
                 want = pl["bound_drop"][c] + k * ((0 if la else pl["bound_lossy_a"][c]) +
                                                   (0 if lb else pl["bound_lossy_b"][c]))
                 assert (b, beta) == (want, pl["bound_shift"])
+
+
+def test_lu_arguments_checked_on_host(mp):
+    """mpcgesv rejects bad arguments before any launch (no GPU needed to see it)."""
+    n = mp_native()
+    lib = n.lib()
+    lib.mpcgesv_workspace_size.restype = ctypes.c_size_t
+    lib.mpcgesv_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int]
+    M3 = n.METHODS["3m"]
+    for args in [(-1, 128, 16, M3), (8, 0, 16, M3), (8, 1025, 16, M3), (8, 128, 0, M3), (8, 128, 16, 7)]:
+        assert lib.mpcgesv_workspace_size(*args) == 0, args
+    need = lib.mpcgesv_workspace_size(64, 256, 16, M3)
+    assert need > 0 and lib.mpcgesv_workspace_size(128, 256, 16, M3) > need
+    lib.mpcgesv.restype = ctypes.c_int
+    lib.mpcgesv.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_int32, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    A, B = _dummy_mat(64, 64), _dummy_mat(64, 2)
+    ipiv, ws = ctypes.c_void_p(0x2000), ctypes.c_void_p(0x100000)
+    call = lambda nn, a, b, piv, w, wb, p=256: lib.mpcgesv(nn, p, a, piv, b, 16, M3, w, wb, None)
+    assert call(64, None, ctypes.byref(B), ipiv, ws, need) == n.MPC_EINVAL                  # no A
+    assert call(64, ctypes.byref(_dummy_mat(64, 63)), ctypes.byref(B), ipiv, ws, need) == n.MPC_EINVAL
+    assert call(64, ctypes.byref(A), ctypes.byref(_dummy_mat(63, 2)), ipiv, ws, need) == n.MPC_EINVAL
+    assert call(64, ctypes.byref(A), ctypes.byref(B), None, ws, need) == n.MPC_EINVAL        # no ipiv
+    assert call(64, ctypes.byref(A), ctypes.byref(B), ipiv, ctypes.c_void_p(0x100010), need) == n.MPC_EINVAL
+    assert call(64, ctypes.byref(A), ctypes.byref(B), ipiv, ws, need - 1) == n.MPC_ENOSPC
+    assert call(64, ctypes.byref(A), ctypes.byref(B), ipiv, ws, need, p=2000) == n.MPC_EINVAL
+    Z = _dummy_mat(0, 0)
+    assert call(0, ctypes.byref(Z), ctypes.byref(_dummy_mat(0, 1)), None, None, 0) == n.MPC_OK   # empty: no-op
+
+
+def test_batched_arguments_checked_on_host(mp):
+    """mpcgemm_batched plans and checks every problem before its first launch."""
+    n = mp_native()
+    lib = n.lib()
+    keep = []
+
+    def problem(m, nn, k, p=256, method="3m", algo="ozaki"):
+        A, B, C = _dummy_mat(m, k), _dummy_mat(k, nn), _dummy_mat(m, nn)
+        keep.extend([A, B, C])
+        return n.MpcProblem(m, nn, k, p, n.METHODS[method], n.ALGOS[algo], 0,
+                            ctypes.addressof(A), ctypes.addressof(B), ctypes.addressof(C))
+
+    good = [problem(32, 40, 24), problem(16, 8, 64, 512, "4m")]
+    arr = (n.MpcProblem * 2)(*good)
+    total = ctypes.c_size_t(0)
+    assert lib.mpcgemm_batched_workspace(2, arr, None, None, ctypes.byref(total)) == n.MPC_OK and total.value > 0
+    ws = ctypes.c_void_p(0x100000)
+    assert lib.mpcgemm_batched(-1, arr, None, ws, total.value, None) == n.MPC_EINVAL
+    assert lib.mpcgemm_batched(2, None, None, ws, total.value, None) == n.MPC_EINVAL
+    assert lib.mpcgemm_batched(0, None, None, None, 0, None) == n.MPC_OK                  # empty batch
+    assert lib.mpcgemm_batched(2, arr, None, ws, total.value - 256, None) == n.MPC_ENOSPC
+    bad = (n.MpcProblem * 2)(good[0], problem(16, 8, 64, 2000))                          # p out of range
+    assert lib.mpcgemm_batched(2, bad, None, ws, total.value, None) == n.MPC_EINVAL
