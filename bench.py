@@ -661,7 +661,7 @@ def main():
     ap.add_argument("--method", choices=["3m", "4m"], default="3m")
     ap.add_argument("--algo", choices=["ozaki", "plain"], default="ozaki",
                     help="the timed step's algorithm (plain: the CUDA-core GEMM, no side measurements)")
-    ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_pair", "tcgen05_2sm", "mma_sync"], default="auto",
+    ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_2sm", "mma_sync"], default="auto",
                     help="slice-GEMM kernel")
     ap.add_argument("--quick", action="store_true", help="skip the 4M / plain side measurements")
     ap.add_argument("--no-e2e", action="store_true")

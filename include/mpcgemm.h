@@ -47,6 +47,8 @@
  *     all scratch space lives in the caller's `workspace` of `ws_bytes`
  *     bytes (device memory, 256-byte aligned), sized by
  *     mpcgemm_workspace_size().  C must not alias A, B or the workspace.
+ *     The one exception is mpcgemm_noalloc(), whose scratch is a static
+ *     device array of the library (see there).
  *   * k == 0 gives C = 0; m == 0 or n == 0 is a no-op (the workspace may be
  *     NULL); inside a batched call such a problem's status block is cleared.
  */
@@ -71,8 +73,8 @@ extern "C" {
 /* ---- algorithm selection --------------------------------------------- */
 enum { MPC_4M = 0, MPC_3M = 1 };          /* Eq. (4m_way) / Eq. (3m_way) */
 enum { MPC_PLAIN = 0, MPC_OZAKI = 1 };    /* Eq. (simple_triple_loop) / Alg. 2 */
-enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2, MPC_KERNEL_TCGEN05_PAIR = 3,
-       MPC_KERNEL_TCGEN05_2SM = 4 };
+/* Slice-GEMM kernels (value 3 is not used and is rejected). */
+enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2, MPC_KERNEL_TCGEN05_2SM = 4 };
 
 /* Largest supported precision and inner size. */
 #define MPC_MAX_P_BITS 1024
@@ -100,12 +102,20 @@ typedef struct mpc_mat {
  *               (0 -> Q = s - 1, the paper's triangle alpha + beta <= d + 1).
  *   max_group   cap on the slice pairs summed in one group (0 -> the int32 limit
  *               G_max); smaller groups make more, shorter work units.
- *   kernel      MPC_KERNEL_*: which slice-GEMM kernel (auto = tcgen05, in CTA pairs
- *               when m > 128; TCGEN05_PAIR always runs CTA pairs that share the B
- *               tile by TMA multicast, TCGEN05 single CTAs, TCGEN05_2SM CTA pairs
- *               that run one 256-row MMA across both SMs, each holding half of B;
- *               the mma.sync kernel is a second, independent implementation of the
- *               same sums).
+ *   kernel      MPC_KERNEL_*: which slice-GEMM kernel (auto = TCGEN05, single
+ *               CTAs with 128 x 256 tiles; TCGEN05_2SM CTA pairs that run one
+ *               256-row MMA across both SMs, each loading its own rows of A and
+ *               half of B; the mma.sync kernel is a second, independent
+ *               implementation of the same sums).
+ *   wait_limit_cycles
+ *               SM clock cycles that one barrier wait of the tcgen05 kernels may
+ *               last before the kernel gives up (0 -> about 4e9, some 2 s).  A
+ *               positive value makes the waits poll, so that the limit holds to
+ *               within a few cycles.  A wait that runs out sets
+ *               mpc_status.device_timeout, the kernel lets its copies and MMAs in
+ *               flight complete, frees its tensor memory and returns; the results
+ *               of that call are then invalid, the device and the library stay
+ *               usable.  For tests of that path; leave it 0 otherwise.
  */
 typedef struct mpc_oz_params {
     int32_t guard_bits;
@@ -114,7 +124,8 @@ typedef struct mpc_oz_params {
     int32_t kernel;
     int32_t max_group;
     int32_t digit_bits;
-    int32_t reserved[2];
+    int32_t wait_limit_cycles;
+    int32_t reserved;
 } mpc_oz_params;
 
 /*
@@ -173,8 +184,9 @@ typedef struct mpc_status {
  * C := RN_p(A B) for m x k A and k x n B, 1 <= p_bits <= MPC_MAX_P_BITS,
  * k <= MPC_MAX_K.  method: MPC_4M or MPC_3M (Eqs. 4m_way / 3m_way; with
  * exact arithmetic both give the same C).  algo: MPC_OZAKI (Alg. 2 on the
- * tensor cores: balanced 8-bit integer slices, exact slice products, exact
- * accumulation, certified rounding with exact fallback) or MPC_PLAIN (the
+ * tensor cores: balanced 9-bit integer slices (8-bit when k >= 2^15) carried
+ * exactly in bf16, exact slice products, exact accumulation, certified
+ * rounding with exact fallback) or MPC_PLAIN (the
  * triple loop of Eq. simple_triple_loop as an exact fixed-point GEMM on the
  * CUDA cores: base-2^28 digit products summed exactly, 4 real products for
  * MPC_4M, 3 for MPC_3M (Eq. 3m_way_base), certified rounding with exact
@@ -271,8 +283,12 @@ int mpcgemm_read_status(const void *workspace, size_t ws_bytes, mpc_status *stat
  * is an interface convenience of the library.
  *
  * Instead of a caller workspace it uses one static device array of
- * MPC_NOALLOC_SCRATCH_BYTES (64 MiB) inside the library; a device that has run
- * this entry point keeps that array until the process exits.  A problem whose
+ * MPC_NOALLOC_SCRATCH_BYTES (64 MiB) inside the library.  The array is
+ * reserved on a device when its device code is loaded there: with CUDA's
+ * default lazy module loading, when this entry point (or its status reader)
+ * first runs on that device; with CUDA_MODULE_LOADING=EAGER, on every device
+ * the process initialises, whether or not it calls this entry point.  It stays
+ * reserved until the process exits.  A problem whose
  * mpcgemm_workspace_size() exceeds it is rejected with MPC_ENOSPC before
  * anything is enqueued (for example m = n = k = 192 fits at p = 256 and 128 at
  * p = 1024 for Ozaki 4M/3M and for plain; 256 at p = 256 for Ozaki
@@ -282,12 +298,20 @@ int mpcgemm_read_status(const void *workspace, size_t ws_bytes, mpc_status *stat
  * previous call's contents there (each call re-initialises what it reads), so
  * calls whose GPU work overlaps -- on different streams or from different host
  * threads -- race and produce wrong results: serialise them.  Arguments, results
- * and errors are those of mpcgemm(), with no workspace arguments.
+ * and errors are those of mpcgemm(), with no workspace arguments; the device
+ * status of the last call on the current device is read with
+ * mpcgemm_noalloc_read_status().
  */
 #define MPC_NOALLOC_SCRATCH_BYTES (64u << 20)
 int mpcgemm_noalloc(int64_t m, int64_t n, int64_t k, int32_t p_bits,
                     const mpc_mat *A, const mpc_mat *B, mpc_mat *C,
                     int method, int algo, void *stream);
+
+/* mpcgemm_read_status() for mpcgemm_noalloc(): synchronises `stream` and reads
+ * the status block of the static array on the current device (the last call
+ * there).  Allocates nothing.  Returns MPC_OK, MPC_ERANGE (status->erange set)
+ * or an error code. */
+int mpcgemm_noalloc_read_status(mpc_status *status, void *stream);
 
 /* Human-readable text of a status code (static storage). */
 const char *mpcgemm_strerror(int code);

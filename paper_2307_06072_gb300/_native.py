@@ -18,10 +18,10 @@ LIB_PATH = os.path.join(_HERE, "libmpcgemm.so")
 MPC_OK, MPC_EINVAL, MPC_ENOSPC, MPC_ERANGE, MPC_ENOTSUP, MPC_ECUDA = 0, -22, -28, -34, -95, -1000
 METHODS = {"4m": 0, "3m": 1}
 ALGOS = {"plain": 0, "ozaki": 1}
-KERNELS = {"auto": 0, "tcgen05": 1, "mma_sync": 2, "tcgen05_pair": 3, "tcgen05_2sm": 4}
+KERNELS = {"auto": 0, "tcgen05": 1, "mma_sync": 2, "tcgen05_2sm": 4}
 
 EXPORTED = ("mpcgemm", "mpcgemm_ex", "mpcgemm_profiled", "mpcgemm_workspace_size", "mpcgemm_plan",
-            "mpcgemm_read_status", "mpcgemm_noalloc", "mpcgemm_batched", "mpcgemm_batched_workspace",
+            "mpcgemm_read_status", "mpcgemm_noalloc", "mpcgemm_noalloc_read_status", "mpcgemm_batched", "mpcgemm_batched_workspace",
             "mpcgesv", "mpcgesv_workspace_size", "mpcgemm_strerror", "mpcgemm_version")
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -34,7 +34,7 @@ class MpcMat(ctypes.Structure):
 class OzParams(ctypes.Structure):
     _fields_ = [("guard_bits", ctypes.c_int32), ("slices", ctypes.c_int32),
                 ("cut_level", ctypes.c_int32), ("kernel", ctypes.c_int32), ("max_group", ctypes.c_int32),
-                ("digit_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("digit_bits", ctypes.c_int32), ("wait_limit_cycles", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class MpcProblem(ctypes.Structure):
@@ -115,6 +115,8 @@ def lib():
         L.mpcgesv_workspace_size.restype = ctypes.c_size_t
         L.mpcgemm_noalloc.argtypes = [I64, I64, I64, I32, P, P, P, ctypes.c_int, ctypes.c_int, P]
         L.mpcgemm_noalloc.restype = ctypes.c_int
+        L.mpcgemm_noalloc_read_status.argtypes = [P, P]
+        L.mpcgemm_noalloc_read_status.restype = ctypes.c_int
         L.mpcgemm_strerror.argtypes = [ctypes.c_int]
         L.mpcgemm_strerror.restype = ctypes.c_char_p
         L.mpcgemm_version.argtypes = []
@@ -139,9 +141,10 @@ def check(code: int) -> int:
     return code
 
 
-def oz_params(guard_bits=0, slices=0, cut_level=0, kernel="auto", max_group=0, digit_bits=0) -> OzParams:
+def oz_params(guard_bits=0, slices=0, cut_level=0, kernel="auto", max_group=0, digit_bits=0,
+              wait_limit_cycles=0) -> OzParams:
     return OzParams(int(guard_bits), int(slices), int(cut_level), KERNELS[kernel] if isinstance(kernel, str)
-                    else int(kernel), int(max_group), int(digit_bits))
+                    else int(kernel), int(max_group), int(digit_bits), int(wait_limit_cycles))
 
 
 def exported_symbols():

@@ -1,9 +1,8 @@
 """Autotuner for the slice-GEMM configuration of a (batched) complex GEMM.
 
 The tunable parts are the work-unit shape and size: the tcgen05 kernel in
-single CTAs (128 x 256 output tiles), in CTA pairs (256 x 256 tiles, the B
-tile shared by multicast) or in CTA pairs running one cta_group::2 MMA (each
-SM holds half of B; pays off with the longer fp32 chunks of 8-bit digits),
+single CTAs (128 x 256 output tiles) or in CTA pairs running one
+cta_group::2 MMA (256 x 256 tiles, each SM loading half of B),
 the digit width, and the cap on slice pairs per group (smaller groups give
 more, shorter units, which balances small problems better; the int32 limit
 is the largest).  The k-block (64 bf16 = one 128-byte swizzled row) is
@@ -20,7 +19,6 @@ from . import _native
 CANDIDATES = (
     {"kernel": "auto"},
     {"kernel": "tcgen05"},
-    {"kernel": "tcgen05_pair"},
     {"kernel": "auto", "max_group": 16},
     {"kernel": "tcgen05_2sm"},
     {"kernel": "tcgen05_2sm", "digit_bits": 8},

@@ -28,6 +28,7 @@ struct Plan {
   mpc_plan pub;
   ProductDesc prod[4];
   int kernel;
+  long long wait_limit;   // cycles per barrier wait of the tcgen05 kernels (0: default)
 };
 
 // Integer bound on the pairs a product drops, in Acc units (dropped level Q + j
@@ -57,7 +58,11 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   P.p_bits = p;
   P.limbs = L;
   out->kernel = prm ? prm->kernel : MPC_KERNEL_AUTO;
-  if (out->kernel < MPC_KERNEL_AUTO || out->kernel > MPC_KERNEL_TCGEN05_2SM) return MPC_EINVAL;
+  if (out->kernel != MPC_KERNEL_AUTO && out->kernel != MPC_KERNEL_TCGEN05 && out->kernel != MPC_KERNEL_MMA_SYNC &&
+      out->kernel != MPC_KERNEL_TCGEN05_2SM)
+    return MPC_EINVAL;
+  if (prm && prm->wait_limit_cycles < 0) return MPC_EINVAL;
+  out->wait_limit = prm ? prm->wait_limit_cycles : 0;
   uint64_t off = 0;
   P.off_status = off;
   off = align256(off + kStatusWords * 4);
@@ -484,9 +489,9 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_
       SliceGemmArgs sa = slice_args(c);
       if (c.pl.kernel == MPC_KERNEL_MMA_SYNC) {
         launch_slicegemm_mma(sa, st);
-      } else {   // auto: the tcgen05 kernel, in CTA pairs when there are at least two row tiles
-        const int pair = c.pl.kernel == MPC_KERNEL_TCGEN05_PAIR || (c.pl.kernel == MPC_KERNEL_AUTO && c.m > 128);
-        const cudaError_t e = launch_slicegemm_tc(sa, st, c.pl.kernel == MPC_KERNEL_TCGEN05_2SM ? 3 : pair ? 2 : 1);
+      } else {   // auto: the single-CTA tcgen05 kernel (measured faster than the 2-SM one)
+        const bool two = c.pl.kernel == MPC_KERNEL_TCGEN05_2SM;
+        const cudaError_t e = launch_slicegemm_tc(sa, st, two, c.pl.wait_limit);
         if (e == cudaErrorNotSupported && c.pl.kernel == MPC_KERNEL_AUTO) launch_slicegemm_mma(sa, st);
         else if (e != cudaSuccess) return e == cudaErrorNotSupported ? MPC_ENOTSUP : cuda_code(e);
       }
@@ -611,7 +616,6 @@ int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *pa
   if (sp) side_join(sp, st);
   thread_local std::vector<SliceGemmArgs> slices;
   slices.clear();
-  bool any_tall = false;
   const int kernel = params ? params->kernel : MPC_KERNEL_AUTO;
   for (int x = 0; x < count; ++x) {
     Call &c = calls[x];
@@ -622,13 +626,12 @@ int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *pa
       launch_slicegemm_mma(slice_args(c), st);
     } else {
       slices.push_back(slice_args(c));
-      any_tall |= c.m > 128;
     }
   }
   if (!slices.empty()) {   // one persistent launch for every Ozaki problem (48 per launch)
-    const int pair = kernel == MPC_KERNEL_TCGEN05_PAIR || (kernel == MPC_KERNEL_AUTO && any_tall);
-    const cudaError_t e = launch_slicegemm_tc_batch(slices.data(), (int)slices.size(), st,
-                                                    kernel == MPC_KERNEL_TCGEN05_2SM ? 3 : pair ? 2 : 1);
+    const bool two = kernel == MPC_KERNEL_TCGEN05_2SM;
+    const cudaError_t e = launch_slicegemm_tc_batch(slices.data(), (int)slices.size(), st, two,
+                                                    params ? params->wait_limit_cycles : 0);
     if (e == cudaErrorNotSupported && kernel == MPC_KERNEL_AUTO) {
       for (const SliceGemmArgs &sa : slices) launch_slicegemm_mma(sa, st);
     } else if (e != cudaSuccess) {

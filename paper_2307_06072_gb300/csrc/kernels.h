@@ -103,8 +103,12 @@ void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, i
                          int want_sum, const int32_t *E, int32_t *lossy, int32_t *digits, cudaStream_t st);
 void launch_group_table(const GroupTableArgs &a, cudaStream_t st);
 void launch_slicegemm_mma(const SliceGemmArgs &a, cudaStream_t st);
-cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int cluster);
-cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, int cluster);
+// two_sm: CTA pairs running one cta_group::2 MMA of M = 256, else single CTAs;
+// wait_limit: cycles a barrier wait may take (0: the default of about 2 s), a
+// positive limit makes the waits poll so that it is exact
+cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, bool two_sm, long long wait_limit = 0);
+cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, bool two_sm,
+                                      long long wait_limit = 0);
 void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st);
 void launch_fallback(const FallbackArgs &f, const MatView &A, const MatView &B, const OutView &C, int blocks,
                      int threads, cudaStream_t st);

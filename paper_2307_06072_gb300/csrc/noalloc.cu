@@ -2,8 +2,12 @@
 // memory.  Its scratch space is a file-scope device array of fixed size
 // (MPC_NOALLOC_SCRATCH_BYTES) instead of a caller-provided workspace.
 //
-// The array belongs to this translation unit's module, so a device holds it
-// (until the process exits) only once this entry point has been used there.
+// The array belongs to this translation unit's device module (which has no
+// kernels), so it is reserved on a device when that module is loaded there:
+// under CUDA's default lazy module loading, when this entry point (or its
+// status reader) first looks the array up on that device; under eager loading
+// (CUDA_MODULE_LOADING=EAGER), on every device the process initialises, whether
+// or not it calls this entry point.  It stays reserved until the process exits.
 // Host code cannot pass `g_noalloc_scratch` to a kernel (in host code the name
 // is a host-side shadow, not a device address); the device address is looked
 // up once per device with cudaGetSymbolAddress and cached.
@@ -49,4 +53,13 @@ extern "C" int mpcgemm_noalloc(int64_t m, int64_t n, int64_t k, int32_t p_bits, 
   if (rc != MPC_OK) return rc;
   return mpcgemm_ex(m, n, k, p_bits, A, B, C, method, algo, nullptr, scratch, (size_t)MPC_NOALLOC_SCRATCH_BYTES,
                     stream);
+}
+
+extern "C" int mpcgemm_noalloc_read_status(mpc_status *status, void *stream) {
+  if (!status) return MPC_EINVAL;
+  void *scratch = nullptr;
+  const int rc = scratch_for_current_device(&scratch);   // a lookup, no allocation
+  if (rc != MPC_OK) return rc;
+  // the status block sits at the start of the array (offset 0 of every plan)
+  return mpcgemm_read_status(scratch, (size_t)MPC_NOALLOC_SCRATCH_BYTES, status, stream);
 }

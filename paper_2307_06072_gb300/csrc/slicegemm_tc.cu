@@ -2,22 +2,30 @@
 // the slice products C_ab := A_a B_b of Alg. 2 (Kouya, Sec. III-C), summed
 // over the pairs of one group, exactly.
 //
-// Work unit = (group g, 128 x 256 output tile).  Its GEMM runs over the
-// concatenated inner dimension K' = count * kpad: for pair (t, q - t) the
-// digit planes D^A_t (rows of A) and D^B_{q-t} (columns of B, K-major).
+// Work unit = (group g, output tile).  Its GEMM runs over the concatenated
+// inner dimension K' = count * kpad: for pair (t, q - t) the digit planes
+// D^A_t (rows of A) and D^B_{q-t} (columns of B, K-major).
 //
-// Persistent CTA per SM, warp-specialised, 320 threads.  Units are handed out
-// dynamically (a global counter): the producer takes the next unit index and
-// publishes it to the MMA and epilogue warps through a 4-slot shared ring, so
-// the units in flight on all SMs stay a contiguous window of the unit order
-// (group-major, groups of equal pair count next to each other, so that the
-// units in flight take equally long and stay in step) and share the same
-// digit planes in L2.
-//   warp 0      TMA producer: 64-element k-blocks of A (128 rows) and B (256
-//               rows) into a 4-stage shared-memory ring (128-byte swizzle).
-//   warp 1      TMEM owner (alloc 512 columns) and, on one lane, the MMA
-//               issuer: tcgen05.mma.cta_group::1.kind::f16, bf16 x bf16 ->
-//               fp32 into one of two 128 x 256 TMEM accumulators.
+// Two variants, both persistent (one CTA, or one CTA pair, per SM or SM
+// pair), warp-specialised, 320 threads per CTA:
+//   * single CTA: a unit is one 128 x 256 tile;
+//   * 2-SM: a cluster of two CTAs runs a unit of two vertically adjacent
+//     128 x 256 tiles as one tcgen05.mma.cta_group::2 of M = 256.  Each CTA
+//     loads its own 128 rows of A and its half of the 256-row B tile (plain
+//     TMA loads, no multicast: the tensor cores read the peer's half from the
+//     peer's shared memory), so an SM fetches 32 KB per k-block instead of
+//     48 KB and a 7-stage ring fits.
+// Units are handed out dynamically (a global counter): the producer (of the
+// leader CTA) takes the next unit index and publishes it to the MMA and
+// epilogue warps (of both CTAs) through a 4-slot shared ring, so the units in
+// flight on all SMs stay a contiguous window of the unit order (group-major,
+// groups of equal pair count next to each other, so that the units in flight
+// take equally long and stay in step) and share the same digit planes in L2.
+//   warp 0      TMA producer: 64-element k-blocks of A and B into the
+//               shared-memory ring (128-byte swizzle).
+//   warp 1      TMEM owner (512 columns) and, on one lane (of the leader),
+//               the MMA issuer: bf16 x bf16 -> fp32 into one of two 256-column
+//               TMEM accumulators.
 //   warps 2..9  epilogue: every chunk of inner elements (4 k-blocks for 9-bit
 //               digits: 256 2^16 <= 2^24; 15 for 8-bit: 960 2^14 < 2^24) the
 //               accumulator holds an exact integer; it is read with
@@ -25,8 +33,9 @@
 //               registers (the group bound keeps every sum below 2^31).
 //               The two TMEM buffers let the MMA fill one while the other
 //               drains.  At the end of a unit the int32 tile is stored.
-// Every mbarrier wait is bounded: on a timeout the kernel records it in the
-// status block, lets in-flight copies and MMAs land, frees TMEM and returns.
+// Every mbarrier wait is bounded (a per-call cycle limit): on a timeout the
+// kernel records it in the status block, lets in-flight copies and MMAs land,
+// frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -42,25 +51,20 @@ namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64;
 
-// Per variant: CL = 1 single CTAs; CL = 2 CTA pairs with cta_group::1 MMAs (each CTA
-// holds the whole 256-row B tile, half of it multicast by the peer); CL = 3 CTA pairs
-// with one cta_group::2 MMA of M = 256 (each CTA holds only its half of B: the tensor
-// cores read the other half from the peer's shared memory).
-template <int CL>
+template <bool TWO>
 struct TcCfg {
-  static constexpr bool kTwoSm = CL == 3;
-  static constexpr int kPair = CL == 1 ? 1 : 2;              // CTAs per unit
-  static constexpr int STAGES = kTwoSm ? 7 : 4;
-  static constexpr int B_ROWS = kTwoSm ? BN / 2 : BN;        // B rows in this CTA's shared memory
+  static constexpr int kPair = TWO ? 2 : 1;                  // CTAs per unit
+  static constexpr int STAGES = TWO ? 7 : 4;
+  static constexpr int B_ROWS = TWO ? BN / 2 : BN;          // B rows in this CTA's shared memory
   static constexpr int A_BYTES = BM * BK * 2, B_BYTES = B_ROWS * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 512;   // 7 x 32 KB + barriers <= 227 KB
 };
 constexpr int NUM_THREADS = 320, EPI_WARPS = 8;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr long long kTimeoutCycles = 4000000000ll;   // ~2 s at 2 GHz
-constexpr int URING = 4;                               // unit-index ring slots
-constexpr int kMaxBatch = 48;                          // problems per launch (kernel parameter space)
-constexpr int kStUnitCounter = 8;                      // status word used as the unit counter
+constexpr long long kDefaultWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+constexpr int URING = 4;                                   // unit-index ring slots
+constexpr int kMaxBatch = 48;                              // problems per launch (kernel parameter space)
+constexpr int kStUnitCounter = 8;                          // status word used as the unit counter
 
 // One launch serves a set of up to kMaxBatch independent problems (a single
 // GEMM is a set of one): their units are numbered consecutively and each
@@ -84,9 +88,19 @@ struct TcMaps {
 
 struct TcParams {
   int count;
+  int poll;               // nonzero: waits poll (mbarrier.test_wait) so that wait_limit is exact
   int64_t units;
+  long long wait_limit;   // cycles a barrier wait may take before the kernel gives up
   int32_t *status;
   TcProblem prob[kMaxBatch];
+};
+
+// What a bounded wait needs: the CTA's abort flag, the status block and the limit.
+struct Waits {
+  volatile int *abort;
+  int32_t *status;
+  long long limit;
+  bool poll;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -105,24 +119,52 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+// one probe of phase `parity`: try_wait may suspend for a while, test_wait returns at once
+template <bool CLUSTER>
+__device__ __forceinline__ bool mbar_probe(uint64_t *bar, uint32_t parity, bool poll) {
   uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
+  if (poll) {
+    if (CLUSTER)
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(ok)
+          : "r"(smem_u32(bar)), "r"(parity)
+          : "memory");
+    else
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(ok)
+          : "r"(smem_u32(bar)), "r"(parity)
+          : "memory");
+  } else {
+    if (CLUSTER)
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(ok)
+          : "r"(smem_u32(bar)), "r"(parity)
+          : "memory");
+    else
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(ok)
+          : "r"(smem_u32(bar)), "r"(parity)
+          : "memory");
+  }
   return ok != 0;
 }
 
-// bounded wait; false on abort (another role gave up) or timeout (sets abort + status)
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, int32_t *status) {
+// Bounded wait; false on abort (another role gave up) or timeout (sets abort + status).
+// CLUSTER: acquire at cluster scope (the phase may have been completed by the peer CTA).
+template <bool CLUSTER = false>
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const Waits &w) {
   const long long t0 = clock64();
-  while (!mbar_try(bar, parity)) {
-    if (*abort) return false;
-    if (clock64() - t0 > kTimeoutCycles) {
-      *abort = 1;
-      atomicOr(reinterpret_cast<int *>(status) + kStTimeout, 1);
+  while (!mbar_probe<CLUSTER>(bar, parity, w.poll)) {
+    if (*w.abort) return false;
+    if (clock64() - t0 > w.limit) {
+      *w.abort = 1;
+      atomicOr(reinterpret_cast<int *>(w.status) + kStTimeout, 1);
       return false;
     }
   }
@@ -132,7 +174,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
 // short bounded wait used only while shutting down after an abort
 __device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
   const long long t0 = clock64();
-  while (!mbar_try(bar, parity) && clock64() - t0 < 2000000ll) {
+  while (!mbar_probe<false>(bar, parity, false) && clock64() - t0 < 2000000ll) {
   }
 }
 
@@ -142,6 +184,17 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
       "[%2];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// TMA load into this CTA's shared memory whose completion is signalled on a barrier that
+// may sit in the peer CTA of the pair (shared::cluster address); no multicast.
+__device__ __forceinline__ void tma_load_3d_pair(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                                 uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
 }
 
@@ -178,53 +231,6 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_cluster(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait with cluster-scope acquire (the slot may have been written by the peer CTA)
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity, volatile int *abort,
-                                                  int32_t *status) {
-  const long long t0 = clock64();
-  while (!mbar_try_cluster(bar, parity)) {
-    if (*abort) return false;
-    if (clock64() - t0 > kTimeoutCycles) {
-      *abort = 1;
-      atomicOr(reinterpret_cast<int *>(status) + kStTimeout, 1);
-      return false;
-    }
-  }
-  return true;
-}
-
-// TMA load into this CTA's shared memory whose completion is signalled on a barrier that
-// may sit in the peer CTA of the pair (shared::cluster address)
-__device__ __forceinline__ void tma_load_3d_pair(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
-                                                 uint32_t bar_cluster) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
-
-// TMA load multicast to the CTAs in `mask`: same shared-memory offset and barrier offset in each
-__device__ __forceinline__ void tma_load_3d_mc(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
-                                               uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
-      "[%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
-      : "memory");
-}
-
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms 1024 B apart.
 __device__ __forceinline__ uint64_t smem_desc(const void *p) {
   const uint64_t addr = smem_u32(p);
@@ -237,50 +243,40 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D fp32, A = B = bf16, both K-major, M = 128, N = 256.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor, kind::f16: D fp32, A = B = bf16, both K-major, N = 256, M = 128 (one
+// CTA) or 256 (a CTA pair: the leader's 128 rows in its TMEM, the peer's in the peer's TMEM).
+template <bool TWO>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((TWO ? 2 : 1) * BM >> 4) << 24);
+}
 
+template <bool TWO>
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+  if (TWO)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc<true>()), "r"(accumulate));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc<false>()), "r"(accumulate));
 }
 
-// The same for a CTA pair: M = 256 rows, the leader's 128 in its TMEM, the peer's 128 in
-// the peer's TMEM at the same address; A and B are read from both CTAs' shared memory.
-constexpr uint32_t kIdesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                             ((uint32_t)((2 * BM) >> 4) << 24);
-
-__device__ __forceinline__ void mma_f16_2sm(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc2), "r"(accumulate));
-}
-
-// arrive on the barrier at this offset in every CTA of `mask` once the pair's MMAs complete
-__device__ __forceinline__ void mma_commit_2sm_mc(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-
+// Arrive on `bar` once the MMAs issued so far complete.  The CTA pair's commit arrives on
+// the barrier at this offset in both CTAs (an arrive signal, not a data copy).
+template <bool TWO>
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// arrive on the barrier at this offset in every CTA of `mask` once the issued MMAs complete
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
+  if (TWO)
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)0x3)
+        : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -307,9 +303,9 @@ struct Unit {
 };
 
 // unit u -> (group, tile); for CTA pairs a unit is a pair of row tiles, CTA `rank` takes one
-template <int CL>
+template <bool TWO>
 __device__ __forceinline__ Unit decode(const TcParams &P, int64_t u, uint32_t rank) {
-  constexpr int CP = TcCfg<CL>::kPair;
+  constexpr int CP = TcCfg<TWO>::kPair;
   Unit x;
   int pi = 0;
   while (pi + 1 < P.count && P.prob[pi + 1].unit0 <= u) ++pi;
@@ -329,30 +325,31 @@ __device__ __forceinline__ Unit decode(const TcParams &P, int64_t u, uint32_t ra
 }
 
 // the group of unit u has no pairs left (all its digit planes were zero)
-template <int CL>
+template <bool TWO>
 __device__ __forceinline__ bool unit_empty(const TcParams &P, int64_t u) {
   int pi = 0;
   while (pi + 1 < P.count && P.prob[pi + 1].unit0 <= u) ++pi;
   const TcProblem &q = P.prob[pi];
   const int64_t r = u - q.unit0;
-  const int tiles = ((q.tiles_m + TcCfg<CL>::kPair - 1) / TcCfg<CL>::kPair) * q.tiles_n;
+  const int tiles = ((q.tiles_m + TcCfg<TWO>::kPair - 1) / TcCfg<TWO>::kPair) * q.tiles_n;
   const int e = q.sched ? q.sched[r / tiles] : (int)(r / tiles);
   return q.groups[e].count == 0;
 }
 
 }  // namespace
 
-// CL = 1: one CTA per unit tile.  CL = 2: a cluster of two CTAs computes the
-// two vertically adjacent 128 x 256 tiles of one unit; each CTA loads half of
-// the shared 256-row B tile and multicasts it into both CTAs' shared memory,
-// so an SM fetches 32 KB instead of 48 KB per k-block.  Then both MMAs must
-// release a stage (empty barriers count 2, MMA commits are multicast) and the
-// leader CTA hands the unit indices to both CTAs through distributed shared
-// memory.
-template <int CL>
+// TWO = false: one CTA per 128 x 256 unit tile.  TWO = true: a cluster of two
+// CTAs computes the two vertically adjacent tiles of one unit with one
+// cta_group::2 MMA of M = 256 issued by the leader (rank 0); each CTA's TMA
+// loads (its 128 A rows and its half of B) complete on the leader's stage
+// barrier, TMEM is allocated and freed by both CTAs together, the leader's MMA
+// commits arrive on both CTAs' barriers, and both CTAs' epilogues hand each
+// drained TMEM buffer back on the leader's barrier.  The leader hands out the
+// unit indices to both CTAs through distributed shared memory.
+template <bool TWO>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_slicegemm_tc(const __grid_constant__ TcMaps maps, const __grid_constant__ TcParams P) {
-  using C = TcCfg<CL>;
+  using C = TcCfg<TWO>;
   constexpr int STAGES = C::STAGES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -364,25 +361,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint64_t *tempty = tfull + 2;
   uint64_t *ufull = tempty + 2;
   uint64_t *uempty = ufull + URING;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(uempty + URING);
+  uint64_t *mdone = uempty + URING;   // the MMA issuer's last commit: every MMA has completed
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
   volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
   volatile int *uring = reinterpret_cast<volatile int *>(tmem_slot + 2);
+  const Waits W{abort, P.status, P.wait_limit, P.poll != 0};
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = CL >= 2 ? cluster_rank() : 0u;
+  const uint32_t rank = TWO ? cluster_rank() : 0u;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CL == 2 ? 2 : 1);   // CL = 2: both CTAs' MMAs; else one (multicast) commit
+      mbar_init(&empty[s], 1);   // one (for the pair: multicast) MMA commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], CL == 3 ? 2 * EPI_WARPS : EPI_WARPS);   // CL = 3: both CTAs drain the leader's MMA
+      mbar_init(&tempty[b], TWO ? 2 * EPI_WARPS : EPI_WARPS);   // pair: both CTAs drain the leader's MMA
     }
     for (int r = 0; r < URING; ++r) {
       mbar_init(&ufull[r], 1);
-      mbar_init(&uempty[r], CL >= 2 ? 2 * (1 + EPI_WARPS) + 1 : 1 + EPI_WARPS);
+      mbar_init(&uempty[r], TWO ? 2 * (1 + EPI_WARPS) + 1 : 1 + EPI_WARPS);
     }
+    mbar_init(mdone, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int q = 0; q < P.count; ++q) {
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   }
   if (warp == 1) {
-    if (CL == 3) {   // one warp of each CTA of the pair allocates, collectively
+    if (TWO) {   // one warp of each CTA of the pair allocates, collectively
       asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                    "r"(TMEM_COLS)
                    : "memory");
@@ -404,12 +404,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   }
   tc_fence_before();
-  if (CL >= 2) cluster_sync();   // every barrier of both CTAs initialised before any remote use
+  if (TWO) cluster_sync();   // every barrier of both CTAs initialised before any remote use
   else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // the unit ring is filled by the leader (rank 0); everyone releases slots on the leader's barrier
-  const uint32_t uempty_leader = CL >= 2 ? mapa(smem_u32(uempty), 0) : smem_u32(uempty);
+  const uint32_t uempty_leader = TWO ? mapa(smem_u32(uempty), 0) : smem_u32(uempty);
+  auto release_slot = [&](int slot) {
+    if (TWO) mbar_arrive_cluster(uempty_leader + 8u * (uint32_t)slot);
+    else mbar_arrive(&uempty[slot]);
+  };
 
   if (warp == 0) {
     if (lane == 0) {
@@ -421,24 +425,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       while (ok) {
         int u;
         if (rank == 0) {
-          if (!mbar_wait(&uempty[slot], uphase ^ 1, abort, P.status)) { ok = false; break; }
+          if (!mbar_wait(&uempty[slot], uphase ^ 1, W)) { ok = false; break; }
           int64_t v = atomicAdd(counter, 1);
-          while (v < P.units && unit_empty<CL>(P, v)) v = atomicAdd(counter, 1);   // groups of zero pairs
+          while (v < P.units && unit_empty<TWO>(P, v)) v = atomicAdd(counter, 1);   // groups of zero pairs
           u = v >= P.units ? -1 : (int)v;
           uring[slot] = u;
           mbar_arrive(&ufull[slot]);
-          if (CL >= 2) {
+          if (TWO) {
             st_cluster_u32(mapa(smem_u32((const void *)&uring[slot]), 1), (uint32_t)u);
             mbar_arrive_cluster(mapa(smem_u32(&ufull[slot]), 1));
           }
         } else {
-          if (!mbar_wait_cluster(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
+          if (!mbar_wait<true>(&ufull[slot], uphase, W)) { ok = false; break; }
           u = uring[slot];
-          mbar_arrive_cluster(uempty_leader + 8u * (uint32_t)slot);
+          release_slot(slot);
         }
         if (++slot == URING) { slot = 0; uphase ^= 1; }
         if (u < 0) break;
-        const Unit x = decode<CL>(P, u, rank);
+        const Unit x = decode<TWO>(P, u, rank);
         const int kbpp = P.prob[x.prob].kbpp;
         const CUtensorMap *tmA = &maps.a[x.prob], *tmB = &maps.b[x.prob];
         for (int kb = 0; kb < x.nkb; ++kb) {
@@ -447,22 +451,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const int t = x.g.t0 + pi, uu = x.g.q - t;
           const int planeA = x.pd.a_plane0 + t - x.pd.a_pos0;
           const int planeB = x.pd.b_plane0 + uu - x.pd.b_pos0;
-          if (!mbar_wait(&empty[stage], phase ^ 1, abort, P.status)) { ok = false; break; }
-          if (CL == 3) {   // both CTAs' copies complete on the leader's stage barrier
+          if (!mbar_wait(&empty[stage], phase ^ 1, W)) { ok = false; break; }
+          if (TWO) {   // both CTAs' copies complete on the leader's stage barrier
             const uint32_t fb = mapa(smem_u32(&full[stage]), 0);
             if (rank == 0) mbar_expect_tx(&full[stage], 2 * STAGE_BYTES);
             tma_load_3d_pair(sA + stage * A_BYTES, tmA, k0, x.tm * BM, planeA, fb);
             tma_load_3d_pair(sB + stage * B_BYTES, tmB, k0, x.tn * BN + (int)rank * (BN / 2), planeB, fb);
-            if (++stage == STAGES) { stage = 0; phase ^= 1; }
-            continue;
-          }
-          mbar_expect_tx(&full[stage], STAGE_BYTES);
-          tma_load_3d(sA + stage * A_BYTES, tmA, k0, x.tm * BM, planeA, &full[stage]);
-          if (CL == 1) {
+          } else {
+            mbar_expect_tx(&full[stage], STAGE_BYTES);
+            tma_load_3d(sA + stage * A_BYTES, tmA, k0, x.tm * BM, planeA, &full[stage]);
             tma_load_3d(sB + stage * B_BYTES, tmB, k0, x.tn * BN, planeB, &full[stage]);
-          } else {   // my half of the B tile, into the same place in both CTAs
-            tma_load_3d_mc(sB + stage * B_BYTES + rank * (B_BYTES / 2), tmB, k0, x.tn * BN + (int)rank * (BN / 2),
-                           planeB, &full[stage], (uint16_t)0x3);
           }
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
@@ -474,100 +472,58 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
       }
     }
-  } else if (warp == 1 && CL == 3) {
-    if (lane == 0 && rank == 0) {
-      // ---------------- MMA issuer of the pair (leader): M = 256 across both CTAs
-      int stage = 0, buf = 0, slot = 0;
-      uint32_t phase = 0, tphase = 0, uphase = 0;
-      bool ok = true;
-      while (ok) {
-        if (!mbar_wait_cluster(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
-        const int u = uring[slot];
-        mbar_arrive_cluster(uempty_leader + 8u * (uint32_t)slot);
-        if (++slot == URING) { slot = 0; uphase ^= 1; }
-        if (u < 0) break;
-        const Unit x = decode<CL>(P, u, rank);
-        const int ck = P.prob[x.prob].chunk_kb;
-        for (int c0 = 0; c0 < x.nkb && ok; c0 += ck) {
-          const int cend = min(x.nkb, c0 + ck);
-          // both CTAs' epilogues have drained this accumulator
-          if (!mbar_wait_cluster(&tempty[buf], tphase ^ 1, abort, P.status)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
-          for (int kb = c0; kb < cend; ++kb) {
-            // both CTAs' halves of the stage have landed (the peer's copies signal here too)
-            if (!mbar_wait_cluster(&full[stage], phase, abort, P.status)) { ok = false; break; }
-            tc_fence_after();
-            const uint64_t ad = smem_desc(sA + stage * A_BYTES);
-            const uint64_t bd = smem_desc(sB + stage * B_BYTES);
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-              mma_f16_2sm(d_tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb > c0 || kk > 0) ? 1u : 0u);
-            mma_commit_2sm_mc(&empty[stage], (uint16_t)0x3);   // both producers may refill the stage
-            if (++stage == STAGES) { stage = 0; phase ^= 1; }
-          }
-          if (!ok) break;
-          mma_commit_2sm_mc(&tfull[buf], (uint16_t)0x3);       // both epilogues may drain
-          buf ^= 1;
-          if (buf == 0) tphase ^= 1;
-        }
-      }
-      if (!ok) {   // wait for the MMAs already issued before TMEM is freed
-        mma_commit_2sm_mc(&tfull[buf], (uint16_t)0x3);
-        mbar_drain(&tfull[buf], tphase);
-      }
-    } else if (lane == 0) {
-      // ---------------- peer: no MMA to issue; only takes its turn on the unit ring
-      int slot = 0;
-      uint32_t uphase = 0;
-      while (true) {
-        if (!mbar_wait_cluster(&ufull[slot], uphase, abort, P.status)) break;
-        const int u = uring[slot];
-        mbar_arrive_cluster(uempty_leader + 8u * (uint32_t)slot);
-        if (++slot == URING) { slot = 0; uphase ^= 1; }
-        if (u < 0) break;
-      }
-    }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- MMA issuer
+    if (lane == 0 && rank == 0) {
+      // ---------------- MMA issuer (for the pair: the leader's, M = 256 across both CTAs)
       int stage = 0, buf = 0, slot = 0;
       uint32_t phase = 0, tphase = 0, uphase = 0;
       bool ok = true;
       while (ok) {
-        if (!mbar_wait_cluster(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
+        if (!mbar_wait<TWO>(&ufull[slot], uphase, W)) { ok = false; break; }
         const int u = uring[slot];
-        mbar_arrive_cluster(uempty_leader + 8u * (uint32_t)slot);
+        release_slot(slot);
         if (++slot == URING) { slot = 0; uphase ^= 1; }
         if (u < 0) break;
-        const Unit x = decode<CL>(P, u, rank);
+        const Unit x = decode<TWO>(P, u, rank);
         const int ck = P.prob[x.prob].chunk_kb;
         for (int c0 = 0; c0 < x.nkb && ok; c0 += ck) {
           const int cend = min(x.nkb, c0 + ck);
-          if (!mbar_wait(&tempty[buf], tphase ^ 1, abort, P.status)) { ok = false; break; }
+          // the epilogue (both CTAs' epilogues) has drained this accumulator
+          if (!mbar_wait<TWO>(&tempty[buf], tphase ^ 1, W)) { ok = false; break; }
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
           for (int kb = c0; kb < cend; ++kb) {
-            if (!mbar_wait(&full[stage], phase, abort, P.status)) { ok = false; break; }
+            // the stage has landed (for the pair: both CTAs' halves; the peer's copies signal here too)
+            if (!mbar_wait<TWO>(&full[stage], phase, W)) { ok = false; break; }
             tc_fence_after();
             const uint64_t ad = smem_desc(sA + stage * A_BYTES);
             const uint64_t bd = smem_desc(sB + stage * B_BYTES);
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)   // K = 16 per instruction: +32 B in the swizzled row
-              mma_f16(d_tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb > c0 || kk > 0) ? 1u : 0u);
-            if (CL == 1) mma_commit(&empty[stage]);
-            else mma_commit_mc(&empty[stage], (uint16_t)0x3);   // both CTAs wait for both MMAs
+              mma_f16<TWO>(d_tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb > c0 || kk > 0) ? 1u : 0u);
+            mma_commit<TWO>(&empty[stage]);   // the producer(s) may refill the stage
             if (++stage == STAGES) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
-          mma_commit(&tfull[buf]);
+          mma_commit<TWO>(&tfull[buf]);       // the epilogue(s) may drain
           buf ^= 1;
           if (buf == 0) tphase ^= 1;
         }
       }
-      if (!ok) {   // wait for the MMAs already issued before TMEM is freed
-        mma_commit(&tfull[buf]);
-        mbar_drain(&tfull[buf], tphase);
+      // Whether it finished or gave up: every MMA issued must complete before TMEM is freed
+      // (after an abort the epilogue may no longer be waiting for the last chunk).
+      mma_commit<TWO>(mdone);
+      mbar_drain(mdone, 0);
+    } else if (TWO && lane == 0) {
+      // ---------------- the peer's warp 1: no MMA to issue; only takes its turn on the unit ring
+      int slot = 0;
+      uint32_t uphase = 0;
+      while (true) {
+        if (!mbar_wait<true>(&ufull[slot], uphase, W)) break;
+        const int u = uring[slot];
+        release_slot(slot);
+        if (++slot == URING) { slot = 0; uphase ^= 1; }
+        if (u < 0) break;
       }
     }
   } else {
@@ -582,16 +538,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
     for (int x = 0; x < 128; ++x) acc[x] = 0;
     while (ok) {
-      if (!mbar_wait_cluster(&ufull[slot], uphase, abort, P.status)) { ok = false; break; }
+      if (!mbar_wait<TWO>(&ufull[slot], uphase, W)) { ok = false; break; }
       const int u = uring[slot];
       __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(uempty_leader + 8u * (uint32_t)slot);
+      if (lane == 0) release_slot(slot);
       if (++slot == URING) { slot = 0; uphase ^= 1; }
       if (u < 0) break;
-      const Unit x = decode<CL>(P, u, rank);
+      const Unit x = decode<TWO>(P, u, rank);
       const int ck = P.prob[x.prob].chunk_kb;
       for (int c0 = 0; c0 < x.nkb; c0 += ck) {
-        if (!mbar_wait(&tfull[buf], tphase, abort, P.status)) { ok = false; break; }
+        if (!mbar_wait(&tfull[buf], tphase, W)) { ok = false; break; }
         tc_fence_after();
         const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + half * 128);
 #pragma unroll
@@ -603,8 +559,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) {   // CL = 3: the peer's warps release the buffer on the leader's barrier
-          if (CL == 3 && rank == 1) mbar_arrive_cluster_relaxed(mapa(smem_u32(&tempty[buf]), 0));
+        if (lane == 0) {   // pair: the peer's warps release the buffer on the leader's barrier
+          if (TWO && rank == 1) mbar_arrive_cluster_relaxed(mapa(smem_u32(&tempty[buf]), 0));
           else mbar_arrive(&tempty[buf]);
         }
         buf ^= 1;
@@ -633,18 +589,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CL == 3) cluster_sync();   // the leader's MMAs into the peer's TMEM are all drained
+  if (TWO) cluster_sync();   // the leader's MMAs into the peer's TMEM are all drained
   if (warp == 1) {
     tc_fence_after();
     __syncwarp();
-    if (CL == 3)
+    if (TWO)
       asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
                    : "memory");
     else
       asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
                    : "memory");
   }
-  if (CL >= 2) cluster_sync();   // neither CTA leaves while its peer may still signal it
+  if (TWO) cluster_sync();   // neither CTA leaves while its peer may still signal it
 }
 
 // ------------------------------------------------------------------ host side
@@ -690,11 +646,13 @@ int num_sms() {
 
 // One persistent launch over the units of up to kMaxBatch problems (the unit
 // counter lives in the first problem's status block, zeroed by its init).
-static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t st, int cluster) {
+template <bool TWO>
+static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t st, long long wait_limit) {
+  using C = TcCfg<TWO>;
   static TcMaps maps;    // host staging of the kernel parameters (copied at launch)
   static TcParams P;
   std::memset(&P, 0, sizeof(P));
-  const int pair = cluster == 1 ? 1 : 2;   // CTAs per unit
+  constexpr int pair = C::kPair;   // CTAs per unit
   int64_t units = 0;
   for (int q = 0; q < count; ++q) {
     const SliceGemmArgs &a = list[q];
@@ -704,7 +662,7 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
       if (a.prod[x].b_plane0 + a.prod[x].b_npos > planes_b) planes_b = a.prod[x].b_plane0 + a.prod[x].b_npos;
     }
     if (!make_map(&maps.a[q], a.dA, a.m, a.kpad, planes_a, BM) ||
-        !make_map(&maps.b[q], a.dB, a.n, a.kpad, planes_b, cluster == 1 ? BN : BN / 2))
+        !make_map(&maps.b[q], a.dB, a.n, a.kpad, planes_b, C::B_ROWS))
       return cudaErrorNotSupported;
     TcProblem &t = P.prob[q];
     t.m = a.m;
@@ -723,22 +681,23 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
   P.count = count;
   P.units = units;
   P.status = list[0].status;
+  P.poll = wait_limit > 0;
+  P.wait_limit = wait_limit > 0 ? wait_limit : kDefaultWaitCycles;
   if (units == 0) return cudaSuccess;
-  static bool attr[4] = {false, false, false, false};
-  auto kfn = cluster == 3 ? k_slicegemm_tc<3> : cluster == 2 ? k_slicegemm_tc<2> : k_slicegemm_tc<1>;
-  const size_t smem = cluster == 3 ? TcCfg<3>::SMEM : cluster == 2 ? TcCfg<2>::SMEM : TcCfg<1>::SMEM;
-  if (!attr[cluster]) {
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static bool attr = false;
+  auto kfn = k_slicegemm_tc<TWO>;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
-    attr[cluster] = true;
+    attr = true;
   }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute la[1];
   cfg.blockDim = dim3(NUM_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = C::SMEM;
   cfg.stream = st;
   int ctas = num_sms();
-  if (pair == 2) {
+  if (TWO) {
     la[0].id = cudaLaunchAttributeClusterDimension;
     la[0].val.clusterDim.x = 2;
     la[0].val.clusterDim.y = 1;
@@ -746,11 +705,10 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
     cfg.attrs = la;
     cfg.numAttrs = 1;
     cfg.gridDim = dim3((unsigned)ctas, 1, 1);
-    static int clusters[4] = {0, 0, 0, 0};   // queried once per variant (also keeps graph capture query-free)
-    if (clusters[cluster] == 0 &&
-        (cudaOccupancyMaxActiveClusters(&clusters[cluster], kfn, &cfg) != cudaSuccess || clusters[cluster] < 1))
-      clusters[cluster] = ctas / 2;
-    ctas = 2 * clusters[cluster];
+    static int clusters = 0;   // queried once (also keeps graph capture query-free)
+    if (clusters == 0 && (cudaOccupancyMaxActiveClusters(&clusters, kfn, &cfg) != cudaSuccess || clusters < 1))
+      clusters = ctas / 2;
+    ctas = 2 * clusters;
   }
   const int64_t need = units * pair;
   if (need < ctas) ctas = (int)need;
@@ -758,25 +716,26 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
   return cudaLaunchKernelEx(&cfg, kfn, maps, P);
 }
 
-cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, int cluster) {
+cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, bool two_sm,
+                                      long long wait_limit) {
   int dev = 0, major = 0, minor = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   if (major != 10 || minor != 3) return cudaErrorNotSupported;   // built for sm_103a only
-  if (cluster < 1 || cluster > 3) return cudaErrorInvalidValue;
   static std::mutex mu;            // the parameter staging below is shared
   std::lock_guard<std::mutex> lock(mu);
   for (int q0 = 0; q0 < count; q0 += kMaxBatch) {
     const int c = count - q0 < kMaxBatch ? count - q0 : kMaxBatch;
-    const cudaError_t e = launch_set(list + q0, c, st, cluster);
+    const cudaError_t e = two_sm ? launch_set<true>(list + q0, c, st, wait_limit)
+                                 : launch_set<false>(list + q0, c, st, wait_limit);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int cluster) {
-  return launch_slicegemm_tc_batch(&a, 1, st, cluster);
+cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, bool two_sm, long long wait_limit) {
+  return launch_slicegemm_tc_batch(&a, 1, st, two_sm, wait_limit);
 }
 
 }  // namespace mpc

@@ -36,7 +36,7 @@ def _problem(m, n, k, p=256, method="3m", algo="ozaki"):
 def fake_gpu(monkeypatch):
     import torch
     calls = []
-    cost = {"auto": 5.0, "tcgen05": 3.0, "tcgen05_pair": 4.0, "tcgen05_2sm": 1.0}
+    cost = {"auto": 5.0, "tcgen05": 3.0, "tcgen05_2sm": 1.0}
 
     def fake_batched(problems, params=None, workspace=None, stream=None):
         calls.append(dict(params))

@@ -4,8 +4,10 @@ It runs the same complex GEMM as mpcgemm() but keeps its scratch in a static
 device array of the library instead of a caller workspace.  The test calls it
 through the C ABI twice in a row (different inputs, so a stale scratch would
 show) and compares each result with mpcgemm()'s on the same inputs -- the
-tolerance of every other parity test here, i.e. bit for bit -- and checks that a
-problem larger than the array is refused with MPC_ENOSPC.  The file is named
+tolerance of every other parity test here, i.e. bit for bit --, reads the
+device status of each call back through mpcgemm_noalloc_read_status (which
+must show no error), and checks that a problem larger than the array is
+refused with MPC_ENOSPC.  The file is named
 to be collected last; it passes alone in a fresh process and after the rest.
 """
 import ctypes
@@ -30,6 +32,10 @@ def _noalloc(A, B, p, method, algo):
     rc = M.lib().mpcgemm_noalloc(m, n, k, p, ctypes.byref(sa), ctypes.byref(sb), ctypes.byref(sc),
                                  M._native.METHODS[method], M._native.ALGOS[algo], int(stream.cuda_stream))
     assert rc == 0, M.strerror(rc)
+    st = M._native.Status()
+    rc = M.lib().mpcgemm_noalloc_read_status(ctypes.byref(st), int(stream.cuda_stream))
+    assert rc == 0, M.strerror(rc)
+    assert (st.erange, st.fallback_overflow, st.uncertified, st.device_timeout) == (0, 0, 0, 0)
     torch.cuda.synchronize()
     s, e, l = dC.to_host()
     return si.MPCMatrix(m, n, p, s, e, l)
