@@ -36,14 +36,10 @@ import synthetic_inputs as si  # noqa: E402
 
 METRIC = "complex MP GEMM 8mnk/s at p=256/512/1024 bits: Ozaki-INT8 vs plain, 1 GB300"
 UNIT = "8mnk/s"
-WORKLOADS = {
-    # name: (m, n, k, p, dist, seed index)
-    "c2_2048_p1024": (2048, 2048, 2048, 1024, "uniform_exp", 2),
-    "c2_2048_p512": (2048, 2048, 2048, 512, "uniform_exp", 2),
-    "c2_1024_p512": (1024, 1024, 1024, 512, "uniform_exp", 2),
-    "c2_1024_p1024": (1024, 1024, 1024, 1024, "uniform_exp", 2),
-    "c1_256_p256": (256, 256, 256, 256, "uniform", 1),
-}
+# name -> (m, n, k, p, dist, seed index): the seeded workloads of synthetic_inputs
+SWEEP = [f"c2_{n}_p{p}" for n in (1024, 2048) for p in (256, 512, 1024)]
+WORKLOADS = {name: si.config_inputs(name) for name in SWEEP}
+WORKLOADS["c1_256_p256"] = si.config_inputs("c1_ozaki_256_p256")
 BATCH_WORKLOAD = "c3_batch64"
 PROFILE = os.path.join(ROOT, "profiles", "oz_slicegemm_c2_2048_p1024.md")
 # the slice GEMM kernel and the group table / unit schedule it runs over
@@ -88,22 +84,8 @@ def make_inputs(workload: str, rank: int):
     return A, B, p
 
 
-def batch_specs(count: int = 64, seed: int = si.SEED_BASE + 3):
-    """Config 3: m, n, k log-uniform in [64, 1024], p from {256, 512, 1024}, 3M."""
-    rng = np.random.default_rng(seed)
-    mnk = np.exp(rng.uniform(np.log(64), np.log(1024), size=(count, 3))).astype(int)
-    ps = rng.choice([256, 512, 1024], size=count)
-    return [(int(m), int(k), int(n), int(p)) for (m, n, k), p in zip(mnk, ps)]
-
-
-def batch_host_problems(specs):
-    """The seeded operands of the batched workload (host side)."""
-    out = []
-    for x, (m, k, n, p) in enumerate(specs):
-        A = si.random_matrix(m, k, p, si.SEED_BASE + 3000 + 2 * x, "uniform")
-        B = si.random_matrix(k, n, p, si.SEED_BASE + 3001 + 2 * x, "uniform")
-        out.append((A, B, p))
-    return out
+batch_specs = si.batch_specs
+batch_host_problems = si.batch_problems
 
 
 def run_batched(mp, torch, dev, stream, steps: int, warmup: int):
@@ -146,8 +128,9 @@ def run_batched(mp, torch, dev, stream, steps: int, warmup: int):
             "sum_8mnk": work, "tuned": best, "tuning_ms": {str(c): round(t, 3) for c, t in tuner.last_timings},
             "workspace_gb": round(total / 1e9, 2),
             "tensor_tflops_whole_call": round(flops / (ms / 1e3) / 1e12, 1),
-            "launch": "one CUDA graph replay per step (split/accumulate per problem, one persistent "
-                      "tcgen05 slice-GEMM launch for all problems)"}
+            "slice_gemm_launches": -(-len(specs) // 48) if best.get("kernel") != "mma_sync" else len(specs),
+            "launch": "one CUDA graph replay per step (split/accumulate per problem, persistent tcgen05 "
+                      "slice-GEMM launches of up to 48 problems each)"}
 
 
 def run_lu(mp, torch, dev, n: int = 2048, p: int = 512, block: int = 128, method: str = "3m"):
@@ -332,6 +315,81 @@ def committed_traffic(kernel_hash: str):
     return float(t.group(1))
 
 
+def sampled_check(mp, A, B, p, dC, count: int, seed: int) -> dict:
+    """Compare `count` sampled output entries (both components) with the exact C oracle."""
+    from oracle import c_oracle
+    rng = np.random.default_rng(seed)
+    ent = np.stack([rng.integers(0, A.rows, count), rng.integers(0, B.cols, count)], axis=1)
+    sg, ex, li = c_oracle.rounded_cgemm(A, B, p, ent)
+    s_, e_, l_ = dC.to_host()
+    ii, jj = ent[:, 0], ent[:, 1]
+    bad = (s_[:, ii, jj] != sg) | (e_[:, ii, jj] != ex) | np.any(l_[:, :, ii, jj] != li, axis=1)
+    return {"entries": int(count), "components": int(2 * count), "mismatches": int(bad.sum())}
+
+
+def slice_roofline(pl, method, m, n, k, gemm_ms, peak, peak_src):
+    flops = pair_count(pl["s"], pl["Q"], method) * 2.0 * m * n * k
+    achieved = flops / (gemm_ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": "oz_slicegemm", "achieved": round(achieved, 2), "peak": peak,
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "algorithmic_flops_per_launch": flops, "kernel_ms": round(gemm_ms, 3),
+            "peak_source": f"bf16_tflops_sustained ({peak_src})"}
+
+
+def run_sweep(mp, torch, dev, stream, ws, names, skip=None, known=None):
+    """Every precision of the metric at n = 1024 and 2048: Ozaki 3M / 4M and plain 3M / 4M,
+    each with its roofline, the speedup of Ozaki over plain, and a sampled oracle check.
+    ``known``: results already measured for the workload ``skip`` (the timed headline)."""
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    out = {}
+    for name in names:
+        m, n, k, p, _, _ = WORKLOADS[name]
+        units = 8.0 * m * n * k
+        if name == skip and known is not None:
+            out[name] = known
+            continue
+        t0 = time.time()
+        A, B, p = si.make_config(name)
+        dA, dB = mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(B, dev)
+        dC = mp.DeviceMatrix.empty(m, n, p, dev)
+        res = {"m": m, "n": n, "k": k, "p_bits": p}
+        for algo in ("ozaki", "plain"):
+            for method in ("3m", "4m"):
+                steps, warm = (3, 2) if algo == "ozaki" else (1, 1)
+                for _ in range(warm):
+                    mp.mpcgemm(dA, dB, dC, p, method, algo, workspace=ws, stream=stream)
+                torch.cuda.synchronize(dev)
+                evs = []
+                start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                start.record(stream)
+                for _ in range(steps):
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+                    mp.mpcgemm(dA, dB, dC, p, method, algo, workspace=ws, stream=stream, events=ev)
+                    evs.append(ev)
+                end.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = start.elapsed_time(end) / steps
+                stages = [float(np.mean([e[x].elapsed_time(e[x + 1]) for e in evs])) for x in range(4)]
+                pl = mp.plan(m, n, k, p, method, algo)
+                roof = (slice_roofline(pl, method, m, n, k, stages[1], peak, peak_src) if algo == "ozaki"
+                        else plain_roofline(mp, m, n, k, p, method, stages[1]))
+                st = mp.read_status(ws, stream)
+                res[f"{algo}_{method}"] = {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": round(ms, 3),
+                                           "steps": steps, "stage_ms": [round(x, 3) for x in stages],
+                                           "roofline": roof, "device_status": st,
+                                           "oracle_check": sampled_check(mp, A, B, p, dC, 16, 4242 + len(name))}
+        for method in ("3m", "4m"):
+            res[f"ozaki_speedup_vs_plain_{method}"] = round(res[f"ozaki_{method}"]["value"] /
+                                                            res[f"plain_{method}"]["value"], 2)
+        res["wall_s"] = round(time.time() - t0, 1)
+        out[name] = res
+        log(f"sweep {name}: ozaki 3m {res['ozaki_3m']['ms_per_step']:.2f} ms, plain 3m "
+            f"{res['plain_3m']['ms_per_step']:.1f} ms")
+        del dA, dB, dC
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as tdist
@@ -419,6 +477,7 @@ def run_ours(args):
     ms_main = max_over_ranks(ms_main)
     st = mp.read_status(ws, stream)
     value = units * args.steps * ws_ / (ms_main / 1e3)
+    gpu_out = dC.to_host() if rank == 0 and ws_ == 1 and not args.no_cpu else None   # checked by the oracle below
     extras = {}
     if not args.quick and algo == "ozaki":
         other = "4m" if method == "3m" else "3m"
@@ -431,6 +490,22 @@ def run_ours(args):
             extras[f"plain_{pm}"] = {"value": units * ws_ / (max_over_ranks(ms_pl) / 1e3), "ms_per_step": ms_pl,
                                      "stage_ms": st_pl, "roofline": plain_roofline(mp, m, n, k, p, pm, st_pl[1])}
         extras["ozaki_speedup_vs_plain"] = value / extras[f"plain_{method}"]["value"]
+        if not args.no_sweep and ws_ == 1:
+            peaks0, src0 = measured_peaks()
+            pk = float(peaks0.get("bf16_tflops_sustained", peaks0.get("bf16_tflops")))
+            known = {"m": m, "n": n, "k": k, "p_bits": p, "reused": "the timed headline measurement"}
+            for mt, ms_, stg in ((method, ms_main / args.steps, stages),
+                                 (other, extras[f"ozaki_{other}"]["ms_per_step"], extras[f"ozaki_{other}"]["stage_ms"])):
+                known[f"ozaki_{mt}"] = {"value": units / (ms_ / 1e3), "unit": UNIT, "ms_per_step": round(ms_, 3),
+                                        "stage_ms": [round(x, 3) for x in stg],
+                                        "roofline": slice_roofline(mp.plan(m, n, k, p, mt, "ozaki"), mt, m, n, k,
+                                                                   stg[1], pk, src0)}
+            for mt in (method, other):
+                known[f"plain_{mt}"] = extras[f"plain_{mt}"]
+            for mt in ("3m", "4m"):
+                known[f"ozaki_speedup_vs_plain_{mt}"] = round(known[f"ozaki_{mt}"]["value"] /
+                                                              known[f"plain_{mt}"]["value"], 2)
+            extras["precision_sweep"] = run_sweep(mp, torch, dev, stream, ws, SWEEP, skip=args.workload, known=known)
         if not args.no_batched:
             extras["batched_c3"] = run_batched(mp, torch, dev, stream, 3, 3)
         if not args.no_lu:
@@ -525,7 +600,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws_ == 1 and not args.no_cpu:
-        cpu = cpu_baseline(A, B, p, args.cpu_seconds)
+        cpu = cpu_baseline(A, B, p, args.cpu_seconds, gpu_out=gpu_out)
 
     if rank == 0:
         line = {
@@ -542,6 +617,7 @@ def run_ours(args):
                          "fallback": stages[3]},
             "device_status": st,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": pl["launches"] * args.steps,
+            "oracle_mismatches": cpu.get("oracle_mismatches") if cpu else None,
             "clocks": clocks.summary(), "extras": extras,
         }
         print(json.dumps(line), flush=True)
@@ -550,8 +626,11 @@ def run_ours(args):
         tdist.destroy_process_group()
 
 
-def cpu_baseline(A, B, p, seconds: float, entries_hint: int = 0):
-    """Time the oracle (C, exact, all host threads) on a bounded sample of output entries."""
+def cpu_baseline(A, B, p, seconds: float, entries_hint: int = 0, gpu_out=None):
+    """Time the oracle (C, exact, all host threads) on a bounded sample of output entries.
+
+    ``gpu_out``: (sign, exp, limb) of the GPU's product of the same A, B; the sampled
+    oracle entries are compared with it (both components, bit for bit)."""
     from oracle import c_oracle
     m, k, n = A.rows, A.cols, B.cols
     threads = c_oracle.max_threads()
@@ -566,11 +645,18 @@ def cpu_baseline(A, B, p, seconds: float, entries_hint: int = 0):
     cnt = entries_hint or int(max(probe, min(200000, probe * seconds / max(dt, 1e-6))))
     ent = sample(cnt)
     t0 = time.perf_counter()
-    c_oracle.rounded_cgemm(A, B, p, ent)
+    sg, ex, li = c_oracle.rounded_cgemm(A, B, p, ent)
     dt = time.perf_counter() - t0
-    return {"value": 8.0 * k * cnt / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{cnt} random output entries (both components) of the same {m}x{k}x{n} p={p} product, "
-                      f"exact C oracle, {dt:.1f} s"}
+    out = {"value": 8.0 * k * cnt / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{cnt} random output entries (both components) of the same {m}x{k}x{n} p={p} product, "
+                     f"exact C oracle, {dt:.1f} s"}
+    if gpu_out is not None:
+        s_, e_, l_ = gpu_out
+        ii, jj = ent[:, 0], ent[:, 1]
+        bad = (s_[:, ii, jj] != sg) | (e_[:, ii, jj] != ex) | np.any(l_[:, :, ii, jj] != li, axis=1)
+        out["oracle_checked_components"] = int(2 * cnt)
+        out["oracle_mismatches"] = int(bad.sum())
+    return out
 
 
 def cpu_baseline_batch(problems, seconds: float):
@@ -664,6 +750,7 @@ def main():
     ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_2sm", "mma_sync"], default="auto",
                     help="slice-GEMM kernel")
     ap.add_argument("--quick", action="store_true", help="skip the 4M / plain side measurements")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the precision sweep (n 1024/2048, p 256/512/1024)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,

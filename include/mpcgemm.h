@@ -116,6 +116,16 @@ typedef struct mpc_mat {
  *               flight complete, frees its tensor memory and returns; the results
  *               of that call are then invalid, the device and the library stay
  *               usable.  For tests of that path; leave it 0 otherwise.
+ *   dump_accumulators
+ *               nonzero: the plan adds a workspace region (mpc_plan.off_acc_dump)
+ *               where the accumulation stage writes, for every output component,
+ *               its exact accumulator Acc (Alg. 2's L-bit sum of the slice
+ *               products, before rounding): acc_slots 32-bit words of |Acc|,
+ *               least significant first, then one word holding 1 if Acc < 0,
+ *               at index ((i n + j) 2 + c) (acc_slots + 1), c = 0 real, 1
+ *               imaginary; its value is Acc 2^(E_i + F_j - (2w - 2) - w Q).
+ *               Rows of A or columns of B that are all zero are not written.
+ *               For stage checks; leave it 0 otherwise.
  */
 typedef struct mpc_oz_params {
     int32_t guard_bits;
@@ -125,7 +135,7 @@ typedef struct mpc_oz_params {
     int32_t max_group;
     int32_t digit_bits;
     int32_t wait_limit_cycles;
-    int32_t reserved;
+    int32_t dump_accumulators;
 } mpc_oz_params;
 
 /*
@@ -150,7 +160,8 @@ typedef struct mpc_plan {
     uint64_t off_status, off_rowexp, off_colexp, off_rowlossy, off_collossy;
     uint64_t off_digits_a, off_digits_b, off_groups, off_group_table;
     uint64_t off_fallback, fallback_capacity, off_fb_scratch, fb_scratch_limbs, fb_threads;
-    uint64_t off_fix_a, off_fix_b;  /* unused (0) */
+    uint64_t off_acc_dump;        /* accumulator dump (dump_accumulators), else 0 */
+    uint64_t off_unused;          /* 0 */
     uint64_t ws_bytes;
     int32_t launches;             /* kernel launches one call makes */
     int32_t digit_bits;           /* Ozaki: bits per digit w (8 or 9); plain: 28 */

@@ -28,9 +28,20 @@ namespace {
 
 constexpr int kMaxWords = 88;   // 32-bit words of the exact accumulator (Q <= 2s, s <= 160)
 
-struct WordAcc {   // 32-bit words of a thread-local array
-  const uint32_t *base;
-  __device__ __forceinline__ uint32_t operator()(int i) const { return base[i]; }
+// a block: kAccT consecutive elements of one row, one thread each
+constexpr int kAccT = 256, kAccBatch = 16, kAccStages = 2;
+
+// The exact accumulators' 32-bit words: a thread-local array (local memory, cached in
+// L1; the kernel leaves most of L1 to it by staging only a batch of groups in shared
+// memory).
+struct AccWords {
+  uint32_t *p;
+  __device__ __forceinline__ uint32_t &operator[](int i) const { return p[i]; }
+};
+
+struct WordAcc {   // read access for the rounding helpers
+  AccWords w;
+  __device__ __forceinline__ uint32_t operator()(int i) const { return w[i]; }
 };
 
 struct LimbAcc {   // 32-bit words of a little-endian uint64 array
@@ -49,7 +60,7 @@ struct DigitAcc {
   int64_t c = 0;      // value not yet emitted, in units of 2^(bits emitted)
   uint64_t bb = 0;    // emitted bits not yet written to `out` (nb of them, nb < 32)
   int nb = 0, cur = 0, next = 0;   // next: shift of the next level
-  __device__ __forceinline__ void step(uint32_t *out, int64_t h, int w) {
+  __device__ __forceinline__ void step(const AccWords &out, int64_t h, int w) {
     c += h;
     bb |= (uint64_t)(c & ((1ll << w) - 1)) << nb;
     c >>= w;   // floor
@@ -61,12 +72,12 @@ struct DigitAcc {
       nb -= 32;
     }
   }
-  __device__ __forceinline__ void add(uint32_t *out, int64_t h, int shift, int w) {
+  __device__ __forceinline__ void add(const AccWords &out, int64_t h, int shift, int w) {
     while (next < shift) step(out, 0, w);
     step(out, h, w);
   }
   // emit the remaining words; returns the sign (magnitude left in out[0, nw))
-  __device__ __forceinline__ bool finish(uint32_t *out, int nw) {
+  __device__ __forceinline__ bool finish(const AccWords &out, int nw) {
     if (cur < nw) {   // the buffered bits below the carry's bits (no carry between them)
       out[cur++] = (uint32_t)(bb | ((uint64_t)c << nb));
       c >>= (32 - nb);
@@ -89,15 +100,6 @@ struct DigitAcc {
 };
 }  // namespace
 
-// One accumulation term per group, in order of descending level: plane index,
-// the two signs, and -- on the last group of a level -- the level's shift.
-struct __align__(16) Term {   // 16 bytes: the accumulation reads it as one int4
-  int32_t plane;
-  int32_t shift;    // w (Q - q) on the last group of level q, else -1
-  int32_t s0, s1;   // the group's sign in the real / imaginary part: -1, 0 or 1
-};
-static_assert(sizeof(Term) == 16, "Term is read as one int4");
-
 // acc + (int64) v * s in one instruction
 __device__ __forceinline__ int64_t mad_wide(int32_t v, int32_t s, int64_t acc) {
   int64_t r;
@@ -106,10 +108,16 @@ __device__ __forceinline__ int64_t mad_wide(int32_t v, int32_t s, int64_t acc) {
 }
 
 // Round (or queue for the exact fallback) one component of one output element.
-__device__ __forceinline__ void finish_component(const AccumArgs &a, const OutView &C, DigitAcc &acc, uint32_t *words,
-                                                 int c, int64_t i, int64_t j, int32_t Ei, int32_t Fj) {
+__device__ __forceinline__ void finish_component(const AccumArgs &a, const OutView &C, DigitAcc &acc,
+                                                 const AccWords &words, int c, int64_t i, int64_t j, int32_t Ei,
+                                                 int32_t Fj) {
   const int64_t o = i * C.ld + j;
   const bool neg = acc.finish(words, a.nslot);
+  if (a.acc_dump) {   // the exact accumulator itself, for stage checks
+    uint32_t *d = a.acc_dump + ((i * a.n + j) * 2 + c) * (int64_t)(a.nslot + 1);
+    for (int x = 0; x < a.nslot; ++x) d[x] = words[x];
+    d[a.nslot] = neg ? 1u : 0u;
+  }
   WordAcc mag{words};
   const int N = bitlen(mag, a.nslot);
   const uint64_t b = a.bounds[c] + (uint64_t)a.k * ((a.lossyA[i] ? a.bounds[2 + c] : 0ull) +
@@ -130,15 +138,15 @@ __device__ __forceinline__ void finish_component(const AccumArgs &a, const OutVi
   }
 }
 
-// One thread per output element (i, j); a block takes kAccT consecutive
-// elements of one row.  The group values are staged through shared memory
-// kAccBatch groups at a time, double-buffered with cp.async: while the block
-// folds one batch the next one is in flight.  Each warp copies contiguous runs
-// of one group plane (16-byte copies when n is a multiple of 4).  The groups of
-// one level are summed in plain int64 (|sum| < 2^36) and folded into the exact
-// accumulators once per level.
-constexpr int kAccT = 256, kAccBatch = 16;
-constexpr size_t kAccStageBytes = 2ull * kAccBatch * kAccT * 4;
+// One thread per output element (i, j); a block takes kAccT consecutive elements of
+// one row.  The term table (plane, level shift, signs per group, in accumulation
+// order, written by k_group_table) is copied into shared memory.  The group values are
+// staged through shared memory kAccBatch groups at a time in a ring of kAccStages
+// buffers filled by cp.async, so that the next batch is in flight while the block
+// folds one.  Each warp copies contiguous runs of one group plane (16-byte copies when
+// n is a multiple of 4).  The groups of one level are summed in plain int64
+// (|sum| < 2^41) and folded into the exact accumulators once per level.
+constexpr size_t kAccStageBytes = (size_t)kAccStages * kAccBatch * kAccT * 4;
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -149,22 +157,18 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_by
                "l"(src), "r"(src_bytes));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
   extern __shared__ __align__(16) unsigned char acc_smem[];
   int32_t(*stage)[kAccBatch][kAccT] = reinterpret_cast<int32_t(*)[kAccBatch][kAccT]>(acc_smem);
-  Term *terms = reinterpret_cast<Term *>(acc_smem + kAccStageBytes);
+  int4 *sterm = reinterpret_cast<int4 *>(acc_smem + kAccStageBytes);   // AccTerm as (plane, shift, s0, s1)
   const int tid = threadIdx.x;
-  for (int x = tid; x < a.n_entries; x += blockDim.x) {
-    const int e = a.order[x];
-    const GroupEntry g = a.groups[e];
-    const bool last = (x + 1 == a.n_entries) || (a.groups[a.order[x + 1]].q != g.q);
-    const bool empty = g.count == 0;   // all its pairs were zero: its plane was never written
-    const bool z0 = a.bounds[6] != 0, z1 = a.bounds[7] != 0;   // components that vanish identically
-    terms[x] = Term{empty ? -1 : e, last ? a.w * (a.Q - g.q) : -1, empty || z0 ? 0 : product_sign(a.method, 0, g.prod),
-                    empty || z1 ? 0 : product_sign(a.method, 1, g.prod)};
-  }
+  uint32_t wbuf[2][kMaxWords];
+  const AccWords words[2] = {AccWords{wbuf[0]}, AccWords{wbuf[1]}};
+  const int4 *terms = reinterpret_cast<const int4 *>(a.terms);
+  for (int x = tid; x < a.n_entries; x += kAccT) sterm[x] = __ldg(&terms[x]);
   const int64_t i = blockIdx.y;
   const int64_t j0 = (int64_t)blockIdx.x * kAccT, j = j0 + tid;
   const int32_t Ei = a.E[i];
@@ -181,43 +185,46 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
   const int32_t *row = a.planes + i * a.n + j0;
   const int nrun = (int)(a.n - j0 < kAccT ? a.n - j0 : kAccT);   // valid elements of this block's run
   const bool vec = (a.n & 3) == 0;
-  __syncthreads();   // the term table is complete
-  auto issue = [&](int x0, int buf) {
-    const int nb = a.n_entries - x0 < kAccBatch ? a.n_entries - x0 : kAccBatch;
-    if (vec) {
-      for (int q = tid; q < nb * (kAccT / 4); q += kAccT) {
-        const int g = q / (kAccT / 4), c4 = 4 * (q % (kAccT / 4));
-        const int plane = terms[x0 + g].plane;
-        const int valid = plane < 0 ? 0 : (nrun - c4 >= 4 ? 4 : (nrun > c4 ? nrun - c4 : 0));
-        const int32_t *src = row + (plane < 0 ? 0 : (int64_t)plane * mn) + (valid ? c4 : 0);
-        cp_async16(&stage[buf][g][c4], src, 4 * valid);   // bytes beyond `valid` are zero-filled
-      }
-    } else {
-      for (int q = tid; q < nb * kAccT; q += kAccT) {
-        const int g = q / kAccT, c = q % kAccT;
-        const int plane = terms[x0 + g].plane;
-        const bool take = plane >= 0 && c < nrun;
-        const int32_t *src = row + (take ? (int64_t)plane * mn + c : 0);
-        cp_async4(&stage[buf][g][c], src, take ? 4 : 0);
+  const int nbatch = (a.n_entries + kAccBatch - 1) / kAccBatch;
+  __syncthreads();   // the term table is in shared memory
+  auto issue = [&](int bidx) {   // batch bidx into ring buffer bidx % kAccStages (an empty group if none)
+    if (bidx < nbatch) {
+      const int x0 = bidx * kAccBatch, buf = bidx % kAccStages;
+      const int nb = a.n_entries - x0 < kAccBatch ? a.n_entries - x0 : kAccBatch;
+      if (vec) {
+        for (int q = tid; q < nb * (kAccT / 4); q += kAccT) {
+          const int g = q / (kAccT / 4), c4 = 4 * (q % (kAccT / 4));
+          const int plane = sterm[x0 + g].x;
+          const int valid = plane < 0 ? 0 : (nrun - c4 >= 4 ? 4 : (nrun > c4 ? nrun - c4 : 0));
+          const int32_t *src = row + (plane < 0 ? 0 : (int64_t)plane * mn) + (valid ? c4 : 0);
+          cp_async16(&stage[buf][g][c4], src, 4 * valid);   // bytes beyond `valid` are zero-filled
+        }
+      } else {
+        for (int q = tid; q < nb * kAccT; q += kAccT) {
+          const int g = q / kAccT, c = q % kAccT;
+          const int plane = sterm[x0 + g].x;
+          const bool take = plane >= 0 && c < nrun;
+          const int32_t *src = row + (take ? (int64_t)plane * mn + c : 0);
+          cp_async4(&stage[buf][g][c], src, take ? 4 : 0);
+        }
       }
     }
-    cp_async_commit();
+    cp_async_commit();   // always one group per batch slot: the wait counts stay uniform
   };
-  uint32_t words[2][kMaxWords];
   DigitAcc acc[2];
   int64_t sum0 = 0, sum1 = 0;
-  issue(0, 0);
-  for (int x0 = 0, buf = 0; x0 < a.n_entries; x0 += kAccBatch, buf ^= 1) {
-    if (x0 + kAccBatch < a.n_entries) issue(x0 + kAccBatch, buf ^ 1);
-    else cp_async_commit();   // an empty group keeps the wait count uniform
-    cp_async_wait1();
+#pragma unroll
+  for (int b = 0; b < kAccStages - 1; ++b) issue(b);
+  for (int bidx = 0; bidx < nbatch; ++bidx) {
+    issue(bidx + kAccStages - 1);
+    cp_async_wait<kAccStages - 1>();   // batch bidx has landed
     __syncthreads();
     if (active) {
+      const int x0 = bidx * kAccBatch, buf = bidx % kAccStages;
       const int nb = a.n_entries - x0 < kAccBatch ? a.n_entries - x0 : kAccBatch;
-      const int4 *tv = reinterpret_cast<const int4 *>(terms) + x0;   // Term as (plane, shift, s0, s1)
 #pragma unroll 4
       for (int u = 0; u < nb; ++u) {
-        const int4 t = tv[u];                      // block-uniform
+        const int4 t = sterm[x0 + u];              // block-uniform (broadcast)
         const int32_t v = stage[buf][u][tid];
         sum0 = mad_wide(v, t.z, sum0);
         sum1 = mad_wide(v, t.w, sum1);
@@ -385,11 +392,11 @@ __global__ void k_zero_output(OutView C, int64_t m, int64_t n, int L) {
 // ---------------------------------------------------------------- launchers
 
 void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st) {
-  const size_t smem = kAccStageBytes + (size_t)a.n_entries * sizeof(Term);
+  const size_t smem = kAccStageBytes + (size_t)a.n_entries * sizeof(AccTerm);
   static std::once_flag once;   // allow the largest table any plan can have, once per process
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_oz_accum, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(kAccStageBytes + (size_t)kMaxGroupsTotal * sizeof(Term)));
+                         (int)(kAccStageBytes + (size_t)kMaxGroupsTotal * sizeof(AccTerm)));
   });
   dim3 g((unsigned)((a.n + kAccT - 1) / kAccT), (unsigned)a.m);
   k_oz_accum<<<g, kAccT, smem, st>>>(a, C);

@@ -192,7 +192,11 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   off = align256(off + (uint64_t)total * sizeof(GroupEntry));
   // accumulation order, the slice GEMM's schedule, the operands' flags, the data-dependent bounds
   P.off_group_order = off;
-  off = align256(off + bounds_offset(total, P.planes_A, P.planes_B) + 8 * 8);
+  off = align256(off + order_region_bytes(total, P.planes_A, P.planes_B));
+  if (prm && prm->dump_accumulators) {
+    P.off_acc_dump = off;
+    off = align256(off + (uint64_t)2 * m * n * (P.acc_slots + 1) * 4);
+  }
   P.ws_bytes = off;
   P.launches = 9;     // init, row max, column max, group table, 2 x digits, slice GEMM, accumulate, fallback
   return MPC_OK;
@@ -326,6 +330,7 @@ void call_pre(Call &c, cudaStream_t st) {
     ga.table = (GroupEntry *)(c.ws + P.off_group_table);
     ga.order = (int32_t *)(c.ws + P.off_group_order);
     ga.bounds = (uint64_t *)(c.ws + P.off_group_order + bounds_offset(P.n_groups_total, P.planes_A, P.planes_B));
+    ga.terms = (AccTerm *)(c.ws + P.off_group_order + terms_offset(P.n_groups_total, P.planes_A, P.planes_B));
     launch_group_table(ga, st);
   }
 }
@@ -419,6 +424,7 @@ void call_accum(Call &c, cudaStream_t st) {
   aa.bound_shift = P.bound_shift;
   aa.w = P.digit_bits;
   aa.bounds = (const uint64_t *)(c.ws + P.off_group_order + bounds_offset(P.n_groups_total, P.planes_A, P.planes_B));
+  aa.terms = (const AccTerm *)(c.ws + P.off_group_order + terms_offset(P.n_groups_total, P.planes_A, P.planes_B));
   for (int x = 0; x < 2; ++x) {
     aa.bound_drop[x] = P.bound_drop[x];
     aa.bound_lossy_a[x] = P.bound_lossy_a[x];
@@ -427,6 +433,7 @@ void call_accum(Call &c, cudaStream_t st) {
   aa.fallback = c.fallback;
   aa.fallback_cap = (int64_t)P.fallback_capacity;
   aa.status = c.status;
+  aa.acc_dump = P.off_acc_dump ? (uint32_t *)(c.ws + P.off_acc_dump) : nullptr;
   launch_oz_accum(aa, c.C, st);
 }
 

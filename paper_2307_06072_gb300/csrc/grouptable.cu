@@ -40,7 +40,10 @@ __device__ __forceinline__ void product_kinds(int method, int prod, int &ka, int
 //   lossy_b[c] likewise;
 // all three are zero for a component of A B that vanishes identically, and
 // zero[c] (bounds[6 + c]) tells the accumulation to add nothing into it: a product
-// needed only there (the 3M sums for real inputs) was emptied.
+// needed only there (the 3M sums for real inputs) was emptied.  Finally all threads
+// write the accumulation's term table (one entry per group, in accumulation order).
+__device__ void serial_passes(const GroupTableArgs &a, const int32_t *s_qc, const uint64_t *s_bd, int *s_start);
+
 __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
   __shared__ uint64_t s_bd[4];
   __shared__ int32_t s_qc[kMaxGroupsTotal];   // per group: (q + 8) << 16 | count, for the serial passes below
@@ -92,7 +95,24 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
     s_qc[e] = ((g.q + 8) << 16) | g.count;   // q >= -2, count <= kMaxSlices + 1
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x == 0) serial_passes(a, s_qc, s_bd, s_start);
+  __syncthreads();   // order and bounds written (global memory, visible within the block)
+  // the accumulation's term table, one entry per group in the accumulation order
+  const int G = n_groups;
+  const bool z0 = a.bounds[6] != 0, z1 = a.bounds[7] != 0;   // components that vanish identically
+  for (int x = threadIdx.x; x < G; x += blockDim.x) {
+    const int e = a.order[x];
+    const int q = (s_qc[e] >> 16) - 8, count = s_qc[e] & 0xFFFF;
+    const bool last = (x + 1 == G) || ((s_qc[a.order[x + 1]] >> 16) - 8 != q);
+    const bool empty = count == 0;   // all its pairs were zero: its plane is never written
+    const int prod = a.table[e].prod;
+    a.terms[x] = AccTerm{empty ? -1 : e, last ? a.w * (a.Q - q) : -1, empty || z0 ? 0 : product_sign(a.method, 0, prod),
+                      empty || z1 ? 0 : product_sign(a.method, 1, prod)};
+  }
+}
+
+// Thread 0's passes: accumulation order, unit schedule, bounds.
+__device__ void serial_passes(const GroupTableArgs &a, const int32_t *s_qc, const uint64_t *s_bd, int *s_start) {
   const ProductDesc *pds = a.prod;
   const int n_products = a.n_products;
   int32_t *order = a.order;

@@ -21,6 +21,16 @@ struct SliceGemmArgs {
   int32_t *status;
 };
 
+// One accumulation term per group, in the accumulation order (descending level):
+// group plane index (-1: an emptied group), the two signs, and -- on the last group
+// of a level -- the level's shift.  Written by k_group_table, read by k_oz_accum.
+struct __align__(16) AccTerm {
+  int32_t plane;
+  int32_t shift;    // w (Q - q) on the last group of level q, else -1
+  int32_t s0, s1;   // the group's sign in the real / imaginary part: -1, 0 or 1
+};
+static_assert(sizeof(AccTerm) == 16, "AccTerm is read as one int4");
+
 // Group table, accumulation order, unit schedule and the data-dependent error
 // bounds of one Ozaki call (k_group_table, after the digits).
 struct GroupTableArgs {
@@ -32,12 +42,22 @@ struct GroupTableArgs {
   GroupEntry *table;
   int32_t *order;                   // accumulation order [G], then the unit schedule [G]
   uint64_t *bounds;                 // out: drop[2], lossy_a[2], lossy_b[2], zero[2]
+  AccTerm *terms;                      // out: the accumulation's term table [G]
 };
 
 // byte offset of the bounds inside the group-order region
 __host__ __device__ inline uint64_t bounds_offset(int64_t groups, int planes_A, int planes_B) {
   const uint64_t b = (uint64_t)groups * 8 + (uint64_t)(planes_A + 2 + planes_B + 2) * 4;
   return (b + 7) & ~7ull;
+}
+
+// byte offset of the term table inside the group-order region (after the 8 bounds), and
+// the region's size
+__host__ __device__ inline uint64_t terms_offset(int64_t groups, int planes_A, int planes_B) {
+  return (bounds_offset(groups, planes_A, planes_B) + 8 * 8 + 15) & ~15ull;
+}
+__host__ __device__ inline uint64_t order_region_bytes(int64_t groups, int planes_A, int planes_B) {
+  return terms_offset(groups, planes_A, planes_B) + (uint64_t)groups * sizeof(AccTerm);
 }
 
 struct AccumArgs {
@@ -51,9 +71,11 @@ struct AccumArgs {
   int bound_shift, w;          // bounds are b 2^beta; w bits per digit
   uint64_t bound_drop[2], bound_lossy_a[2], bound_lossy_b[2];   // data-independent (plan)
   const uint64_t *bounds;       // the call's bounds (drop[2], lossy_a[2], lossy_b[2], zero[2]), from k_group_table
+  const AccTerm *terms;            // the term table, from k_group_table
   int64_t *fallback;            // list of (i*n + j)*2 + c
   int64_t fallback_cap;
   int32_t *status;
+  uint32_t *acc_dump;           // null, or per component: nslot words of |Acc| and its sign
 };
 
 struct FallbackArgs {

@@ -59,7 +59,7 @@ struct TcCfg {
   static constexpr int A_BYTES = BM * BK * 2, B_BYTES = B_ROWS * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 512;   // 7 x 32 KB + barriers <= 227 KB
 };
-constexpr int NUM_THREADS = 320, EPI_WARPS = 8;
+constexpr int EPI_WARPS = 8;   // 16 warps of 64 columns measured slower (more spills, no faster drain)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long kDefaultWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 constexpr int URING = 4;                                   // unit-index ring slots
@@ -347,9 +347,10 @@ __device__ __forceinline__ bool unit_empty(const TcParams &P, int64_t u) {
 // drained TMEM buffer back on the leader's barrier.  The leader hands out the
 // unit indices to both CTAs through distributed shared memory.
 template <bool TWO>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
+__global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     k_slicegemm_tc(const __grid_constant__ TcMaps maps, const __grid_constant__ TcParams P) {
   using C = TcCfg<TWO>;
+  constexpr int COLS = 4 * BN / EPI_WARPS;    // accumulator columns per epilogue thread (one TMEM lane)
   constexpr int STAGES = C::STAGES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -529,14 +530,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   } else {
     // ---------------- epilogue: warps 2..9
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. +31 (hardware rule: warp id % 4)
-    const int half = (warp - 2) >> 2;          // columns half*128 .. +127
+    const int part = (warp - 2) >> 2;          // columns part*COLS .. +COLS-1
     const int row_in_tile = quad * 32 + lane;
     int buf = 0, slot = 0;
     uint32_t tphase = 0, uphase = 0;
     bool ok = true;
-    int32_t acc[128];
+    int32_t acc[COLS];
 #pragma unroll
-    for (int x = 0; x < 128; ++x) acc[x] = 0;
+    for (int x = 0; x < COLS; ++x) acc[x] = 0;
     while (ok) {
       if (!mbar_wait<TWO>(&ufull[slot], uphase, W)) { ok = false; break; }
       const int u = uring[slot];
@@ -549,9 +550,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       for (int c0 = 0; c0 < x.nkb; c0 += ck) {
         if (!mbar_wait(&tfull[buf], tphase, W)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + half * 128);
+        const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + part * COLS);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < COLS / 32; ++j) {
           uint32_t r[32];
           tmem_ld32(taddr + (uint32_t)(j * 32), r);
 #pragma unroll
@@ -570,21 +571,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       // store the int32 tile rows of this thread
       const int64_t pm = P.prob[x.prob].m, pn = P.prob[x.prob].n;
       const int64_t row = (int64_t)x.tm * BM + row_in_tile;
-      const int64_t col0 = (int64_t)x.tn * BN + half * 128;
+      const int64_t col0 = (int64_t)x.tn * BN + part * COLS;
       if (row < pm) {
         int32_t *dst = P.prob[x.prob].out + (int64_t)x.e * pm * pn + row * pn + col0;
-        if (col0 + 128 <= pn && ((pn & 3) == 0)) {
+        if (col0 + COLS <= pn && ((pn & 3) == 0)) {
 #pragma unroll
-          for (int v = 0; v < 32; ++v)
+          for (int v = 0; v < COLS / 4; ++v)
             reinterpret_cast<int4 *>(dst)[v] = make_int4(acc[4 * v], acc[4 * v + 1], acc[4 * v + 2], acc[4 * v + 3]);
         } else {
 #pragma unroll
-          for (int v = 0; v < 128; ++v)
+          for (int v = 0; v < COLS; ++v)
             if (col0 + v < pn) dst[v] = acc[v];
         }
       }
 #pragma unroll
-      for (int v = 0; v < 128; ++v) acc[v] = 0;
+      for (int v = 0; v < COLS; ++v) acc[v] = 0;
     }
   }
   tc_fence_before();
@@ -693,7 +694,7 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
   }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute la[1];
-  cfg.blockDim = dim3(NUM_THREADS, 1, 1);
+  cfg.blockDim = dim3(64 + 32 * EPI_WARPS, 1, 1);
   cfg.dynamicSmemBytes = C::SMEM;
   cfg.stream = st;
   int ctas = num_sms();

@@ -108,55 +108,118 @@ __device__ __forceinline__ uint64_t word_at_bit(const uint64_t *M, int L, int64_
 }
 
 // Per element and component: the shifted magnitude |X| = M >> sh (M the L-limb
-// mantissa, sh may be negative), read 64 bits at a time, least significant first,
-// straight from the input limbs: word w of |X| is bits [64 w + sh, 64 w + sh + 64)
-// of M, i.e. limbs w + floor(sh / 64) and the next one; the next one is kept for
-// the following word, so every limb is loaded once and nothing is held in memory
-// indexed at run time.
+// mantissa, sh may be negative), read 32 bits at a time, least significant first,
+// straight from the input limbs (as 32-bit halves): word w of |X| is bits
+// [32 w + sh, 32 w + sh + 32) of M; the upper half-limb is kept for the following
+// word, so every half-limb is loaded once and nothing is held in memory indexed at
+// run time.
 struct LimbStream {
-  const uint64_t *p;   // limb 0 of the element (limb j at p[j * stride])
-  int64_t j;           // index of the limb in `cur`
-  uint64_t cur;
-  int off;             // sh mod 64
+  const uint32_t *p;   // low half of limb 0 (half-limb j at p[(j / 2) * 2 * stride + (j & 1)])
+  int64_t j;           // index of the half-limb in `cur`
+  uint32_t cur;
+  int off;             // sh mod 32
   bool live;
-  __device__ __forceinline__ uint64_t limb(int64_t jj, int64_t stride, int L) const {
-    return (live && jj >= 0 && jj < L) ? p[jj * stride] : 0ull;
+  __device__ __forceinline__ uint32_t half(int64_t jj, int64_t stride, int L) const {
+    return (live && jj >= 0 && jj < 2 * (int64_t)L) ? p[(jj >> 1) * 2 * stride + (jj & 1)] : 0u;
   }
   __device__ __forceinline__ void start(const uint64_t *base, bool nz, int64_t sh, int64_t stride, int L) {
-    p = base;
+    p = reinterpret_cast<const uint32_t *>(base);
     live = nz;
-    off = (int)(sh & 63);
-    j = sh >> 6;   // floor
-    cur = limb(j, stride, L);
+    off = (int)(sh & 31);
+    j = sh >> 5;   // floor
+    cur = half(j, stride, L);
   }
-  __device__ __forceinline__ uint64_t next(int64_t stride, int L) {
-    const uint64_t hi = limb(j + 1, stride, L);
-    const uint64_t x = off ? ((cur >> off) | (hi << (64 - off))) : cur;
+  __device__ __forceinline__ uint32_t next(int64_t stride, int L) {
+    const uint32_t hi = half(j + 1, stride, L);
+    const uint32_t x = __funnelshift_r(cur, hi, off);   // off = 0: cur
     cur = hi;
     ++j;
     return x;
   }
 };
 
+// Balanced digits without a carry per digit.  With H = sum_{pos < T-1} 2^(w-1) 2^(w pos)
+// and Y = X + H (two's complement), the digits of X in base 2^w with the lower digits in
+// [-2^(w-1), 2^(w-1)) are  d_pos = field_pos(Y) - 2^(w-1)  (pos < T-1) and the top digit
+// d_{T-1} = Y >> w (T-1) (arithmetic), the unique such representation of X.
+//
+// Digits are produced in blocks of 32 (32 w bits = w 32-bit words of Y), so that every
+// field sits at a compile-time bit offset.  bf16 of a digit: the float 2^23 + field
+// (an integer OR) minus 2^23 + 2^(w-1) (one exact subtraction), whose upper 16 bits are
+// the bf16 (|d| <= 256 has at most 8 significant bits).
+template <int W>
+__host__ __device__ constexpr uint32_t hpattern(int j) {   // H's bits in word j of a block
+  uint32_t v = 0;
+  for (int b = 0; b < 32; ++b)
+    if ((32 * j + b) % W == W - 1) v |= 1u << b;
+  return v;
+}
+
+// The `width` bits at [off, off + width) of the W words y, in the low bits of the result;
+// `next` is the word that follows y.  Called with `off` and `width` constant after loop
+// unrolling, so the indexing and shifts fold away.
+template <int W>
+__device__ __forceinline__ uint32_t bits_at(const uint32_t *y, uint32_t next, int off, int width) {
+  const int wd = off / 32, sh = off % 32;
+  if (sh + width <= 32) return y[wd] >> sh;
+  return __funnelshift_r(y[wd], wd + 1 == W ? next : y[wd + 1], sh);
+}
+
+// One block of 32 digit positions (global positions 32 blk + i) of one digit stream of
+// two elements: y0 / y1 hold the 32 w bits of Y for each element.  T = digit count;
+// TAIL: this block holds digit T-1 (the top digit) or positions >= T.
+template <int W, bool TAIL>
+__device__ __forceinline__ void emit_block(const uint32_t *y0, const uint32_t *y1, uint32_t next0, uint32_t next1,
+                                           int blk, int T, __nv_bfloat162 *out, int64_t plane_step, bool store,
+                                           uint32_t &nzmask) {
+  constexpr uint32_t MASK = (1u << W) - 1u;
+  const float bias = 8388608.0f + (float)(1 << (W - 1));   // 2^23 + 2^(w-1)
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int pos = 32 * blk + i;
+    float d0, d1;
+    if (TAIL && pos == T - 1) {   // top digit: Y >> w (T-1) as a signed (w+1)-bit value
+      const uint32_t f0 = bits_at<W>(y0, next0, W * i, W + 1), f1 = bits_at<W>(y1, next1, W * i, W + 1);
+      const int t0 = ((int32_t)(f0 << (31 - W))) >> (31 - W), t1 = ((int32_t)(f1 << (31 - W))) >> (31 - W);
+      d0 = __int_as_float(0x4B000000 | (uint32_t)(t0 + 2 * (1 << (W - 1)))) - (8388608.0f + (float)(2 << (W - 1)));
+      d1 = __int_as_float(0x4B000000 | (uint32_t)(t1 + 2 * (1 << (W - 1)))) - (8388608.0f + (float)(2 << (W - 1)));
+    } else {
+      const uint32_t f0 = bits_at<W>(y0, next0, W * i, W), f1 = bits_at<W>(y1, next1, W * i, W);
+      d0 = __int_as_float(0x4B000000 | (f0 & MASK)) - bias;
+      d1 = __int_as_float(0x4B000000 | (f1 & MASK)) - bias;
+    }
+    const uint32_t packed = __byte_perm(__float_as_uint(d0), __float_as_uint(d1), 0x7632);
+    if (!TAIL || pos < T) {
+      if (store) out[-(int64_t)pos * plane_step] = *reinterpret_cast<const __nv_bfloat162 *>(&packed);
+      if (packed) nzmask |= 1u << i;
+    }
+  }
+}
+
 // One thread per (line, l, l+1): digits of two adjacent elements of a line.
 // Side A: line = row i, element (i, l).  Side B: line = column j, element (l, j).
 // Output planes: digits[(plane * lines + line) * kpad + l], plane = t (real),
-// s + t (imaginary), 2s + 1 + t (sums, t = -1 .. s-1).
-__device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad,
-                                               int L, int s, int wd, int want_sum, const int32_t *E, int32_t *lossy,
-                                               __nv_bfloat16 *digits, int64_t l0, int64_t line, bool in_range,
-                                               int *nz) {
-  const bool leader = (threadIdx.x & 31) == 0;
-  const int64_t pstride = lines * kpad;
+// s + t (imaginary), 2s + 1 + t (sums, t = -1 .. s-1); digit position pos (least
+// significant first) of the real part is plane s - 1 - pos.
+template <int W>
+__global__ void __launch_bounds__(128, 4) k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64_t kpad, int L,
+                                                   int s, int want_sum, const int32_t *E, int32_t *lossy,
+                                                   __nv_bfloat16 *digits, int32_t *plane_nz) {
+  __shared__ uint32_t nzbits[3][8];   // [stream][32-digit block]: a nonzero digit there
+  __shared__ int nzcomp[2];
+  if (threadIdx.x < 24) nzbits[threadIdx.x / 8][threadIdx.x % 8] = 0;
+  if (threadIdx.x < 2) nzcomp[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t l0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  const int64_t line = blockIdx.y;
+  // kpad is even: l0 + 1 < kpad; out-of-range threads still take part in the warp reductions
+  const bool in_range = l0 < kpad && line < lines;
+  const int64_t pstride2 = lines * kpad / 2;
   __nv_bfloat162 *out = reinterpret_cast<__nv_bfloat162 *>(digits + line * kpad + l0);
-  const int64_t pstride2 = pstride / 2;
-  const int nplanes = 2 * s + (want_sum ? s + 1 : 0);
   const int32_t e_line = in_range ? E[line] : INT32_MIN;
-  const int64_t xbits = (int64_t)wd * s;                 // |X| < 2^(xbits - 1)
+  const int64_t xbits = (int64_t)W * s;                  // |X| < 2^(xbits - 1)
   LimbStream m[2][2];                                    // [element][re, im]
-  bool neg[2][2];
-  uint64_t cneg[2][2], csum[2];                          // two's-complement and X_re + X_im carries
-  int cbal[2][2], cbal_s[2];                             // balanced-digit carries
+  uint32_t neg[2][2];
   bool ok = true;
   bool nzv[2] = {false, false};   // a nonzero real / imaginary value among the two elements
 #pragma unroll
@@ -171,9 +234,7 @@ __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64
       // |X| bit b  <->  M bit b + sh:  X = |v| 2^(ws-1-E), |v| = M 2^(exp-64L)
       const int64_t sh = nzc ? (64 * (int64_t)L + (int64_t)e_line - (int64_t)X.exp[c][idx] - (xbits - 1)) : 0;
       m[q][c].start(X.limb[c] + idx, nzc, sh, X.plane, L);
-      neg[q][c] = nzc && X.sign[c][idx];
-      cneg[q][c] = 1;
-      cbal[q][c] = 0;
+      neg[q][c] = (nzc && X.sign[c][idx]) ? 1u : 0u;
       if (nzc && sh > 0) {   // the bits of M below sh are dropped: the line is lossy unless they are zero
         if (sh >= 64 * (int64_t)L) {
           ok = false;
@@ -186,125 +247,98 @@ __device__ __forceinline__ void oz_digits_pair(const MatView &X, int side, int64
         }
       }
     }
-    csum[q] = 0;
-    cbal_s[q] = 0;
   }
   if (!ok) atomicOr(lossy + line, 1);
 #pragma unroll
   for (int c = 0; c < 2; ++c)
-    if (__ballot_sync(0xffffffffu, nzv[c]) && leader) nz[nplanes + c] = 1;
-  // Digits, least significant first, from LSB-first bit streams of the two's-complement
-  // words of X_re, X_im (wd*s bits) and X_re + X_im: every stream keeps a 128-bit buffer
-  // (lo, hi) holding `nbuf` bits; all streams advance in step (wd bits per digit).
-  const int ndig = want_sum ? s + 1 : s;
-  const uint32_t fmask = (1u << wd) - 1u;
-  const int half = 1 << (wd - 1), full = 1 << wd;
-  uint64_t blo[2][3], bhi[2][3];                         // [element][re, im, sum]
+    if (__any_sync(0xffffffffu, nzv[c]) && (threadIdx.x & 31) == 0) nzcomp[c] = 1;
+  // Y = X'' + H + neg for the real and imaginary parts (X'' = |X| or its one's complement,
+  // so that X'' + neg is X in two's complement) and Y = X''_re + X''_im + H' + neg_re + neg_im
+  // for the 3M sum, 32 digit positions (W words of 32 bits) per block.
+  uint32_t cy[2][3];
 #pragma unroll
-  for (int q = 0; q < 2; ++q)
+  for (int q = 0; q < 2; ++q) {
+    cy[q][0] = neg[q][0];
+    cy[q][1] = neg[q][1];
+    cy[q][2] = neg[q][0] + neg[q][1];
+  }
+  const int Ts = s + 1;                                   // digits of the 3M sums
+  const int nblk = ((want_sum ? Ts : s) + 31) / 32;
+  for (int blk = 0; blk < nblk; ++blk) {
+    uint32_t xw[2][2][W];                                 // [element][re, im] one's-complement words of |X|
 #pragma unroll
-    for (int c = 0; c < 3; ++c) blo[q][c] = bhi[q][c] = 0;
-  int nbuf = 0, wnext = 0;
-  for (int pos = 0; pos < ndig; ++pos) {
-    if (nbuf < wd) {   // append word `wnext` of every stream above the bits still buffered
-      uint64_t wc[2][3];
-      const int64_t top = xbits - 64 * (int64_t)wnext;   // bits of |X| in this word
-      const uint64_t tmask = top >= 64 ? ~0ull : (top <= 0 ? 0ull : ((1ull << top) - 1ull));
+    for (int j = 0; j < W; ++j) {
+      const int64_t top = xbits - 32 * ((int64_t)blk * W + j);   // bits of |X| in this word
+      const uint32_t tmask = top >= 32 ? ~0u : (top <= 0 ? 0u : ((1u << top) - 1u));
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
+      for (int q = 0; q < 2; ++q)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          uint64_t x = m[q][c].next(X.plane, L) & tmask;
-          if (neg[q][c]) {
-            const uint64_t t = ~x + cneg[q][c];
-            cneg[q][c] = (cneg[q][c] && t == 0) ? 1ull : 0ull;
-            x = t;
-          }
-          wc[q][c] = x;
+          const uint32_t x = m[q][c].next(X.plane, L) & tmask;
+          xw[q][c][j] = neg[q][c] ? ~x : x;
         }
-        const uint64_t a0 = wc[q][0] + wc[q][1];
-        const uint64_t c1 = a0 < wc[q][0];
-        const uint64_t a1 = a0 + csum[q];
-        const uint64_t c2 = a1 < a0;
-        wc[q][2] = a1;
-        csum[q] = c1 | c2;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          blo[q][c] |= wc[q][c] << nbuf;
-          bhi[q][c] = nbuf ? (wc[q][c] >> (64 - nbuf)) : 0ull;
-        }
-      }
-      nbuf += 64;
-      ++wnext;
     }
-    int fld[2][3];
+    // One stream at a time (not unrolled: a single copy of the block code keeps the
+    // instruction cache warm); operands and carries are picked by selects so that
+    // nothing is indexed at run time.  Stream st: 0 re (X_re + H), 1 im (X_im + H),
+    // 2 the 3M sums (X_re + X_im + H').
+#pragma unroll 1
+    for (int st = 0; st < (want_sum ? 3 : 2); ++st) {
+      const int T = st == 2 ? Ts : s;
+      if (32 * blk >= T) continue;
+      uint32_t y[2][W];
+      uint32_t c[2];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+      for (int q = 0; q < 2; ++q) c[q] = st == 0 ? cy[q][0] : st == 1 ? cy[q][1] : cy[q][2];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        fld[q][c] = (int)(blo[q][c] & fmask);
-        blo[q][c] = (blo[q][c] >> wd) | (bhi[q][c] << (64 - wd));
-        bhi[q][c] >>= wd;
-      }
-    nbuf -= wd;
-    if (pos < s) {
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        float f[2];
+      for (int j = 0; j < W; ++j) {
+        const int64_t lim = (int64_t)W * (T - 1) - 32 * ((int64_t)blk * W + j);   // H below digit T-1 only
+        const uint32_t h = hpattern<W>(j) & (lim >= 32 ? ~0u : (lim <= 0 ? 0u : ((1u << lim) - 1u)));
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          int dg;
-          if (pos == s - 1) {   // top digit: the signed field plus the carry
-            dg = (fld[q][c] >= half ? fld[q][c] - full : fld[q][c]) + cbal[q][c];
-          } else {
-            dg = fld[q][c] + cbal[q][c];
-            cbal[q][c] = dg >= half;
-            if (dg >= half) dg -= full;
-          }
-          f[q] = (float)dg;
+          const uint32_t x = st == 1 ? xw[q][1][j] : xw[q][0][j];
+          const uint32_t x2 = st == 2 ? xw[q][1][j] : 0u;
+          const uint64_t t = (uint64_t)x + x2 + h + c[q];   // carry in and out <= 2
+          c[q] = (uint32_t)(t >> 32);
+          y[q][j] = (uint32_t)t;
         }
-        if (in_range) out[(int64_t)(c * s + (s - 1 - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
-        if (__ballot_sync(0xffffffffu, f[0] != 0.f || f[1] != 0.f) && leader) nz[c * s + (s - 1 - pos)] = 1;
       }
-    }
-    if (want_sum) {
-      float f[2];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        int dg;
-        if (pos == s) {
-          dg = (fld[q][2] >= half ? fld[q][2] - full : fld[q][2]) + cbal_s[q];
-        } else {
-          dg = fld[q][2] + cbal_s[q];
-          cbal_s[q] = dg >= half;
-          if (dg >= half) dg -= full;
-        }
-        f[q] = (float)dg;
+        if (st == 0) cy[q][0] = c[q];
+        else if (st == 1) cy[q][1] = c[q];
+        else cy[q][2] = c[q];
       }
-      if (in_range) out[(int64_t)(2 * s + (s - pos)) * pstride2] = __floats2bfloat162_rn(f[0], f[1]);
-      if (__ballot_sync(0xffffffffu, f[0] != 0.f || f[1] != 0.f) && leader) nz[2 * s + (s - pos)] = 1;
+      // planes: re  s-1-pos,  im  2s-1-pos,  sums  3s-pos
+      const int64_t plane0 = st == 0 ? s - 1 : st == 1 ? 2 * s - 1 : 3 * s;
+      uint32_t nzmask = 0;
+      if (32 * blk + 31 < T - 1) {
+        emit_block<W, false>(y[0], y[1], 0u, 0u, blk, T, out + plane0 * pstride2, pstride2, in_range, nzmask);
+      } else {
+        // The block holds the top digit, so every bit of |X| lies in it (w T <= 32 w (blk + 1))
+        // and the word after it is the sign extension of X'' (-1 per negative input) plus the
+        // carry: it gives the top digit's sign bit when that digit ends the block.
+        uint32_t nxt[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+          nxt[q] = c[q] - (st == 0 ? neg[q][0] : st == 1 ? neg[q][1] : neg[q][0] + neg[q][1]);
+        emit_block<W, true>(y[0], y[1], nxt[0], nxt[1], blk, T, out + plane0 * pstride2, pstride2, in_range, nzmask);
+      }
+      const uint32_t any = __reduce_or_sync(0xffffffffu, nzmask);
+      if ((threadIdx.x & 31) == 0 && any) atomicOr(&nzbits[st][blk], any);
     }
   }
-}
-
-// Digit planes of one operand; plane_nz[x] is set when plane x has a nonzero digit
-// (the group table then skips the slice pairs of all-zero planes), and
-// plane_nz[nplanes + c] when component c (re, im) has a nonzero value.
-__global__ void k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s,
-                            int wd, int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits,
-                            int32_t *plane_nz) {
-  __shared__ int nz[3 * kMaxSlices + 1 + 2];
-  const int nflags = 2 * s + (want_sum ? s + 1 : 0) + 2;
-  for (int x = threadIdx.x; x < nflags; x += blockDim.x) nz[x] = 0;
   __syncthreads();
-  const int64_t l0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-  const int64_t line = blockIdx.y;
-  // kpad is even: l0 + 1 < kpad; out-of-range threads still take part in the warp votes
-  oz_digits_pair(X, side, lines, k, kpad, L, s, wd, want_sum, E, lossy, digits, l0, line, l0 < kpad && line < lines,
-                 nz);
-  __syncthreads();
-  for (int x = threadIdx.x; x < nflags; x += blockDim.x)
-    if (nz[x]) atomicOr(plane_nz + x, 1);
+  // plane flags: digit position pos of stream st is plane plane0(st) - pos
+  const int ndig[3] = {s, s, want_sum ? Ts : 0};
+  for (int st = 0; st < 3; ++st)
+    for (int pos = threadIdx.x; pos < ndig[st]; pos += blockDim.x)
+      if ((nzbits[st][pos >> 5] >> (pos & 31)) & 1u) {   // block pos / 32, digit pos % 32
+        const int plane = st == 0 ? s - 1 - pos : st == 1 ? 2 * s - 1 - pos : 3 * s - pos;
+        atomicOr(plane_nz + plane, 1);
+      }
+  const int nplanes = 2 * s + (want_sum ? Ts : 0);
+  if (threadIdx.x < 2 && nzcomp[threadIdx.x]) atomicOr(plane_nz + nplanes + threadIdx.x, 1);
 }
 
 // Plain path: X = floor(|a| 2^(64 Lp - E)) as Lp limbs (Lp = L + 1), sign kept apart.
@@ -397,7 +431,10 @@ void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int6
                       int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, int32_t *plane_nz,
                       cudaStream_t st) {
   dim3 g((unsigned)((kpad / 2 + 127) / 128), (unsigned)lines);
-  k_oz_digits<<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, wd, want_sum, E, lossy, digits, plane_nz);
+  if (wd == 9)
+    k_oz_digits<9><<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits, plane_nz);
+  else
+    k_oz_digits<8><<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits, plane_nz);
 }
 
 void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, int L, int D, int DP, int W,

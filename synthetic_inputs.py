@@ -224,7 +224,9 @@ def config_inputs(name: str):
         "c0_plain_32_p128": (32, 32, 32, 128, "uniform", 0),
         # Ozaki 4M, 256^3, p = 256, uniform [-1, 1)
         "c1_ozaki_256_p256": (256, 256, 256, 256, "uniform", 1),
-        # Ozaki 3M / 4M / plain, n in {1024, 2048}, p in {512, 1024}, u * 2^e
+        # Ozaki 3M / 4M / plain, n in {1024, 2048}, p in {256, 512, 1024}, u * 2^e
+        "c2_1024_p256": (1024, 1024, 1024, 256, "uniform_exp", 2),
+        "c2_2048_p256": (2048, 2048, 2048, 256, "uniform_exp", 2),
         "c2_1024_p512": (1024, 1024, 1024, 512, "uniform_exp", 2),
         "c2_1024_p1024": (1024, 1024, 1024, 1024, "uniform_exp", 2),
         "c2_2048_p512": (2048, 2048, 2048, 512, "uniform_exp", 2),
@@ -238,3 +240,23 @@ def make_config(name: str):
     A = random_matrix(m, k, p, SEED_BASE + idx, dist)
     B = random_matrix(k, n, p, SEED_BASE + idx + 1000, dist)
     return A, B, p
+
+
+def batch_specs(count: int = 64, seed: int = SEED_BASE + 3):
+    """The batched workload: (m, k, n, p) of `count` problems, m, n, k log-uniform in
+    [64, 1024], p drawn from {256, 512, 1024}."""
+    rng = np.random.default_rng(seed)
+    mnk = np.exp(rng.uniform(np.log(64), np.log(1024), size=(count, 3))).astype(int)
+    ps = rng.choice([256, 512, 1024], size=count)
+    return [(int(m), int(k), int(n), int(p)) for (m, n, k), p in zip(mnk, ps)]
+
+
+def batch_problems(specs):
+    """The seeded operands (host side) of the batched workload: [(A, B, p)]."""
+    out = []
+    for x, (m, k, n, p) in enumerate(specs):
+        A = random_matrix(m, k, p, SEED_BASE + 3000 + 2 * x, "uniform")
+        B = random_matrix(k, n, p, SEED_BASE + 3001 + 2 * x, "uniform")
+        out.append((A, B, p))
+    return out
+

@@ -75,3 +75,29 @@ def take_entries(C, entries):
     """(sign[2, N], exp[2, N], limb[2, L, N]) of listed (i, j) entries."""
     ii, jj = entries[:, 0], entries[:, 1]
     return C.sign[:, ii, jj], C.exp[:, ii, jj], C.limb[:, :, ii, jj]
+
+
+def ws_accumulators(ws, pl, m, n):
+    """Exact accumulators dumped by the accumulation stage: object array [2, m, n] of Python ints."""
+    import torch
+    ns = pl["acc_slots"] + 1
+    off = pl["off_acc_dump"]
+    raw = ws.tensor[off: off + 4 * 2 * m * n * ns].view(torch.int32).cpu().numpy().view(np.uint32)
+    raw = raw.reshape(m, n, 2, ns)
+    out = np.zeros((2, m, n), dtype=object)
+    for i in range(m):
+        for j in range(n):
+            for c in range(2):
+                w = raw[i, j, c]
+                v = int.from_bytes(w[:-1].astype("<u4").tobytes(), "little")
+                out[c, i, j] = -v if w[-1] else v
+    return out
+
+
+def sampled_entries(m, n, count, seed):
+    """`count` random output entries, the first and last one always included."""
+    rng = np.random.default_rng(seed)
+    ent = np.stack([rng.integers(0, m, count), rng.integers(0, n, count)], axis=1)
+    ent[0] = (0, 0)
+    ent[1] = (m - 1, n - 1)
+    return ent

@@ -127,3 +127,32 @@ def test_autotuner_picks_a_working_configuration():
     torch.cuda.synchronize()
     for (dA, dB, dC, p, method, algo), (A, B) in zip(probs, host):
         assert gu.same(_result(dC, p), c_oracle.rounded_cgemm_matrix(A, B, p))
+
+
+def test_batched_workload_of_64_problems_sampled():
+    """The benchmark's batched workload itself (64 Ozaki-3M problems, m, n, k log-uniform
+    in [64, 1024], p in {256, 512, 1024}) under every configuration the autotuner may
+    pick: sampled entries of every problem equal the exact C oracle bit for bit."""
+    import torch
+    from paper_2307_06072_gb300.autotune import CANDIDATES
+    M = gu.mp()
+    host = si.batch_problems(si.batch_specs())
+    probs, ref, ents = [], [], []
+    for x, (A, B, p) in enumerate(host):
+        probs.append((M.DeviceMatrix.from_mpc(A), M.DeviceMatrix.from_mpc(B),
+                      M.DeviceMatrix.empty(A.rows, B.cols, p), p, "3m", "ozaki"))
+        ent = gu.sampled_entries(A.rows, B.cols, 8, 900 + x)
+        ents.append(ent)
+        ref.append(c_oracle.rounded_cgemm(A, B, p, ent))
+    for cand in CANDIDATES:
+        for (_, _, dC, _, _, _) in probs:
+            dC.sign.fill_(0xFF)   # stale values must not survive
+        ws = M.mpcgemm_batched(probs, params=cand)
+        torch.cuda.synchronize()
+        total, offs = M.batched_workspace(probs, cand)
+        for x, (dA, dB, dC, p, method, algo) in enumerate(probs):
+            gs, ge, gl = gu.take_entries(_result(dC, p), ents[x])
+            sg, ex, li = ref[x]
+            assert np.array_equal(gs, sg) and np.array_equal(ge, ex) and np.array_equal(gl, li), (cand, x)
+            st = M.read_status(ws, offset=offs[x])
+            assert st["device_timeout"] == 0 and st["uncertified"] == 0, (cand, x)
