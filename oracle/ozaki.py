@@ -35,6 +35,25 @@ Algorithm 2 of the paper (Kouya, Sec. III-C) in this library's reading:
    p-bit grid lies within B of Acc, RN_p(Acc) == RN_p(T) ("certified");
    otherwise the entry is recomputed exactly (O1) -- so the final output is
    always RN_p(T).
+
+Per-part split (``split="per_part"``, 4M).  Alg. 2 splits every real matrix
+(Re A, Im A, Re B, Im B) on its own: mu, the row maximum of that part, is taken
+again before every slice, and tau follows it.  On the fixed per-row grid of
+step 2 a re-measured maximum only decides at which grid position the next
+nonzero digit of that part starts.  The variant therefore gives part P a digit
+offset z_P: the number of leading digit positions that are zero in every line
+of P, z_P = min over lines of floor((E_line - E^P_line) / w) (E^P_line the
+largest exponent of part P in the line; an all-zero part gets Z_CAP).  Part P
+is cut on the grid 2^(E - (w-1) - w(z_P + t)), t < s: X_P = sign floor(|v|
+2^(w(s + z_P) - 1 - E)) in s digits at positions z_P .. z_P + s - 1.  Every
+output component c takes its own cut level Q_c = Q + z_c, z_c the smallest
+z_a + z_b over the products entering c, so a part that is smaller by 2^-D
+everywhere keeps its full s digits instead of losing about D/w of them to
+leading zeros, and the products of a component far below its magnitude keep
+only the pairs that reach its precision (the paper's future-work remark that
+the number of divisions should follow the magnitudes of the real and imaginary
+parts, Sec. V, item 3).  Accumulation, bounds and certification are those of
+the default path with the component's own Q_c.
 """
 from __future__ import annotations
 
@@ -47,6 +66,7 @@ import numpy as np
 from . import exact as o1
 
 DIGIT_BITS = 9                  # default digit width w (8 is the other supported width)
+Z_CAP = 2048                    # per-part split: offset of an all-zero part, and the cap of z
 INT32_MAX = 2 ** 31 - 1
 
 
@@ -86,10 +106,23 @@ class Params:
     method: str
     guard: int = DEFAULT_GUARD
     w: int = DIGIT_BITS          # bits per digit
+    split: str = "common"        # "common" (one exponent per line) or "per_part"
+    Qc: dict = None              # per-part split: cut level per component ('re', 'im')
 
     @property
     def products(self):
         return PRODUCTS_4M if self.method == "4m" else PRODUCTS_3M
+
+    def q_comp(self, comp: str) -> int:
+        """Cut level of output component `comp`."""
+        return self.Qc[comp] if self.Qc else self.Q
+
+    def q_prod(self, prod: str) -> int:
+        """Cut level of the component a real product enters (4M: one component each;
+        3M: the common Q)."""
+        if not self.Qc:
+            return self.Q
+        return self.Qc["re" if prod in ("rr", "ii") else "im"]
 
 
 def make_params(p: int, k: int, method: str = "4m", guard: int = DEFAULT_GUARD,
@@ -210,10 +243,25 @@ def balanced_digits_array(X, nd: int, w: int = DIGIT_BITS):
     return out
 
 
-def split_operand(mat, s: int, side: str, method: str, w: int = DIGIT_BITS) -> Split:
+def part_exponents(mat, c: int, by: str):
+    """Largest exponent of component c per row ('rows') or column ('cols'); None if zero."""
+    nz = mantissas(mat, c) != 0
+    e = np.where(nz, mat.exp[c].astype(np.int64), np.iinfo(np.int64).min)
+    emax = e.max(axis=1 if by == "rows" else 0)
+    return [None if v == np.iinfo(np.int64).min else int(v) for v in emax]
+
+
+def part_offset(E: list, EP: list, w: int) -> int:
+    """z_P: leading digit positions of part P that are zero in every line (Z_CAP if P is zero)."""
+    zs = [(e - ep) // w for e, ep in zip(E, EP) if ep is not None]
+    return min(min(zs), Z_CAP) if zs else Z_CAP
+
+
+def split_operand(mat, s: int, side: str, method: str, w: int = DIGIT_BITS, split: str = "common") -> Split:
     """Alg. 2's split for A (side='A', lines = rows) or B (side='B', lines = columns).
 
-    For B the digit planes are stored K-major: digits[.][u][j][l].
+    For B the digit planes are stored K-major: digits[.][u][j][l].  With
+    split="per_part" (4M only) each part has its own digit offset (module notes).
     """
     by = "rows" if side == "A" else "cols"
     E = row_exponents(mat, by)
@@ -225,15 +273,22 @@ def split_operand(mat, s: int, side: str, method: str, w: int = DIGIT_BITS) -> S
         Nre, Nim, xre, xim = Nre.T, Nim.T, xre.T, xim.T
     Eline = np.array([0 if e is None else e for e in E], np.int64)[:, None]
     zero_line = np.array([e is None for e in E])[:, None]
-    Xr, okr = fixed_point_array(Nre, xre, Eline, s, w)
-    Xi, oki = fixed_point_array(Nim, xim, Eline, s, w)
+    z = {"re": 0, "im": 0}
+    if split == "per_part":
+        if method != "4m":
+            raise ValueError("the per-part split is defined for the 4M method")
+        for c, which in enumerate(("re", "im")):
+            z[which] = part_offset(E, part_exponents(mat, c, by), w)
+    # part P: s digits at positions z_P .. z_P + s - 1, i.e. the grid of s + z_P digits
+    Xr, okr = fixed_point_array(Nre, xre, Eline, s + z["re"], w)
+    Xi, oki = fixed_point_array(Nim, xim, Eline, s + z["im"], w)
     Xr = np.where(zero_line, 0, Xr)
     Xi = np.where(zero_line, 0, Xi)
     ok = (okr & oki) | zero_line
     sp = Split(E=E, lossless=[bool(v) for v in ok.all(axis=1)])
     sp.digits["re"] = balanced_digits_array(Xr, s, w)
     sp.digits["im"] = balanced_digits_array(Xi, s, w)
-    sp.first_pos["re"] = sp.first_pos["im"] = 0
+    sp.first_pos["re"], sp.first_pos["im"] = z["re"], z["im"]
     if method == "3m":
         sp.digits["sum"] = balanced_digits_array(Xr + Xi, s + 1, w)
         sp.first_pos["sum"] = -1
@@ -341,7 +396,7 @@ def group_sums(spA: Split, spB: Split, prod: str, prm: Params):
     DA, DB = spA.digits[wa], spB.digits[wb]
     fa, fb = spA.first_pos[wa], spB.first_pos[wb]
     tA, tB = positions(spA, wa, prm.s), positions(spB, wb, prm.s)
-    gs = groups_for(tA, tB, prm.Q, prm.gmax)
+    gs = groups_for(tA, tB, prm.q_prod(prod), prm.gmax)
     out = []
     for g in gs:
         ts = range(g.t0, g.t0 + g.count)
@@ -398,7 +453,10 @@ def bound_exponent(prm: Params) -> int:
     """beta: the bound is b * 2**beta with beta = max(0, 2w - 1 + w(Q - s)).
 
     One unit of the split grid, 2**(E-(ws-1)), times |b| < 2**F, in Acc units
-    2**(E+F-(2w-2)-wQ), is 2**(2w-1+w(Q-s))."""
+    2**(E+F-(2w-2)-wQ), is 2**(2w-1+w(Q-s)).  Per-part split: a part with offset z_a
+    has the unit 2**(E-(w(s+z_a)-1)) and the other factor |b| < 2**(F-w z_b), so in the
+    units 2**(E+F-(2w-2)-w Q_c) of its component (Q_c = Q + z_c, z_c <= z_a + z_b) the
+    same term is at most 2**(2w-1+w(Q-s)): beta is unchanged."""
     return max(0, 2 * prm.w - 1 + prm.w * (prm.Q - prm.s))
 
 
@@ -441,13 +499,13 @@ def product_bound(prm: Params, spA: Split, spB: Split, pr: str):
     have a nonzero value somewhere: otherwise the product and its digit product
     are both exactly zero.  Cached on the splits (it depends on them only).
     """
-    key = ("bound", pr, prm.Q, prm.k, prm.s, prm.w)
+    key = ("bound", pr, prm.q_prod(pr), prm.k, prm.s, prm.w)
     cache = spA.__dict__.setdefault("_bound_cache", {})
     hit = cache.get(key)
     if hit is None or hit[0] is not spB:        # keyed on the very B split (kept alive here)
         wa, wb = PRODUCT_OPERANDS[pr]
         tA, tB = positions(spA, wa, prm.s), positions(spB, wb, prm.s)
-        bd = drop_bound(tA, tB, prm.Q, prm.k, tuple(spA.live[wa]), tuple(spB.live[wb]), prm.w)
+        bd = drop_bound(tA, tB, prm.q_prod(pr), prm.k, tuple(spA.live[wa]), tuple(spB.live[wb]), prm.w)
         hit = (spB, (bd, value_nonzero(spA, wa) and value_nonzero(spB, wb)))
         cache[key] = hit
     return hit[1]
@@ -484,23 +542,34 @@ class OzakiResult:
     C: object             # MPCMatrix, final rounded output (== O1)
 
 
+def component_offsets(spA: Split, spB: Split) -> dict:
+    """Per-part split: z_c = min over the 4M products of component c of z_a + z_b."""
+    za, zb = spA.first_pos, spB.first_pos
+    return {"re": min(za["re"] + zb["re"], za["im"] + zb["im"]),
+            "im": min(za["re"] + zb["im"], za["im"] + zb["re"])}
+
+
 def ozaki_cgemm(A, B, p: int, method: str = "4m", guard: int = DEFAULT_GUARD,
                 s: int | None = None, Q: int | None = None, fallback=None, max_group: int = 0,
-                w: int | None = None) -> OzakiResult:
+                w: int | None = None, split: str = "common") -> OzakiResult:
     """Emulate the whole Ozaki complex GEMM; ``fallback(i, j) -> (re, im)`` exact values.
 
     Without ``fallback`` the exact O1 triple loop is used for uncertified entries.
+    ``split``: "common" (one exponent per line for both parts) or "per_part" (4M).
     """
     m, k, n = A.rows, A.cols, B.cols
     prm = make_params(p, k, method, guard, s, Q, max_group, w)
     w = prm.w
-    spA = split_operand(A, prm.s, "A", method, w)
-    spB = split_operand(B, prm.s, "B", method, w)
+    spA = split_operand(A, prm.s, "A", method, w, split)
+    spB = split_operand(B, prm.s, "B", method, w, split)
+    if split == "per_part":
+        prm.split = split
+        prm.Qc = {c: prm.Q + z for c, z in component_offsets(spA, spB).items()}
     groups, sums, acc_p = {}, {}, {}
     for pr in prm.products:
         gs, gsum = group_sums(spA, spB, pr, prm)
         groups[pr], sums[pr] = gs, gsum
-        acc_p[pr] = accumulate(gs, gsum, prm.Q, w) if gs else np.zeros((m, n), dtype=object)
+        acc_p[pr] = accumulate(gs, gsum, prm.q_prod(pr), w) if gs else np.zeros((m, n), dtype=object)
     acc_re = acc_p["rr"] - acc_p["ii"]
     acc_im = (acc_p["ri"] + acc_p["ir"]) if method == "4m" else (acc_p["ss"] - acc_p["rr"] - acc_p["ii"])
     scale = np.zeros((m, n), dtype=object)
@@ -511,9 +580,9 @@ def ozaki_cgemm(A, B, p: int, method: str = "4m", guard: int = DEFAULT_GUARD,
         for j in range(n):
             Ei = spA.E[i] if spA.E[i] is not None else 0
             Fj = spB.E[j] if spB.E[j] is not None else 0
-            x = Ei + Fj - prod_log2(prm.w) - prm.w * prm.Q
-            scale[i, j] = x
+            scale[i, j] = Ei + Fj - prod_log2(prm.w) - prm.w * prm.Q
             for c, (comp, acc) in enumerate((("re", acc_re), ("im", acc_im))):
+                x = Ei + Fj - prod_log2(prm.w) - prm.w * prm.q_comp(comp)
                 b, beta = entry_bound(prm, spA, spB, i, j, comp)
                 a = int(acc[i, j])
                 if certify(a, b, beta, p):
@@ -549,8 +618,8 @@ def exact_accumulators(A, B, spA: Split, spB: Split, prm: Params):
         for j in range(n):
             Ei = spA.E[i] if spA.E[i] is not None else 0
             Fj = spB.E[j] if spB.E[j] is not None else 0
-            x = Ei + Fj - prod_log2(prm.w) - prm.w * prm.Q
             for comp, T in (("re", re), ("im", im)):
+                x = Ei + Fj - prod_log2(prm.w) - prm.w * prm.q_comp(comp)
                 out[comp][i, j] = o1.to_fraction(T[i][j]) / (Fraction(2) ** x)
     return out
 
