@@ -73,6 +73,9 @@ extern "C" {
 /* ---- algorithm selection --------------------------------------------- */
 enum { MPC_4M = 0, MPC_3M = 1 };          /* Eq. (4m_way) / Eq. (3m_way) */
 enum { MPC_PLAIN = 0, MPC_OZAKI = 1 };    /* Eq. (simple_triple_loop) / Alg. 2 */
+/* Split of the Ozaki path: one exponent per row / column for both parts (default), or
+ * the per-part split of Alg. 2 (4M only; see mpc_oz_params.split). */
+enum { MPC_SPLIT_COMMON = 0, MPC_SPLIT_PER_PART = 1 };
 /* Slice-GEMM kernels (value 3 is not used and is rejected). */
 enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2, MPC_KERNEL_TCGEN05_2SM = 4 };
 
@@ -126,6 +129,20 @@ typedef struct mpc_mat {
  *               imaginary; its value is Acc 2^(E_i + F_j - (2w - 2) - w Q).
  *               Rows of A or columns of B that are all zero are not written.
  *               For stage checks; leave it 0 otherwise.
+ *   split       MPC_SPLIT_COMMON (0): one exponent per row of A / column of B for
+ *               both parts, s digits each.  MPC_SPLIT_PER_PART (1, 4M only, else
+ *               MPC_EINVAL): Alg. 2 cuts every real part (Re A, Im A, Re B, Im B)
+ *               on its own; here part P gets a digit offset z_P, the number of
+ *               leading digit positions that are zero in every row (column) of P,
+ *               measured on the device, and its s digits sit at positions
+ *               z_P .. z_P + s - 1 of the row's grid; each output component c is
+ *               cut at level Q_c = Q + z_c (z_c = min over its products of
+ *               z_a + z_b, Sec. V item 3: divisions that follow the magnitudes of
+ *               the real and imaginary parts).  When one part is smaller than the
+ *               other by 2^-D everywhere it keeps all its s digits (the default
+ *               loses about D/w of them to leading zeros, and its rounding then
+ *               needs the exact fallback); when no part is smaller it is the
+ *               default split.  The result is the same correctly rounded product.
  */
 typedef struct mpc_oz_params {
     int32_t guard_bits;
@@ -136,6 +153,8 @@ typedef struct mpc_oz_params {
     int32_t digit_bits;
     int32_t wait_limit_cycles;
     int32_t dump_accumulators;
+    int32_t split;
+    int32_t reserved[3];
 } mpc_oz_params;
 
 /*
@@ -166,6 +185,8 @@ typedef struct mpc_plan {
     int32_t launches;             /* kernel launches one call makes */
     int32_t digit_bits;           /* Ozaki: bits per digit w (8 or 9); plain: 28 */
     uint64_t off_group_order;     /* groups ordered by descending level */
+    int32_t split;                /* MPC_SPLIT_* */
+    int32_t reserved_plan;
 } mpc_plan;
 
 /*

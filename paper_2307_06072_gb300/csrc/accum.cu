@@ -2,14 +2,15 @@
 // Eqs. (4m_way) / (3m_way)), and the exact fallback.
 //
 // k_oz_accum: one thread per output element (i, j).  The group sums of every
-// real product are shifted by w (Q - q) and added, with the sign the complex
-// formula gives them, into two exact accumulators (Re, Im):
+// real product are shifted by w (Q_c - q) and added, with the sign the complex
+// formula gives them, into two exact accumulators (Re, Im; Q_c = Q unless the
+// per-part split gives component c its own cut level):
 //     4M: Re = rr - ii,        Im = ri + ir
 //     3M: Re = rr - ii,        Im = ss - rr - ii
 // Groups are visited in order of increasing shift; the groups of one level are
 // summed in int64, and each accumulator takes one level sum per step, keeping a
 // running carry in registers and emitting finished 32-bit words.
-// Value = Acc * 2^(E_i + F_j - (2w - 2) - wQ).
+// Value = Acc * 2^(E_i + F_j - (2w - 2) - w Q_c).
 // The result is RN_p(Acc) when no rounding midpoint lies within the error
 // bound b * 2^beta of Acc (then it equals RN_p of the exact product);
 // otherwise the component is queued for k_exact_fallback.
@@ -125,7 +126,8 @@ __device__ __forceinline__ void finish_component(const AccumArgs &a, const OutVi
   if (N == 0 && b == 0) {
     store_zero(a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
   } else if (N > 0 && certified(mag, a.nslot, N, a.p, b, a.bound_shift)) {
-    const int64_t scale = (int64_t)Ei + (int64_t)Fj - prod_log2(a.w) - (int64_t)a.w * a.Q;
+    const int64_t Qc = (int64_t)a.bounds[8 + c];   // the component's cut level
+    const int64_t scale = (int64_t)Ei + (int64_t)Fj - prod_log2(a.w) - (int64_t)a.w * Qc;
     if (!round_store(mag, a.nslot, N, neg, scale, a.p, a.L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o,
                      C.plane)) {
       status_set(a.status, kStErange, 1);
@@ -228,10 +230,14 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
         const int32_t v = stage[buf][u][tid];
         sum0 = mad_wide(v, t.z, sum0);
         sum1 = mad_wide(v, t.w, sum1);
-        if (t.y >= 0) {   // the last group of a level
-          acc[0].add(words[0], sum0, t.y, a.w);
-          acc[1].add(words[1], sum1, t.y, a.w);
-          sum0 = sum1 = 0;
+        const int sh0 = (int16_t)(t.y & 0xFFFF), sh1 = t.y >> 16;   // a component's level ends here
+        if (sh0 >= 0) {
+          acc[0].add(words[0], sum0, sh0, a.w);
+          sum0 = 0;
+        }
+        if (sh1 >= 0) {
+          acc[1].add(words[1], sum1, sh1, a.w);
+          sum1 = 0;
         }
       }
     }

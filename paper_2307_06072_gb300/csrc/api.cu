@@ -62,6 +62,9 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
       out->kernel != MPC_KERNEL_TCGEN05_2SM)
     return MPC_EINVAL;
   if (prm && prm->wait_limit_cycles < 0) return MPC_EINVAL;
+  P.split = prm ? prm->split : MPC_SPLIT_COMMON;
+  if (P.split != MPC_SPLIT_COMMON && P.split != MPC_SPLIT_PER_PART) return MPC_EINVAL;
+  if (P.split == MPC_SPLIT_PER_PART && algo == MPC_OZAKI && method != MPC_4M) return MPC_EINVAL;
   out->wait_limit = prm ? prm->wait_limit_cycles : 0;
   uint64_t off = 0;
   P.off_status = off;
@@ -198,7 +201,8 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
     off = align256(off + (uint64_t)2 * m * n * (P.acc_slots + 1) * 4);
   }
   P.ws_bytes = off;
-  P.launches = 9;     // init, row max, column max, group table, 2 x digits, slice GEMM, accumulate, fallback
+  // init, row max, column max, group table, 2 x digits, slice GEMM, accumulate, fallback (+ 2 part offsets)
+  P.launches = P.split == MPC_SPLIT_PER_PART ? 11 : 9;
   return MPC_OK;
 }
 
@@ -310,10 +314,13 @@ void call_pre(Call &c, cudaStream_t st) {
                         (int32_t *)(c.ws + P.off_digits_b), st);
   } else {
     const int want_sum = P.method == MPC_3M;
+    const bool per_part = P.split == MPC_SPLIT_PER_PART;
+    if (per_part) launch_part_offsets(c.A, c.B, c.m, c.n, c.k, L, P.digit_bits, c.E, c.F, c.status, st);
     launch_oz_digits(c.A, 0, c.m, c.k, P.kpad, L, P.s, P.digit_bits, want_sum, c.E, c.lossyA,
-                     (__nv_bfloat16 *)(c.ws + P.off_digits_a), plane_nz, st);
+                     (__nv_bfloat16 *)(c.ws + P.off_digits_a), plane_nz, per_part ? c.status + kStPartZ : nullptr, st);
     launch_oz_digits(c.B, 1, c.n, c.k, P.kpad, L, P.s, P.digit_bits, want_sum, c.F, c.lossyB,
-                     (__nv_bfloat16 *)(c.ws + P.off_digits_b), plane_nz + flagsA, st);
+                     (__nv_bfloat16 *)(c.ws + P.off_digits_b), plane_nz + flagsA,
+                     per_part ? c.status + kStPartZ + 2 : nullptr, st);
     GroupTableArgs ga{};
     for (int x = 0; x < 4; ++x) ga.prod[x] = c.pl.prod[x];
     ga.n_products = P.n_products;
@@ -331,6 +338,7 @@ void call_pre(Call &c, cudaStream_t st) {
     ga.order = (int32_t *)(c.ws + P.off_group_order);
     ga.bounds = (uint64_t *)(c.ws + P.off_group_order + bounds_offset(P.n_groups_total, P.planes_A, P.planes_B));
     ga.terms = (AccTerm *)(c.ws + P.off_group_order + terms_offset(P.n_groups_total, P.planes_A, P.planes_B));
+    ga.zwords = per_part ? c.status + kStPartZ : nullptr;
     launch_group_table(ga, st);
   }
 }

@@ -31,8 +31,12 @@ __host__ __device__ constexpr int plain_limbs(int D) { return (56 * D + 18 + 63)
 constexpr int kStatusWords = 16;
 constexpr int kDefaultGuard = 40;
 
-// status block (int32 words at the start of the workspace)
-enum StatusWord { kStErange = 0, kStFallbackCount = 1, kStFallbackOverflow = 2, kStUncertified = 3, kStTimeout = 4 };
+// status block (int32 words at the start of the workspace); words 10..13 hold the
+// per-part split's offsets as kZCap - z (A re, A im, B re, B im; maxima, so 0 = zero part)
+enum StatusWord { kStErange = 0, kStFallbackCount = 1, kStFallbackOverflow = 2, kStUncertified = 3, kStTimeout = 4,
+                  kStPartZ = 10 };
+// per-part split: the offset of an all-zero part, and the cap of every offset
+constexpr int kZCap = 2048;
 
 // Digit sets of one operand: planes [0, s) real part, [s, 2s) imaginary part,
 // [2s, 3s+1) the 3M sums (positions -1 .. s-1).

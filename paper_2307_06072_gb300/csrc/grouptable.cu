@@ -24,14 +24,16 @@ __device__ __forceinline__ void product_kinds(int method, int prod, int &ka, int
   }
 }
 
+__device__ void serial_passes(const GroupTableArgs &a, const int32_t *s_qc, const uint64_t *s_bd, int *s_start);
+
 // Per product (one warp each): the group table, levels ascending; then every
 // group loses the pairs at its two ends whose A or B digit plane is all zero
 // (their products are exactly zero), so it never splits and the table keeps its
 // size; a group of zero pairs only keeps its place (count 0: no unit, no term).
-// The warp also counts the dropped pairs (levels above Q) whose planes are both
-// nonzero.  Thread 0 then merges the products' groups into the accumulation order
-// (descending level, i.e. ascending shift), writes the slice GEMM's unit schedule
-// and the call's error bounds:
+// The warp also counts the dropped pairs (levels above the product's cut level)
+// whose planes are both nonzero.  Thread 0 then merges the products' groups into
+// the accumulation order (descending level, i.e. ascending shift), writes the slice
+// GEMM's unit schedule and the call's error bounds:
 //   drop[c]    = sum over the products of component c of ceil(B_prod / 2^beta),
 //                B_prod = k (2^(w-2) n_{Q+1} + ceil(max_{j>=2} n_{Q+j} / 3)) over live pairs;
 //   lossy_a[c] = sum of the products' truncation factors (4 for the 3M sums, else 1),
@@ -42,17 +44,48 @@ __device__ __forceinline__ void product_kinds(int method, int prod, int &ka, int
 // zero[c] (bounds[6 + c]) tells the accumulation to add nothing into it: a product
 // needed only there (the 3M sums for real inputs) was emptied.  Finally all threads
 // write the accumulation's term table (one entry per group, in accumulation order).
-__device__ void serial_passes(const GroupTableArgs &a, const int32_t *s_qc, const uint64_t *s_bd, int *s_start);
-
+//
+// Per-part split (zwords set, 4M): the digit positions of product x's operands start
+// at the parts' offsets z (read from the status words), component c is cut at
+// Q_c = Q + z_c, z_c = min over its products of z_a + z_b, and the product's pairs are
+// t + u <= Q_c.  Levels are true positions while the order, the bounds and the terms
+// are formed; the table entries are then rewritten relative to the operands' first
+// digit plane (t0 - z_a, q - z_a - z_b), which is what the slice-GEMM kernels index.
 __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
   __shared__ uint64_t s_bd[4];
   __shared__ int32_t s_qc[kMaxGroupsTotal];   // per group: (q + 8) << 16 | count, for the serial passes below
   __shared__ int s_start[kMaxSlices + 3];
+  __shared__ int s_pos[4][2];                 // per product: true first digit positions of A and B
+  __shared__ int s_qp[4];                     // per product: its cut level
+  __shared__ int s_qcomp[2];                  // per component: its cut level Q_c
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    int zc[2] = {1 << 30, 1 << 30};
+    for (int x = 0; x < a.n_products; ++x) {
+      int pa = a.prod[x].a_pos0, pb = a.prod[x].b_pos0;
+      if (a.zwords) {   // 4M: operands re (kind 0) or im (kind 1) of A and B
+        int ka, kb;
+        product_kinds(a.method, x, ka, kb);
+        pa = kZCap - a.zwords[ka];
+        pb = kZCap - a.zwords[2 + kb];
+        for (int c = 0; c < 2; ++c)
+          if (product_sign(a.method, c, x) != 0 && pa + pb < zc[c]) zc[c] = pa + pb;
+      }
+      s_pos[x][0] = pa;
+      s_pos[x][1] = pb;
+    }
+    for (int c = 0; c < 2; ++c) s_qcomp[c] = a.Q + (a.zwords ? zc[c] : 0);
+    for (int x = 0; x < a.n_products; ++x)   // 4M: every product enters one component
+      s_qp[x] = a.zwords ? s_qcomp[product_sign(a.method, 0, x) != 0 ? 0 : 1] : a.Q;
+  }
+  __syncthreads();
   if (warp < a.n_products) {
-    const ProductDesc pd = a.prod[warp];
+    ProductDesc pd = a.prod[warp];
+    pd.a_pos0 = s_pos[warp][0];
+    pd.b_pos0 = s_pos[warp][1];
+    const int Qp = s_qp[warp];
     if (lane == 0)
-      build_groups(warp, pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, a.Q, a.gmax, a.table + pd.group0,
+      build_groups(warp, pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, Qp, a.gmax, a.table + pd.group0,
                    pd.n_groups);
     __syncwarp();
     // a product that enters only components of A B that vanish identically is not needed
@@ -64,8 +97,13 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
     auto live = [&](int t, int u) {
       return needed && a.flagsA[pd.a_plane0 + t - pd.a_pos0] != 0 && a.flagsB[pd.b_plane0 + u - pd.b_pos0] != 0;
     };
+    const int ng = build_groups(warp, pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, Qp, a.gmax, nullptr, 0);
     for (int e = pd.group0 + lane; e < pd.group0 + pd.n_groups; e += 32) {
       GroupEntry g = a.table[e];
+      if (e >= pd.group0 + ng) {   // beyond the product's cut: an empty group at its top level (lists stay ascending)
+        const int qtop = min(Qp, pd.a_pos0 + pd.a_npos - 1 + pd.b_pos0 + pd.b_npos - 1);
+        g = GroupEntry{warp, qtop, pd.a_pos0, 0};
+      }
       while (g.count > 0 && !live(g.t0, g.q - g.t0)) {
         ++g.t0;
         --g.count;
@@ -73,16 +111,16 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
       while (g.count > 0 && !live(g.t0 + g.count - 1, g.q - (g.t0 + g.count - 1))) --g.count;
       a.table[e] = g;
     }
-    // live dropped pairs per level above Q
+    // live dropped pairs per level above the cut
     const int qmax = pd.a_pos0 + pd.a_npos - 1 + pd.b_pos0 + pd.b_npos - 1;
     uint64_t n1 = 0, nmax = 0;
-    for (int q = a.Q + 1; q <= qmax; ++q) {
+    for (int q = Qp + 1; q <= qmax; ++q) {
       const int lo = max(pd.a_pos0, q - (pd.b_pos0 + pd.b_npos - 1));
       const int hi = min(pd.a_pos0 + pd.a_npos - 1, q - pd.b_pos0);
       unsigned cnt = 0;
       for (int t = lo + lane; t <= hi; t += 32) cnt += live(t, q - t) ? 1u : 0u;
       cnt = __reduce_add_sync(0xffffffffu, cnt);
-      if (q == a.Q + 1) n1 = cnt;
+      if (q == Qp + 1) n1 = cnt;
       else if (cnt > nmax) nmax = cnt;
     }
     if (lane == 0) s_bd[warp] = (uint64_t)a.k * (((uint64_t)1 << (a.w - 2)) * n1 + (nmax + 2) / 3);
@@ -95,19 +133,46 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
     s_qc[e] = ((g.q + 8) << 16) | g.count;   // q >= -2, count <= kMaxSlices + 1
   }
   __syncthreads();
-  if (threadIdx.x == 0) serial_passes(a, s_qc, s_bd, s_start);
+  if (threadIdx.x == 0) {
+    serial_passes(a, s_qc, s_bd, s_start);
+    for (int c = 0; c < 2; ++c) a.bounds[8 + c] = (uint64_t)(int64_t)s_qcomp[c];
+  }
   __syncthreads();   // order and bounds written (global memory, visible within the block)
-  // the accumulation's term table, one entry per group in the accumulation order
+  // The accumulation's term table, one entry per group in the accumulation order.  For
+  // component c the groups of the products entering it form levels; the last group of
+  // each such level carries the level's shift w (Q_c - q) for c.
   const int G = n_groups;
   const bool z0 = a.bounds[6] != 0, z1 = a.bounds[7] != 0;   // components that vanish identically
   for (int x = threadIdx.x; x < G; x += blockDim.x) {
     const int e = a.order[x];
     const int q = (s_qc[e] >> 16) - 8, count = s_qc[e] & 0xFFFF;
-    const bool last = (x + 1 == G) || ((s_qc[a.order[x + 1]] >> 16) - 8 != q);
     const bool empty = count == 0;   // all its pairs were zero: its plane is never written
     const int prod = a.table[e].prod;
-    a.terms[x] = AccTerm{empty ? -1 : e, last ? a.w * (a.Q - q) : -1, empty || z0 ? 0 : product_sign(a.method, 0, prod),
-                      empty || z1 ? 0 : product_sign(a.method, 1, prod)};
+    int shift[2];
+    for (int c = 0; c < 2; ++c) {
+      shift[c] = -1;
+      if (product_sign(a.method, c, prod) == 0) continue;
+      bool last = true;
+      for (int y = x + 1; y < G; ++y) {
+        const int f = a.order[y];
+        if (product_sign(a.method, c, a.table[f].prod) == 0) continue;
+        last = ((s_qc[f] >> 16) - 8) != q;
+        break;
+      }
+      if (last) shift[c] = a.w * (s_qcomp[c] - q);
+    }
+    a.terms[x] = AccTerm{empty ? -1 : e, (int32_t)(((uint32_t)shift[1] << 16) | ((uint32_t)shift[0] & 0xFFFFu)),
+                         empty || z0 ? 0 : product_sign(a.method, 0, prod), empty || z1 ? 0 : product_sign(a.method, 1, prod)};
+  }
+  __syncthreads();   // every reader of the true levels is done
+  if (a.zwords) {    // the slice GEMMs index digit planes from each operand's first position
+    for (int e = threadIdx.x; e < G; e += blockDim.x) {
+      GroupEntry g = a.table[e];
+      const int pa = s_pos[g.prod][0], pb = s_pos[g.prod][1];
+      g.q -= pa + pb;
+      g.t0 -= pa;
+      a.table[e] = g;
+    }
   }
 }
 

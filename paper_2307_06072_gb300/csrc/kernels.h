@@ -22,11 +22,12 @@ struct SliceGemmArgs {
 };
 
 // One accumulation term per group, in the accumulation order (descending level):
-// group plane index (-1: an emptied group), the two signs, and -- on the last group
-// of a level -- the level's shift.  Written by k_group_table, read by k_oz_accum.
+// group plane index (-1: an emptied group), the two signs, and per component -- on the
+// last group of a level among the groups of the products entering that component --
+// the level's shift w (Q_c - q), else -1.  Written by k_group_table, read by k_oz_accum.
 struct __align__(16) AccTerm {
   int32_t plane;
-  int32_t shift;    // w (Q - q) on the last group of level q, else -1
+  int32_t shifts;   // low 16 bits: real part's shift, high 16 bits: imaginary part's (int16, -1: none)
   int32_t s0, s1;   // the group's sign in the real / imaginary part: -1, 0 or 1
 };
 static_assert(sizeof(AccTerm) == 16, "AccTerm is read as one int4");
@@ -41,8 +42,9 @@ struct GroupTableArgs {
   const int32_t *flagsA, *flagsB;   // per digit plane: any nonzero digit; then per component: any nonzero value
   GroupEntry *table;
   int32_t *order;                   // accumulation order [G], then the unit schedule [G]
-  uint64_t *bounds;                 // out: drop[2], lossy_a[2], lossy_b[2], zero[2]
+  uint64_t *bounds;                 // out: drop[2], lossy_a[2], lossy_b[2], zero[2], then Q_c[2] (int64)
   AccTerm *terms;                      // out: the accumulation's term table [G]
+  const int32_t *zwords;               // per-part split: kZCap - z of A re, A im, B re, B im (else null)
 };
 
 // byte offset of the bounds inside the group-order region
@@ -51,10 +53,10 @@ __host__ __device__ inline uint64_t bounds_offset(int64_t groups, int planes_A, 
   return (b + 7) & ~7ull;
 }
 
-// byte offset of the term table inside the group-order region (after the 8 bounds), and
-// the region's size
+// byte offset of the term table inside the group-order region (after the 8 bounds and
+// the two components' cut levels Q_c), and the region's size
 __host__ __device__ inline uint64_t terms_offset(int64_t groups, int planes_A, int planes_B) {
-  return (bounds_offset(groups, planes_A, planes_B) + 8 * 8 + 15) & ~15ull;
+  return (bounds_offset(groups, planes_A, planes_B) + 10 * 8 + 15) & ~15ull;
 }
 __host__ __device__ inline uint64_t order_region_bytes(int64_t groups, int planes_A, int planes_B) {
   return terms_offset(groups, planes_A, planes_B) + (uint64_t)groups * sizeof(AccTerm);
@@ -70,7 +72,8 @@ struct AccumArgs {
   const int32_t *E, *F, *lossyA, *lossyB;
   int bound_shift, w;          // bounds are b 2^beta; w bits per digit
   uint64_t bound_drop[2], bound_lossy_a[2], bound_lossy_b[2];   // data-independent (plan)
-  const uint64_t *bounds;       // the call's bounds (drop[2], lossy_a[2], lossy_b[2], zero[2]), from k_group_table
+  const uint64_t *bounds;       // the call's bounds (drop[2], lossy_a[2], lossy_b[2], zero[2]) and cut
+                                // levels Q_c[2] (int64), from k_group_table
   const AccTerm *terms;            // the term table, from k_group_table
   int64_t *fallback;            // list of (i*n + j)*2 + c
   int64_t fallback_cap;
@@ -118,9 +121,13 @@ void launch_init(int32_t *status, int32_t *E, int64_t m, int32_t *F, int64_t n, 
                  cudaStream_t st, int32_t *extra = nullptr, int64_t n_extra = 0);
 void launch_line_max(const MatView &A, const MatView &B, int64_t m, int64_t n, int64_t k, int L, int32_t *E,
                      int32_t *F, cudaStream_t st);
+// per-part split: the part offsets z of A (re, im) and B (re, im) into status words kStPartZ..
+void launch_part_offsets(const MatView &A, const MatView &B, int64_t m, int64_t n, int64_t k, int L, int w,
+                         const int32_t *E, const int32_t *F, int32_t *status, cudaStream_t st);
+// zoff: null (one grid per line) or this operand's two offset words (kZCap - z of re, im)
 void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s, int wd,
                       int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, int32_t *plane_nz,
-                      cudaStream_t st);
+                      const int32_t *zoff, cudaStream_t st);
 void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, int L, int D, int DP, int W,
                          int want_sum, const int32_t *E, int32_t *lossy, int32_t *digits, cudaStream_t st);
 void launch_group_table(const GroupTableArgs &a, cudaStream_t st);

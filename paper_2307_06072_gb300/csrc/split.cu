@@ -64,6 +64,48 @@ __global__ void k_colmax(MatView B, int64_t k, int64_t n, int L, int rows_per_bl
   if (best != INT32_MIN) atomicMax(F + j, best);
 }
 
+// Per-part split: z_P = min over lines of floor((E_line - E^P_line) / w), E^P_line the
+// largest exponent of part P (re or im) in the line (rows of A, columns of B); parts
+// without a nonzero element leave the word at 0 (offset kZCap).  Stored as kZCap - z
+// through atomicMax (the status block starts zeroed).
+__global__ void k_part_rows(MatView A, int64_t m, int64_t k, int L, int w, const int32_t *E, int32_t *zw) {
+  const int64_t i = blockIdx.x;
+  if (i >= m || E[i] == INT32_MIN) return;
+  int best[2] = {INT32_MIN, INT32_MIN};
+  for (int64_t l = threadIdx.x; l < k; l += blockDim.x) {
+    const int64_t idx = i * A.ld + l;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      if (comp_nonzero(A, c, idx, L)) best[c] = max(best[c], A.exp[c][idx]);
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    for (int o = 16; o > 0; o >>= 1) best[c] = max(best[c], __shfl_xor_sync(0xffffffffu, best[c], o));
+    if ((threadIdx.x & 31) == 0 && best[c] != INT32_MIN) {
+      const int64_t z = ((int64_t)E[i] - best[c]) / w;   // E_i >= every exponent of the row
+      atomicMax(zw + c, kZCap - (int)(z < kZCap ? z : kZCap));
+    }
+  }
+}
+
+__global__ void k_part_cols(MatView B, int64_t k, int64_t n, int L, int w, const int32_t *F, int32_t *zw) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || F[j] == INT32_MIN) return;
+  int best[2] = {INT32_MIN, INT32_MIN};
+  for (int64_t l = 0; l < k; ++l) {
+    const int64_t idx = l * B.ld + j;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      if (comp_nonzero(B, c, idx, L)) best[c] = max(best[c], B.exp[c][idx]);
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+    if (best[c] != INT32_MIN) {
+      const int64_t z = ((int64_t)F[j] - best[c]) / w;
+      atomicMax(zw + c, kZCap - (int)(z < kZCap ? z : kZCap));
+    }
+}
+
 __global__ void k_init(int32_t *status, int32_t *E, int64_t m, int32_t *F, int64_t n, int32_t *lossyA,
                        int32_t *lossyB, int32_t *extra, int64_t n_extra) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -204,7 +246,8 @@ __device__ __forceinline__ void emit_block(const uint32_t *y0, const uint32_t *y
 template <int W>
 __global__ void __launch_bounds__(128, 4) k_oz_digits(MatView X, int side, int64_t lines, int64_t k, int64_t kpad, int L,
                                                    int s, int want_sum, const int32_t *E, int32_t *lossy,
-                                                   __nv_bfloat16 *digits, int32_t *plane_nz) {
+                                                   __nv_bfloat16 *digits, int32_t *plane_nz,
+                                                   const int32_t *zoff) {
   __shared__ uint32_t nzbits[3][8];   // [stream][32-digit block]: a nonzero digit there
   __shared__ int nzcomp[2];
   if (threadIdx.x < 24) nzbits[threadIdx.x / 8][threadIdx.x % 8] = 0;
@@ -232,7 +275,10 @@ __global__ void __launch_bounds__(128, 4) k_oz_digits(MatView X, int side, int64
       const bool nzc = live && comp_nonzero(X, c, idx, L);
       if (nzc) nzv[c] = true;
       // |X| bit b  <->  M bit b + sh:  X = |v| 2^(ws-1-E), |v| = M 2^(exp-64L)
-      const int64_t sh = nzc ? (64 * (int64_t)L + (int64_t)e_line - (int64_t)X.exp[c][idx] - (xbits - 1)) : 0;
+      // per-part split: part c sits z_c digit positions lower on the line's grid (its s digits
+      // are those of X scaled by 2^(w(s + z_c) - 1 - E)); |X| < 2^(ws-1) still holds
+      const int64_t xb = zoff ? (int64_t)W * (s + (kZCap - zoff[c])) : xbits;
+      const int64_t sh = nzc ? (64 * (int64_t)L + (int64_t)e_line - (int64_t)X.exp[c][idx] - (xb - 1)) : 0;
       m[q][c].start(X.limb[c] + idx, nzc, sh, X.plane, L);
       neg[q][c] = (nzc && X.sign[c][idx]) ? 1u : 0u;
       if (nzc && sh > 0) {   // the bits of M below sh are dropped: the line is lossy unless they are zero
@@ -427,14 +473,20 @@ void launch_line_max(const MatView &A, const MatView &B, int64_t m, int64_t n, i
   k_colmax<<<g, 128, 0, st>>>(B, k, n, L, rpb, F);
 }
 
+void launch_part_offsets(const MatView &A, const MatView &B, int64_t m, int64_t n, int64_t k, int L, int w,
+                         const int32_t *E, const int32_t *F, int32_t *status, cudaStream_t st) {
+  k_part_rows<<<(unsigned)m, 256, 0, st>>>(A, m, k, L, w, E, status + kStPartZ);
+  k_part_cols<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(B, k, n, L, w, F, status + kStPartZ + 2);
+}
+
 void launch_oz_digits(const MatView &X, int side, int64_t lines, int64_t k, int64_t kpad, int L, int s, int wd,
                       int want_sum, const int32_t *E, int32_t *lossy, __nv_bfloat16 *digits, int32_t *plane_nz,
-                      cudaStream_t st) {
+                      const int32_t *zoff, cudaStream_t st) {
   dim3 g((unsigned)((kpad / 2 + 127) / 128), (unsigned)lines);
   if (wd == 9)
-    k_oz_digits<9><<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits, plane_nz);
+    k_oz_digits<9><<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits, plane_nz, zoff);
   else
-    k_oz_digits<8><<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits, plane_nz);
+    k_oz_digits<8><<<g, 128, 0, st>>>(X, side, lines, k, kpad, L, s, want_sum, E, lossy, digits, plane_nz, zoff);
 }
 
 void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, int L, int D, int DP, int W,

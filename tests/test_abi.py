@@ -183,3 +183,22 @@ def test_batched_arguments_checked_on_host(mp):
     assert lib.mpcgemm_batched(2, arr, None, ws, total.value - 256, None) == n.MPC_ENOSPC
     bad = (n.MpcProblem * 2)(good[0], problem(16, 8, 64, 2000))                          # p out of range
     assert lib.mpcgemm_batched(2, bad, None, ws, total.value, None) == n.MPC_EINVAL
+
+
+def test_per_part_split_plan(mp):
+    """The per-part split is a 4M option: 3M is rejected on the host; a 4M plan keeps the
+    default sizes (the device cuts fewer pairs, never more) and makes two more launches
+    (the part offsets of A and B)."""
+    import ctypes
+    out = mp._native.Plan()
+    prm = mp._native.oz_params(split="per_part")
+    rc = mp.lib().mpcgemm_plan(64, 64, 64, 256, 1, 1, ctypes.byref(prm), ctypes.byref(out))
+    assert rc == mp._native.MPC_EINVAL
+    d = mp.plan(300, 200, 100, 256, "4m", "ozaki", dict(split="per_part"))
+    base = mp.plan(300, 200, 100, 256, "4m", "ozaki")
+    assert d["split"] == 1 and base["split"] == 0
+    assert d["ws_bytes"] == base["ws_bytes"] and d["n_groups_total"] == base["n_groups_total"]
+    assert d["launches"] == base["launches"] + 2
+    prm.split = 2
+    rc = mp.lib().mpcgemm_plan(64, 64, 64, 256, 0, 1, ctypes.byref(prm), ctypes.byref(out))
+    assert rc == mp._native.MPC_EINVAL
