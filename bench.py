@@ -128,9 +128,60 @@ def run_batched(mp, torch, dev, stream, steps: int, warmup: int):
             "sum_8mnk": work, "tuned": best, "tuning_ms": {str(c): round(t, 3) for c, t in tuner.last_timings},
             "workspace_gb": round(total / 1e9, 2),
             "tensor_tflops_whole_call": round(flops / (ms / 1e3) / 1e12, 1),
-            "slice_gemm_launches": -(-len(specs) // 48) if best.get("kernel") != "mma_sync" else len(specs),
-            "launch": "one CUDA graph replay per step (split/accumulate per problem, persistent tcgen05 "
-                      "slice-GEMM launches of up to 48 problems each)"}
+            "slice_gemm_launches": -(-len(specs) // 64) if best.get("kernel") != "mma_sync" else len(specs),
+            "launch": "one CUDA graph replay per step (split/accumulate per problem, one persistent tcgen05 "
+                      "slice-GEMM launch for all 64 problems)"}
+
+
+def shifted_part(mat, c: int, by: int):
+    """The matrix with component c scaled by 2^by (exponents of its nonzero entries)."""
+    out = mat.copy()
+    nz = out.limb[c, -1] != 0
+    out.exp[c] = np.where(nz, out.exp[c] + by, out.exp[c]).astype(np.int32)
+    return out
+
+
+def run_per_part(mp, torch, dev, stream, n: int = 512, p: int = 512, shift: int = -100, steps: int = 3):
+    """The per-part split against the default one when every imaginary part is 2^shift
+    times the size of the real parts: times, stage times (the default split sends every
+    imaginary component to the exact fallback), part offsets, kept pairs, oracle check."""
+    A = shifted_part(si.random_matrix(n, n, p, si.SEED_BASE + 6, "uniform_exp"), 1, shift)
+    B = shifted_part(si.random_matrix(n, n, p, si.SEED_BASE + 1006, "uniform_exp"), 1, shift)
+    dA, dB = mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(B, dev)
+    out = {"m": n, "n": n, "k": n, "p_bits": p, "method": "4m", "imaginary_scale": f"2^{shift}"}
+    for split in ("common", "per_part"):
+        dC = mp.DeviceMatrix.empty(n, n, p, dev)
+        prm = {"split": split}
+        ws = mp.Workspace(dev)
+        mp.mpcgemm(dA, dB, dC, p, "4m", "ozaki", workspace=ws, stream=stream, params=prm)
+        torch.cuda.synchronize(dev)
+        evs = []
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            mp.mpcgemm(dA, dB, dC, p, "4m", "ozaki", workspace=ws, stream=stream, params=prm, events=ev)
+            evs.append(ev)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        st = mp.read_status(ws, stream)
+        pl = mp.plan(n, n, n, p, "4m", "ozaki", prm)
+        G = pl["n_groups_total"]
+        table = ws.tensor[pl["off_group_table"]: pl["off_group_table"] + 16 * G].view(torch.int32).cpu().numpy()
+        zw = ws.tensor[40:56].view(torch.int32).cpu().numpy()
+        ms = start.elapsed_time(end) / steps
+        out[split] = {"ms_per_step": round(ms, 3), "value": 8.0 * n ** 3 / (ms / 1e3), "unit": UNIT,
+                      "stage_ms": {k_: round(float(np.mean([e[x].elapsed_time(e[x + 1]) for e in evs])), 3)
+                                   for x, k_ in enumerate(("split", "slice_gemm", "accumulate_round", "fallback"))},
+                      "slices_per_part": pl["s"], "kept_pairs": int(table.reshape(G, 4)[:, 3].sum()),
+                      "fallback_components": st["fallback_entries"], "device_status": st,
+                      "oracle_check": sampled_check(mp, A, B, p, dC, 16, 77)}
+        if split == "per_part":
+            out[split]["part_offsets_z"] = {"A_re": 2048 - int(zw[0]), "A_im": 2048 - int(zw[1]),
+                                            "B_re": 2048 - int(zw[2]), "B_im": 2048 - int(zw[3])}
+        del ws, dC
+    out["speedup_per_part_vs_common"] = round(out["common"]["ms_per_step"] / out["per_part"]["ms_per_step"], 1)
+    return out
 
 
 def run_lu(mp, torch, dev, n: int = 2048, p: int = 512, block: int = 128, method: str = "3m"):
@@ -506,6 +557,8 @@ def run_ours(args):
                 known[f"ozaki_speedup_vs_plain_{mt}"] = round(known[f"ozaki_{mt}"]["value"] /
                                                               known[f"plain_{mt}"]["value"], 2)
             extras["precision_sweep"] = run_sweep(mp, torch, dev, stream, ws, SWEEP, skip=args.workload, known=known)
+        if not args.no_sweep and ws_ == 1:
+            extras["per_part_split"] = run_per_part(mp, torch, dev, stream)
         if not args.no_batched:
             extras["batched_c3"] = run_batched(mp, torch, dev, stream, 3, 3)
         if not args.no_lu:
@@ -747,7 +800,7 @@ def main():
     ap.add_argument("--method", choices=["3m", "4m"], default="3m")
     ap.add_argument("--algo", choices=["ozaki", "plain"], default="ozaki",
                     help="the timed step's algorithm (plain: the CUDA-core GEMM, no side measurements)")
-    ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_2sm", "mma_sync"], default="auto",
+    ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_n128", "tcgen05_2sm", "mma_sync"], default="auto",
                     help="slice-GEMM kernel")
     ap.add_argument("--quick", action="store_true", help="skip the 4M / plain side measurements")
     ap.add_argument("--no-sweep", action="store_true", help="skip the precision sweep (n 1024/2048, p 256/512/1024)")

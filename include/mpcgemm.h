@@ -77,7 +77,8 @@ enum { MPC_PLAIN = 0, MPC_OZAKI = 1 };    /* Eq. (simple_triple_loop) / Alg. 2 *
  * the per-part split of Alg. 2 (4M only; see mpc_oz_params.split). */
 enum { MPC_SPLIT_COMMON = 0, MPC_SPLIT_PER_PART = 1 };
 /* Slice-GEMM kernels (value 3 is not used and is rejected). */
-enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2, MPC_KERNEL_TCGEN05_2SM = 4 };
+enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2, MPC_KERNEL_TCGEN05_2SM = 4,
+       MPC_KERNEL_TCGEN05_N128 = 5 };
 
 /* Largest supported precision and inner size. */
 #define MPC_MAX_P_BITS 1024
@@ -106,10 +107,11 @@ typedef struct mpc_mat {
  *   max_group   cap on the slice pairs summed in one group (0 -> the int32 limit
  *               G_max); smaller groups make more, shorter work units.
  *   kernel      MPC_KERNEL_*: which slice-GEMM kernel (auto = TCGEN05, single
- *               CTAs with 128 x 256 tiles; TCGEN05_2SM CTA pairs that run one
- *               256-row MMA across both SMs, each loading its own rows of A and
- *               half of B; the mma.sync kernel is a second, independent
- *               implementation of the same sums).
+ *               CTAs with 128 x 256 tiles and two TMEM accumulators; TCGEN05_N128
+ *               single CTAs with 128 x 128 tiles and four; TCGEN05_2SM CTA pairs
+ *               that run one 256-row MMA across both SMs, each loading its own
+ *               rows of A and half of B; the mma.sync kernel is a second,
+ *               independent implementation of the same sums).
  *   wait_limit_cycles
  *               SM clock cycles that one barrier wait of the tcgen05 kernels may
  *               last before the kernel gives up (0 -> about 4e9, some 2 s).  A
@@ -247,7 +249,7 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits,
 /*
  * Batched form: `count` independent complex GEMMs, possibly of different sizes,
  * precisions and methods, in one call.  The Ozaki problems share ONE persistent
- * tcgen05 slice-GEMM launch (48 problems per launch), so small problems fill
+ * tcgen05 slice-GEMM launch (64 problems per launch), so small problems fill
  * the GPU together; the split, accumulation and fallback kernels run per
  * problem; in batches of 16 problems or more they are spread over 8
  * library-owned side streams that are forked from and

@@ -1,8 +1,10 @@
 """Autotuner for the slice-GEMM configuration of a (batched) complex GEMM.
 
 The tunable parts are the work-unit shape and size: the tcgen05 kernel in
-single CTAs (128 x 256 output tiles) or in CTA pairs running one
-cta_group::2 MMA (256 x 256 tiles, each SM loading half of B),
+single CTAs with 128 x 256 output tiles (two TMEM accumulators) or 128 x 128
+tiles (four TMEM accumulators: the MMAs run further ahead of the drain), or in
+CTA pairs running one cta_group::2 MMA (256 x 256 tiles, each SM loading half
+of B),
 the digit width, and the cap on slice pairs per group (smaller groups give
 more, shorter units, which balances small problems better; the int32 limit
 is the largest).  The k-block (64 bf16 = one 128-byte swizzled row) is
@@ -17,10 +19,13 @@ import math
 from . import _native
 
 CANDIDATES = (
-    {"kernel": "auto"},
     {"kernel": "tcgen05"},
-    {"kernel": "auto", "max_group": 16},
+    {"kernel": "tcgen05", "max_group": 8},
+    {"kernel": "tcgen05", "max_group": 16},
+    {"kernel": "tcgen05_n128"},
+    {"kernel": "tcgen05_n128", "max_group": 8},
     {"kernel": "tcgen05_2sm"},
+    {"kernel": "tcgen05_2sm", "max_group": 8},
     {"kernel": "tcgen05_2sm", "digit_bits": 8},
 )
 
@@ -41,7 +46,7 @@ class Autotuner:
         self.cache: dict[tuple, dict] = {}
         self.last_timings: list[tuple[dict, float]] = []
 
-    def choose(self, problems, workspace=None, stream=None, repeats: int = 1) -> dict:
+    def choose(self, problems, workspace=None, stream=None, repeats: int = 3) -> dict:
         """Best parameters for this batch (timed on first sight of its signature)."""
         import torch
         from . import mpcgemm_batched

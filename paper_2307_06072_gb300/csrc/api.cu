@@ -59,7 +59,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   P.limbs = L;
   out->kernel = prm ? prm->kernel : MPC_KERNEL_AUTO;
   if (out->kernel != MPC_KERNEL_AUTO && out->kernel != MPC_KERNEL_TCGEN05 && out->kernel != MPC_KERNEL_MMA_SYNC &&
-      out->kernel != MPC_KERNEL_TCGEN05_2SM)
+      out->kernel != MPC_KERNEL_TCGEN05_2SM && out->kernel != MPC_KERNEL_TCGEN05_N128)
     return MPC_EINVAL;
   if (prm && prm->wait_limit_cycles < 0) return MPC_EINVAL;
   P.split = prm ? prm->split : MPC_SPLIT_COMMON;
@@ -204,6 +204,11 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   // init, row max, column max, group table, 2 x digits, slice GEMM, accumulate, fallback (+ 2 part offsets)
   P.launches = P.split == MPC_SPLIT_PER_PART ? 11 : 9;
   return MPC_OK;
+}
+
+// the tcgen05 variant of a kernel choice (auto: single CTAs with 128 x 256 tiles)
+int tile_of(int kernel) {
+  return kernel == MPC_KERNEL_TCGEN05_2SM ? kTile2Sm : kernel == MPC_KERNEL_TCGEN05_N128 ? kTileNarrow : kTileSingle;
 }
 
 int cuda_code(cudaError_t e) { return e == cudaSuccess ? MPC_OK : MPC_ECUDA - (int)e; }
@@ -504,9 +509,8 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_
       SliceGemmArgs sa = slice_args(c);
       if (c.pl.kernel == MPC_KERNEL_MMA_SYNC) {
         launch_slicegemm_mma(sa, st);
-      } else {   // auto: the single-CTA tcgen05 kernel (measured faster than the 2-SM one)
-        const bool two = c.pl.kernel == MPC_KERNEL_TCGEN05_2SM;
-        const cudaError_t e = launch_slicegemm_tc(sa, st, two, c.pl.wait_limit);
+      } else {   // auto: the single-CTA tcgen05 kernel with 128 x 256 tiles
+        const cudaError_t e = launch_slicegemm_tc(sa, st, tile_of(c.pl.kernel), c.pl.wait_limit);
         if (e == cudaErrorNotSupported && c.pl.kernel == MPC_KERNEL_AUTO) launch_slicegemm_mma(sa, st);
         else if (e != cudaSuccess) return e == cudaErrorNotSupported ? MPC_ENOTSUP : cuda_code(e);
       }
@@ -643,9 +647,8 @@ int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *pa
       slices.push_back(slice_args(c));
     }
   }
-  if (!slices.empty()) {   // one persistent launch for every Ozaki problem (48 per launch)
-    const bool two = kernel == MPC_KERNEL_TCGEN05_2SM;
-    const cudaError_t e = launch_slicegemm_tc_batch(slices.data(), (int)slices.size(), st, two,
+  if (!slices.empty()) {   // one persistent launch for every Ozaki problem (64 per launch)
+    const cudaError_t e = launch_slicegemm_tc_batch(slices.data(), (int)slices.size(), st, tile_of(kernel),
                                                     params ? params->wait_limit_cycles : 0);
     if (e == cudaErrorNotSupported && kernel == MPC_KERNEL_AUTO) {
       for (const SliceGemmArgs &sa : slices) launch_slicegemm_mma(sa, st);

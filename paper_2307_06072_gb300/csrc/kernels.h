@@ -132,11 +132,13 @@ void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, i
                          int want_sum, const int32_t *E, int32_t *lossy, int32_t *digits, cudaStream_t st);
 void launch_group_table(const GroupTableArgs &a, cudaStream_t st);
 void launch_slicegemm_mma(const SliceGemmArgs &a, cudaStream_t st);
-// two_sm: CTA pairs running one cta_group::2 MMA of M = 256, else single CTAs;
-// wait_limit: cycles a barrier wait may take (0: the default of about 2 s), a
-// positive limit makes the waits poll so that it is exact
-cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, bool two_sm, long long wait_limit = 0);
-cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, bool two_sm,
+// tile: kTileSingle (one CTA per 128 x 256 tile, two TMEM accumulators), kTile2Sm (CTA
+// pairs running one cta_group::2 MMA of M = 256) or kTileNarrow (one CTA per 128 x 128
+// tile, four TMEM accumulators); wait_limit: cycles a barrier wait may take (0: the
+// default of about 2 s), a positive limit makes the waits poll so that it is exact
+enum { kTileSingle = 0, kTile2Sm = 1, kTileNarrow = 2 };
+cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int tile, long long wait_limit = 0);
+cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, int tile,
                                       long long wait_limit = 0);
 void launch_oz_accum(const AccumArgs &a, const OutView &C, cudaStream_t st);
 void launch_fallback(const FallbackArgs &f, const MatView &A, const MatView &B, const OutView &C, int blocks,

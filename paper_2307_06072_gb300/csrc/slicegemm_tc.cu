@@ -49,21 +49,26 @@ namespace mpc {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int BM = 128, BK = 64;
 
-template <bool TWO>
+// A variant: one CTA or a CTA pair (TWO) per unit, unit tiles of BM x BNT per CTA.
+// The TMEM's 512 columns hold NBUF = 512 / BNT fp32 accumulators; the stage ring fills
+// the shared memory (227 KB).
+template <bool TWO, int BNT>
 struct TcCfg {
   static constexpr int kPair = TWO ? 2 : 1;                  // CTAs per unit
-  static constexpr int STAGES = TWO ? 7 : 4;
-  static constexpr int B_ROWS = TWO ? BN / 2 : BN;          // B rows in this CTA's shared memory
+  static constexpr int BN = BNT;
+  static constexpr int B_ROWS = TWO ? BNT / 2 : BNT;        // B rows in this CTA's shared memory
   static constexpr int A_BYTES = BM * BK * 2, B_BYTES = B_ROWS * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 512;   // 7 x 32 KB + barriers <= 227 KB
+  static constexpr int STAGES = (227 * 1024 - 1024 - 512) / STAGE_BYTES;   // 4 (48 KB stages) or 7 (32 KB)
+  static constexpr int NBUF = 512 / BNT;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 512;
 };
 constexpr int EPI_WARPS = 8;   // 16 warps of 64 columns measured slower (more spills, no faster drain)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long kDefaultWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 constexpr int URING = 4;                                   // unit-index ring slots
-constexpr int kMaxBatch = 48;                              // problems per launch (kernel parameter space)
+constexpr int kMaxBatch = 64;                              // problems per launch (kernel parameter space)
 constexpr int kStUnitCounter = 8;                          // status word used as the unit counter
 
 // One launch serves a set of up to kMaxBatch independent problems (a single
@@ -94,6 +99,19 @@ struct TcParams {
   int32_t *status;
   TcProblem prob[kMaxBatch];
 };
+
+static_assert(sizeof(TcMaps) + sizeof(TcParams) <= 32764, "kernel parameters must fit the 32 KB parameter space");
+
+// the problem whose units include unit u (binary search over the problems' first units)
+__device__ __forceinline__ int problem_of(const TcParams &P, int64_t u) {
+  int lo = 0, hi = P.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.prob[mid].unit0 <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 // What a bounded wait needs: the CTA's abort flag, the status block and the limit.
 struct Waits {
@@ -243,25 +261,25 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D fp32, A = B = bf16, both K-major, N = 256, M = 128 (one
+// Instruction descriptor, kind::f16: D fp32, A = B = bf16, both K-major, N = BNT, M = 128 (one
 // CTA) or 256 (a CTA pair: the leader's 128 rows in its TMEM, the peer's in the peer's TMEM).
-template <bool TWO>
+template <bool TWO, int BNT>
 __host__ __device__ constexpr uint32_t idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((TWO ? 2 : 1) * BM >> 4) << 24);
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BNT >> 3) << 17) | ((uint32_t)((TWO ? 2 : 1) * BM >> 4) << 24);
 }
 
-template <bool TWO>
+template <bool TWO, int BNT>
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
   if (TWO)
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc<true>()), "r"(accumulate));
+        "l"(a), "l"(b), "r"(idesc<true, BNT>()), "r"(accumulate));
   else
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc<false>()), "r"(accumulate));
+        "l"(a), "l"(b), "r"(idesc<false, BNT>()), "r"(accumulate));
 }
 
 // Arrive on `bar` once the MMAs issued so far complete.  The CTA pair's commit arrives on
@@ -305,10 +323,9 @@ struct Unit {
 // unit u -> (group, tile); for CTA pairs a unit is a pair of row tiles, CTA `rank` takes one
 template <bool TWO>
 __device__ __forceinline__ Unit decode(const TcParams &P, int64_t u, uint32_t rank) {
-  constexpr int CP = TcCfg<TWO>::kPair;
+  constexpr int CP = TWO ? 2 : 1;
   Unit x;
-  int pi = 0;
-  while (pi + 1 < P.count && P.prob[pi + 1].unit0 <= u) ++pi;
+  const int pi = problem_of(P, u);
   const TcProblem &q = P.prob[pi];
   const int64_t r = u - q.unit0;
   const int tiles_mu = (q.tiles_m + CP - 1) / CP;
@@ -327,11 +344,9 @@ __device__ __forceinline__ Unit decode(const TcParams &P, int64_t u, uint32_t ra
 // the group of unit u has no pairs left (all its digit planes were zero)
 template <bool TWO>
 __device__ __forceinline__ bool unit_empty(const TcParams &P, int64_t u) {
-  int pi = 0;
-  while (pi + 1 < P.count && P.prob[pi + 1].unit0 <= u) ++pi;
-  const TcProblem &q = P.prob[pi];
+  const TcProblem &q = P.prob[problem_of(P, u)];
   const int64_t r = u - q.unit0;
-  const int tiles = ((q.tiles_m + TcCfg<TWO>::kPair - 1) / TcCfg<TWO>::kPair) * q.tiles_n;
+  const int tiles = ((q.tiles_m + (TWO ? 1 : 0)) / (TWO ? 2 : 1)) * q.tiles_n;
   const int e = q.sched ? q.sched[r / tiles] : (int)(r / tiles);
   return q.groups[e].count == 0;
 }
@@ -346,10 +361,11 @@ __device__ __forceinline__ bool unit_empty(const TcParams &P, int64_t u) {
 // commits arrive on both CTAs' barriers, and both CTAs' epilogues hand each
 // drained TMEM buffer back on the leader's barrier.  The leader hands out the
 // unit indices to both CTAs through distributed shared memory.
-template <bool TWO>
+template <bool TWO, int BNT>
 __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
     k_slicegemm_tc(const __grid_constant__ TcMaps maps, const __grid_constant__ TcParams P) {
-  using C = TcCfg<TWO>;
+  using C = TcCfg<TWO, BNT>;
+  constexpr int BN = BNT, NBUF = C::NBUF;
   constexpr int COLS = 4 * BN / EPI_WARPS;    // accumulator columns per epilogue thread (one TMEM lane)
   constexpr int STAGES = C::STAGES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
@@ -359,8 +375,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
   uint64_t *empty = full + STAGES;
   uint64_t *tfull = empty + STAGES;
-  uint64_t *tempty = tfull + 2;
-  uint64_t *ufull = tempty + 2;
+  uint64_t *tempty = tfull + NBUF;
+  uint64_t *ufull = tempty + NBUF;
   uint64_t *uempty = ufull + URING;
   uint64_t *mdone = uempty + URING;   // the MMA issuer's last commit: every MMA has completed
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
@@ -375,7 +391,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);   // one (for the pair: multicast) MMA commit
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NBUF; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], TWO ? 2 * EPI_WARPS : EPI_WARPS);   // pair: both CTAs drain the leader's MMA
     }
@@ -501,14 +517,13 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
             const uint64_t bd = smem_desc(sB + stage * B_BYTES);
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)   // K = 16 per instruction: +32 B in the swizzled row
-              mma_f16<TWO>(d_tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb > c0 || kk > 0) ? 1u : 0u);
+              mma_f16<TWO, BNT>(d_tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb > c0 || kk > 0) ? 1u : 0u);
             mma_commit<TWO>(&empty[stage]);   // the producer(s) may refill the stage
             if (++stage == STAGES) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
           mma_commit<TWO>(&tfull[buf]);       // the epilogue(s) may drain
-          buf ^= 1;
-          if (buf == 0) tphase ^= 1;
+          if (++buf == NBUF) { buf = 0; tphase ^= 1; }
         }
       }
       // Whether it finished or gave up: every MMA issued must complete before TMEM is freed
@@ -564,8 +579,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
           if (TWO && rank == 1) mbar_arrive_cluster_relaxed(mapa(smem_u32(&tempty[buf]), 0));
           else mbar_arrive(&tempty[buf]);
         }
-        buf ^= 1;
-        if (buf == 0) tphase ^= 1;
+        if (++buf == NBUF) { buf = 0; tphase ^= 1; }
       }
       if (!ok) break;
       // store the int32 tile rows of this thread
@@ -647,9 +661,9 @@ int num_sms() {
 
 // One persistent launch over the units of up to kMaxBatch problems (the unit
 // counter lives in the first problem's status block, zeroed by its init).
-template <bool TWO>
+template <bool TWO, int BNT>
 static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t st, long long wait_limit) {
-  using C = TcCfg<TWO>;
+  using C = TcCfg<TWO, BNT>;
   static TcMaps maps;    // host staging of the kernel parameters (copied at launch)
   static TcParams P;
   std::memset(&P, 0, sizeof(P));
@@ -670,7 +684,7 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
     t.n = a.n;
     t.kbpp = (int)(a.kpad / BK);
     t.tiles_m = (int)((a.m + BM - 1) / BM);
-    t.tiles_n = (int)((a.n + BN - 1) / BN);
+    t.tiles_n = (int)((a.n + BNT - 1) / BNT);
     t.chunk_kb = a.chunk_kb;
     t.unit0 = units;
     t.groups = a.groups;
@@ -685,8 +699,8 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
   P.poll = wait_limit > 0;
   P.wait_limit = wait_limit > 0 ? wait_limit : kDefaultWaitCycles;
   if (units == 0) return cudaSuccess;
-  static bool attr = false;
-  auto kfn = k_slicegemm_tc<TWO>;
+  static bool attr = false;   // one per instantiation
+  auto kfn = k_slicegemm_tc<TWO, BNT>;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
@@ -717,7 +731,7 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
   return cudaLaunchKernelEx(&cfg, kfn, maps, P);
 }
 
-cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, bool two_sm,
+cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, int tile,
                                       long long wait_limit) {
   int dev = 0, major = 0, minor = 0;
   cudaGetDevice(&dev);
@@ -728,15 +742,16 @@ cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cuda
   std::lock_guard<std::mutex> lock(mu);
   for (int q0 = 0; q0 < count; q0 += kMaxBatch) {
     const int c = count - q0 < kMaxBatch ? count - q0 : kMaxBatch;
-    const cudaError_t e = two_sm ? launch_set<true>(list + q0, c, st, wait_limit)
-                                 : launch_set<false>(list + q0, c, st, wait_limit);
+    const cudaError_t e = tile == kTile2Sm      ? launch_set<true, 256>(list + q0, c, st, wait_limit)
+                          : tile == kTileNarrow ? launch_set<false, 128>(list + q0, c, st, wait_limit)
+                                                : launch_set<false, 256>(list + q0, c, st, wait_limit);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, bool two_sm, long long wait_limit) {
-  return launch_slicegemm_tc_batch(&a, 1, st, two_sm, wait_limit);
+cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int tile, long long wait_limit) {
+  return launch_slicegemm_tc_batch(&a, 1, st, tile, wait_limit);
 }
 
 }  // namespace mpc

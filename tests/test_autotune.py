@@ -36,7 +36,7 @@ def _problem(m, n, k, p=256, method="3m", algo="ozaki"):
 def fake_gpu(monkeypatch):
     import torch
     calls = []
-    cost = {"auto": 5.0, "tcgen05": 3.0, "tcgen05_2sm": 1.0}
+    cost = {"auto": 5.0, "tcgen05": 3.0, "tcgen05_n128": 4.0, "tcgen05_2sm": 1.0}
 
     def fake_batched(problems, params=None, workspace=None, stream=None):
         calls.append(dict(params))
@@ -60,7 +60,7 @@ def test_picks_the_fastest_candidate_and_skips_failures(fake_gpu):
     assert len(timed) == len(autotune.CANDIDATES) - 1
     ms = {str(c): t for c, t in tuner.last_timings}
     assert ms[str({"kernel": "tcgen05"})] == pytest.approx(3.0)           # per repeat
-    assert ms[str({"kernel": "auto", "max_group": 16})] == pytest.approx(5.5)
+    assert ms[str({"kernel": "tcgen05", "max_group": 16})] == pytest.approx(3.5)
 
 
 def test_cached_per_signature(fake_gpu):

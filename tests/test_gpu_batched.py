@@ -59,7 +59,7 @@ def test_batched_equals_single_calls_and_oracle(kernel):
 def test_batch_larger_than_one_launch():
     import torch
     M = gu.mp()
-    specs = [(16 + x, 24, 20 + 2 * x, 128 + 64 * (x % 3), "3m" if x % 2 else "4m", "ozaki") for x in range(53)]
+    specs = [(16 + x % 40, 24, 20 + 2 * (x % 40), 128 + 64 * (x % 3), "3m" if x % 2 else "4m", "ozaki") for x in range(70)]   # more than the 64 problems of one launch
     probs, host = _make(specs, 1700)
     M.mpcgemm_batched(probs)
     torch.cuda.synchronize()

@@ -5,8 +5,9 @@ agree bit for bit, the outputs must equal O1, and no bounded wait may time out.
 Shapes cover single and many tiles, ragged M / N / K edges, 3M sum digits,
 units of one pair and of 15 pairs (9-bit digits: 120 chunks of 256 elements) or
 63 pairs (8-bit digits: 960-element chunks), both TMEM buffers, and more units
-than SMs (persistent loop).  Kernels: single CTAs and CTA pairs running one
-256-row cta_group::2 MMA.
+than SMs (persistent loop).  Kernels: single CTAs with 128 x 256 tiles (two TMEM
+accumulators) and with 128 x 128 tiles (four), and CTA pairs running one 256-row
+cta_group::2 MMA.
 """
 import numpy as np
 import pytest
@@ -35,7 +36,7 @@ def _planes(A, B, p, method, kernel, w):
     return C, gu.ws_groups(ws, pl, A.rows, B.cols), st
 
 
-@pytest.mark.parametrize("kernel", ["tcgen05", "tcgen05_2sm"])
+@pytest.mark.parametrize("kernel", ["tcgen05", "tcgen05_2sm", "tcgen05_n128"])
 @pytest.mark.parametrize("m,k,n,p,method,dist,w", CASES)
 def test_tcgen05_matches_mma_sync_and_oracle(m, k, n, p, method, dist, w, kernel):
     """(260 rows = 3 row tiles: the 2-SM kernel's second CTA of the last pair has no rows.)"""
