@@ -153,7 +153,11 @@ def substitute(a, ipiv, b, p: int):
 
 
 def pack_values(rows, p):
-    """[[(re, im)]] -> MPCMatrix (format arrays)."""
-    re = [[v[0] for v in row] for row in rows]
-    im = [[v[1] for v in row] for row in rows]
+    """[[(re, im)]] -> MPCMatrix (format arrays).
+
+    Entries the factorisation never changed keep the input's mantissa, whose integer
+    carries the 64L - p zero bits below the p-bit grid; rounding a p-bit value to p bits
+    returns the same value with a mantissa of at most p bits, as the format wants."""
+    re = [[rn(v[0], p) for v in row] for row in rows]
+    im = [[rn(v[1], p) for v in row] for row in rows]
     return o1.pack(re, im, p)

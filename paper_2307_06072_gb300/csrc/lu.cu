@@ -18,6 +18,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "mpscalar.cuh"
+#include "mpscalar_fast.cuh"
 
 namespace mpc {
 
@@ -41,8 +42,22 @@ struct MatRW {
   }
 };
 
+// RN_p of the exact sum of the terms: the register-resident form for L = 4, 8 when the
+// terms' window fits it, else the generic one (same result).  Not inlined: one copy serves
+// every kernel.
+__device__ __noinline__ bool sum_round(const Term *t, int nt, int p, int L, MPOut o, bool *truncated) {
+  int r = -1;
+  if (L == 8) r = fastmp::sum_round<8>(t, nt, p, o);
+  else if (L == 4) r = fastmp::sum_round<4>(t, nt, p, o);
+  if (r >= 0) {
+    *truncated = false;
+    return r == 1;
+  }
+  return mp_sum_round(t, nt, p, L, o, truncated);
+}
+
 // exact a - l * u per component (Eq. 4m_way_base), rounded once; into (r, col) of M
-__device__ void cfma_store(const MatRW &M, int64_t r, int64_t col, const MPRef &are, const MPRef &aim,
+__device__ __noinline__ void cfma_store(const MatRW &M, int64_t r, int64_t col, const MPRef &are, const MPRef &aim,
                            const MPRef &lre, const MPRef &lim, const MPRef &ure, const MPRef &uim, int p, int L,
                            int32_t *status) {
   bool trunc = false, ok = true;
@@ -50,13 +65,13 @@ __device__ void cfma_store(const MatRW &M, int64_t r, int64_t col, const MPRef &
   {
     Term t[3] = {{are, are, false, false}, {lre, ure, true, true}, {lim, uim, true, false}};
     bool tr;
-    ok &= mp_sum_round(t, 3, p, L, ore, &tr);
+    ok &= sum_round(t, 3, p, L, ore, &tr);
     trunc |= tr;
   }
   {
     Term t[3] = {{aim, aim, false, false}, {lre, uim, true, true}, {lim, ure, true, true}};
     bool tr;
-    ok &= mp_sum_round(t, 3, p, L, oim, &tr);
+    ok &= sum_round(t, 3, p, L, oim, &tr);
     trunc |= tr;
   }
   if (trunc) atomicOr(reinterpret_cast<int *>(status) + kStTruncated, 1);
@@ -66,8 +81,18 @@ __device__ void cfma_store(const MatRW &M, int64_t r, int64_t col, const MPRef &
 // complex quotient a / d, componentwise RN_p of the exact value, into (r, col).
 // Both exact numerators are formed before anything is stored (the output may
 // be a itself).
-__device__ void cdiv_store(const MatRW &M, int64_t r, int64_t col, const MPRef &are, const MPRef &aim,
-                           const MPRef &dre, const MPRef &dim, int p, int L, int32_t *status) {
+__device__ __noinline__ void cdiv_store(const MatRW &M, int64_t r, int64_t col, const MPRef &are, const MPRef &aim,
+                                        const MPRef &dre, const MPRef &dim, int p, int L, int32_t *status) {
+  {   // the register-resident form for L = 4, 8 when the windows fit it (same result)
+    int rf = -1;
+    if (L == 8) rf = fastmp::cdiv<8>(are, aim, dre, dim, p, M.out(0, r, col), M.out(1, r, col));
+    else if (L == 4) rf = fastmp::cdiv<4>(are, aim, dre, dim, p, M.out(0, r, col), M.out(1, r, col));
+    if (rf == 2) return;   // d == 0: refused earlier
+    if (rf >= 0) {
+      if (rf == 0) atomicOr(reinterpret_cast<int *>(status) + kStErange, 1);
+      return;
+    }
+  }
   uint64_t den[kWinLimbs], num[2][kWinLimbs];
   int nwd, nwn[2];
   int64_t lsbd, lsbn[2];
@@ -125,7 +150,7 @@ __global__ void __launch_bounds__(256) k_lu_pivot(MatRW A, int64_t n, int64_t j,
     MPOut o{&ks, &k.e, k.m, 1};
     Term t[2] = {{re, re, false, false}, {im, im, false, false}};
     bool tr;
-    mp_sum_round(t, 2, p, L, o, &tr);
+    sum_round(t, 2, p, L, o, &tr);
     k.nz = k.m[L - 1] != 0;
     if (brow < 0 || key_greater(k, best, L)) {
       best = k;
@@ -220,7 +245,7 @@ __global__ void k_sub_block(MatRW A, int64_t r0, int64_t c0, int64_t rows, int64
     MPRef a = A.ref(c, r0 + r, c0 + col), q = P.ref(c, r, col);
     Term tt[2] = {{a, a, false, false}, {q, q, false, true}};
     bool tr;
-    ok &= mp_sum_round(tt, 2, p, L, A.out(c, r0 + r, c0 + col), &tr);
+    ok &= sum_round(tt, 2, p, L, A.out(c, r0 + r, c0 + col), &tr);
     trunc |= tr;
   }
   if (trunc) atomicOr(reinterpret_cast<int *>(status) + kStTruncated, 1);
@@ -230,7 +255,7 @@ __global__ void k_sub_block(MatRW A, int64_t r0, int64_t c0, int64_t rows, int64
 // Solve with the factors for one right-hand side column per block (blockIdx.x), every
 // step inside the block: for n up to the block size every row has a thread of its own,
 // and a single launch costs less than 2n of them.
-__global__ void __launch_bounds__(1024) k_lu_solve(MatRW LU, int64_t n, const int32_t *ipiv, MatRW Bm, int p, int L,
+__global__ void __launch_bounds__(256) k_lu_solve(MatRW LU, int64_t n, const int32_t *ipiv, MatRW Bm, int p, int L,
                                                    int32_t *status) {
   const int64_t col = blockIdx.x;
   if (status[kStSingular]) return;
@@ -467,7 +492,7 @@ extern "C" int mpcgesv(int64_t n, int32_t p_bits, mpc_mat *A, int32_t *ipiv, mpc
   // solve: forward then backward substitution, every element's operations in the same
   // order as the column-oriented loops (bit-identical results), one launch per step
   const int64_t nrhs = B->cols;
-  constexpr int64_t kSolveBlock = 1024;
+  constexpr int64_t kSolveBlock = 256;   // one block per column up to n = 256, then a launch per step
   if (n > 0 && nrhs > 0 && n <= kSolveBlock) {
     k_lu_solve<<<(unsigned)nrhs, (unsigned)kSolveBlock, 0, st>>>(Am, n, ipiv, Bm, p_bits, L, status);
   } else if (n > 0 && nrhs > 0) {

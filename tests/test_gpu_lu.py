@@ -30,7 +30,8 @@ def _gpu_lu(A, B, p, K, method="3m"):
 
 
 @pytest.mark.parametrize("n,K,p,method,nrhs", [(40, 16, 128, "3m", 1), (23, 1, 192, "4m", 2),
-                                               (33, 8, 256, "4m", 1), (17, 17, 128, "3m", 1)])
+                                               (33, 8, 256, "4m", 1), (17, 17, 128, "3m", 1),
+                                               (24, 8, 512, "4m", 2), (21, 4, 500, "3m", 1)])
 def test_lu_matches_oracle_bit_for_bit(n, K, p, method, nrhs):
     A = si.random_matrix(n, n, p, 800 + n, "uniform")       # no diagonal boost: pivoting happens
     B = si.random_matrix(n, nrhs, p, 900 + n, "uniform")
@@ -103,3 +104,20 @@ def test_baseline_lu_solution_error(n, K, p, method):
             v = exact.to_fraction(exact.component(X, c, i, 0))
             worst = max(worst, abs(v - 1))
     assert worst < Fraction(1, 2 ** (p - 16)), float(worst)
+
+
+@pytest.mark.parametrize("n,p", [(300, 512), (260, 256)])
+def test_per_step_solve_at_register_precisions(n, p):
+    """Between 256 and 1024 unknowns the solve takes one launch per substitution step; at
+    p = 512 and 256 every scalar operation takes the register-resident path.  With the
+    GPU's own factors and interchanges the oracle's substitution gives the same X bit for bit."""
+    from oracle import exact as o1
+    A = si.shifted_diagonal_matrix(n, p, 972 + n)
+    B = si.random_matrix(n, 1, p, 973 + n, "uniform")
+    LU, ipiv, X, st, sing = _gpu_lu(A, B, p, 64, "4m")
+    assert sing == 0 and st["erange"] == 0 and st["uncertified"] == 0
+    lv, bv = o1.matrix_values(LU), o1.matrix_values(B)
+    a = [[(lv[0][i][j], lv[1][i][j]) for j in range(n)] for i in range(n)]
+    b = [[(bv[0][i][0], bv[1][i][0])] for i in range(n)]
+    assert gu.same(X, lu.pack_values(lu.substitute(a, ipiv, b, p), p))
+
