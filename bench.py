@@ -218,31 +218,60 @@ def run_lu(mp, torch, dev, n: int = 2048, p: int = 512, block: int = 128, method
             "note": "A = U + nI (U uniform [-1,1)), x = 1+i, b = RN(Ax) by this library's GEMM"}
 
 
-def run_serving(mp, torch, dev, seed: int = si.SEED_BASE + 5, count: int = 40):
-    """Mixed GEMM (config-3 shapes) and LU (n 128..256) requests with Poisson arrivals."""
+def run_serving(mp, torch, dev, seed: int = si.SEED_BASE + 5, count: int = 1200,
+                gaps_ms=(8.0, 4.0, 2.0), pool: int = 32):
+    """Mixed GEMM (batched-workload shapes) and LU (n 64..256) requests, Poisson arrivals,
+    at several offered loads.
+
+    GEMM operands come from a pool of ``pool`` (shape, p) entries generated once; every
+    request has its own output.  An LU solve overwrites its operands, so each LU request
+    gets fresh device copies of a pooled system before every load."""
     from paper_2307_06072_gb300.serve import Request, Server
     rng = np.random.default_rng(seed)
-    reqs, t = [], 0.0
-    for x in range(count):
-        t += float(rng.exponential(0.004))
-        if x % 6 == 5:
-            n, p = int(rng.choice([128, 256])), int(rng.choice([256, 512]))
-            A = si.shifted_diagonal_matrix(n, p, seed + 10 * x)
-            B = si.random_matrix(n, 1, p, seed + 10 * x + 1)
-            reqs.append(Request(x, "lu", t, mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(B, dev), p,
-                                block=64, work=8.0 * n ** 3 / 3))
-        else:
-            m, k, n = (int(v) for v in np.exp(rng.uniform(np.log(64), np.log(1024), 3)))
-            p = int(rng.choice([256, 512, 1024]))
-            A = si.random_matrix(m, k, p, seed + 10 * x)
-            B = si.random_matrix(k, n, p, seed + 10 * x + 1)
-            reqs.append(Request(x, "gemm", t, mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(B, dev), p,
-                                C=mp.DeviceMatrix.empty(m, n, p, dev), work=8.0 * m * n * k))
-    srv = Server(slots=4, hbm_budget=48 << 30, device=dev)
-    out = srv.run(reqs)
-    out["note"] = (f"{count} requests (every 6th an LU solve, n in {{128, 256}}), Poisson arrivals with a 4 ms "
-                   "mean gap, 4 stream slots, 48 GB budget; latency = completion - arrival")
-    return out
+    gem, lus = [], []
+    for x in range(pool):
+        m, k, n = (int(v) for v in np.exp(rng.uniform(np.log(64), np.log(1024), 3)))
+        p = int(rng.choice([256, 512, 1024]))
+        gem.append((m, k, n, p, mp.DeviceMatrix.from_mpc(si.random_matrix(m, k, p, seed + 10 * x), dev),
+                    mp.DeviceMatrix.from_mpc(si.random_matrix(k, n, p, seed + 10 * x + 1), dev)))
+    for x in range(8):
+        n, p = (64, 128, 256)[x % 3], (256, 512)[x % 2]
+        lus.append((n, p, si.shifted_diagonal_matrix(n, p, seed + 500 + x), si.random_matrix(n, 1, p, seed + 600 + x)))
+    kinds = ["lu" if x % 10 == 9 else "gemm" for x in range(count)]
+    picks = [int(rng.integers(len(lus) if kd == "lu" else len(gem))) for kd in kinds]
+    outs = {x: mp.DeviceMatrix.empty(gem[q][0], gem[q][2], gem[q][3], dev)
+            for x, (kd, q) in enumerate(zip(kinds, picks)) if kd == "gemm"}
+    budget = 48 << 30
+    srv = Server(slots=4, hbm_budget=budget, device=dev)
+    loads = []
+    for gap in gaps_ms:
+        t, reqs = 0.0, []
+        for x, (kd, q) in enumerate(zip(kinds, picks)):
+            t += float(rng.exponential(gap / 1e3))
+            if kd == "lu":
+                n, p, A, B = lus[q]
+                reqs.append(Request(x, "lu", t, mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(B, dev),
+                                    p, block=64, work=8.0 * n ** 3 / 3))
+            else:
+                m, k, n, p, A, B = gem[q]
+                reqs.append(Request(x, "gemm", t, A, B, p, C=outs[x], work=8.0 * m * n * k))
+        torch.cuda.synchronize()
+        srv.batches, srv.max_inflight, srv.peak_in_use = [], 0, 0
+        out = srv.run(reqs)
+        lat_g = np.array([r.latency for r in reqs if r.kind == "gemm" and r.t_done is not None])
+        lat_l = np.array([r.latency for r in reqs if r.kind == "lu" and r.t_done is not None])
+        out.update({"offered_req_s": round(count / t, 1), "mean_gap_ms": gap,
+                    "gemm_p50_ms": float(np.percentile(lat_g, 50) * 1e3),
+                    "gemm_p99_ms": float(np.percentile(lat_g, 99) * 1e3),
+                    "lu_p50_ms": float(np.percentile(lat_l, 50) * 1e3) if lat_l.size else None,
+                    "lu_p99_ms": float(np.percentile(lat_l, 99) * 1e3) if lat_l.size else None})
+        loads.append({k_: (round(v, 3) if isinstance(v, float) else v) for k_, v in out.items()})
+    return {"loads": loads,
+            "note": (f"{count} requests per load (every 10th an LU solve, n in {{64, 128, 256}}, p in {{256, 512}}; "
+                     f"GEMMs m, n, k log-uniform in [64, 1024], p in {{256, 512, 1024}}, operands from a pool of "
+                     f"{pool}), Poisson arrivals at mean gaps {list(gaps_ms)} ms, 4 stream slots each with a "
+                     f"{budget / 4 / 2**30:.0f} GiB workspace reserved at start, at most 64 GEMMs per batched call; "
+                     "latency = completion on the GPU - arrival")}
 
 
 def hbm_stage_rooflines(pl, m, n, k, stages, hbm_gbs, src):

@@ -1,14 +1,17 @@
 """Request loop for mixed complex GEMM and LU-solve requests on one GPU.
 
 Requests arrive over time (their ``arrival`` offsets); operands already live
-on the device.  The loop keeps a few CUDA streams ("slots").  Whenever a slot
-is free it admits waiting requests in arrival order, as long as their device
-memory footprint (the workspace the library will use) fits the HBM budget
-next to what is in flight: waiting GEMMs are admitted together and run as one
-batched call (continuous batching: requests that arrived while others were
-running join the next batch), an LU solve runs alone in its slot.  Work in
-different slots overlaps on the device.  A request's latency runs from its
-arrival to the completion of its work on the GPU.
+on the device.  The loop keeps a few CUDA streams ("slots"), each with a
+workspace of budget / slots bytes allocated once when the server starts, so
+the memory the loop uses is fixed and bounded by the budget.  Whenever a slot
+is free it admits waiting requests in arrival order as long as their
+workspace footprint fits that slot's workspace: waiting GEMMs are admitted
+together and run as one batched call (continuous batching: requests that
+arrived while others were running join the next batch), an LU solve runs
+alone in its slot.  A request whose footprint exceeds a slot's workspace can
+never run and is rejected (counted in the statistics).  Work in different
+slots overlaps on the device.  A request's latency runs from its arrival to
+the completion of its work on the GPU.
 
 Every operation is deterministic (exact arithmetic, one rounding per result),
 so a request's result does not depend on what it ran with.
@@ -16,11 +19,11 @@ so a request's result does not depend on what it ran with.
 from __future__ import annotations
 
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
-from . import _native, batched_workspace, mpcgemm_batched, mpcgesv
+from . import Workspace, _native, batched_workspace, mpcgemm_batched, mpcgesv
 
 
 @dataclass
@@ -50,21 +53,27 @@ class _Flight:
     reqs: list
     event: object
     nbytes: int
-    keep: list = field(default_factory=list)
 
 
 class Server:
-    def __init__(self, slots: int = 4, hbm_budget: int = 32 << 30, max_batch: int = 48, device="cuda"):
+    def __init__(self, slots: int = 4, hbm_budget: int = 32 << 30, max_batch: int = 64, device="cuda"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
         self.budget = int(hbm_budget)
+        self.slot_bytes = (self.budget // slots) & ~255
+        self.workspaces = []
+        for _ in range(slots):                       # the loop's whole device memory, reserved once
+            ws = Workspace(self.device)
+            ws.get(self.slot_bytes)
+            self.workspaces.append(ws)
         self.max_batch = max_batch
         self.in_use = 0
         self.peak_in_use = 0
         self.batches = []         # sizes of the GEMM batches launched
         self.max_inflight = 0
+        self.rejected = []        # requests larger than a slot's workspace
 
     def footprint(self, req: Request) -> int:
         if req.kind == "gemm":
@@ -72,29 +81,30 @@ class Server:
         return int(_native.lib().mpcgesv_workspace_size(req.A.rows, req.p, req.block,
                                                         _native.METHODS[req.method])) + 4 * req.A.rows
 
-    def _launch(self, slot: int, reqs: list, t: float) -> _Flight:
+    def _launch(self, slot: int, reqs: list, t: float, nbytes: int) -> _Flight:
         torch = self.torch
         st = self.streams[slot]
-        nbytes = sum(self.footprint(r) for r in reqs)
-        keep = []
+        ws = self.workspaces[slot]   # admission kept nbytes within it: nothing is allocated here
         with torch.cuda.stream(st):
             if reqs[0].kind == "gemm":
                 problems = [(r.A, r.B, r.C, r.p, r.method, "ozaki") for r in reqs]
-                ws = mpcgemm_batched(problems, stream=st)
+                mpcgemm_batched(problems, workspace=ws, stream=st)
                 self.batches.append(len(reqs))
             else:
                 r = reqs[0]
-                r.ipiv, ws = mpcgesv(r.A, r.B, r.p, r.block, r.method, stream=st)
-            keep.append(ws)
+                r.ipiv, _ = mpcgesv(r.A, r.B, r.p, r.block, r.method, workspace=ws, stream=st)
             ev = torch.cuda.Event()
             ev.record(st)
         for r in reqs:
             r.t_admit = t
-        return _Flight(slot, reqs, ev, nbytes, keep)
+        return _Flight(slot, reqs, ev, nbytes)
 
     def run(self, requests: list) -> dict:
         """Serve all requests; returns latency / throughput statistics."""
-        pending = sorted(requests, key=lambda r: r.arrival)
+        size = {id(r): self.footprint(r) for r in requests}   # planned once per request
+        served = [r for r in requests if size[id(r)] <= self.slot_bytes]
+        self.rejected = [r for r in requests if size[id(r)] > self.slot_bytes]
+        pending = sorted(served, key=lambda r: r.arrival)
         queue: list = []
         flights: list = []
         free = list(range(len(self.streams)))
@@ -115,36 +125,35 @@ class Server:
             while free and queue:
                 head = queue[0]
                 if head.kind == "lu":
-                    need = self.footprint(head)
-                    if flights and self.in_use + need > self.budget:
-                        break
-                    batch = [queue.pop(0)]
-                else:
+                    batch, need = [queue.pop(0)], size[id(head)]
+                else:   # waiting GEMMs in arrival order, as many as fit the slot's workspace
                     batch, need = [], 0
                     for r in list(queue):
                         if r.kind != "gemm" or len(batch) >= self.max_batch:
                             continue
-                        b = self.footprint(r)
-                        if self.in_use + need + b > self.budget and (flights or batch):
+                        b = size[id(r)]
+                        if need + b > self.slot_bytes:
                             continue
                         batch.append(r)
                         need += b
                         queue.remove(r)
-                    if not batch:
-                        break
                 slot = free.pop(0)
                 self.in_use += need
                 self.peak_in_use = max(self.peak_in_use, self.in_use)
-                flights.append(self._launch(slot, batch, time.perf_counter() - t0))
+                flights.append(self._launch(slot, batch, time.perf_counter() - t0, need))
                 self.max_inflight = max(self.max_inflight, len(flights))
                 progressed = True
             if not progressed:
                 time.sleep(0.0002)
         total = time.perf_counter() - t0
-        lat = np.array([r.latency for r in requests])
-        work = sum(r.work for r in requests)
-        return {"requests": len(requests), "seconds": total, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                "p99_ms": float(np.percentile(lat, 99) * 1e3), "throughput_req_s": len(requests) / total,
-                "work_8mnk_s": work / total, "gemm_batches": list(self.batches),
-                "max_in_flight": self.max_inflight,
-                "peak_in_use_gb": round(self.peak_in_use / 1e9, 3), "budget_gb": round(self.budget / 1e9, 3)}
+        lat = np.array([r.latency for r in served]) if served else np.zeros(1)
+        work = sum(r.work for r in served)
+        return {"requests": len(served), "rejected": len(self.rejected), "seconds": total,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "p999_ms": float(np.percentile(lat, 99.9) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+                "throughput_req_s": len(served) / total, "work_8mnk_s": work / total,
+                "gemm_batches": len(self.batches), "mean_gemm_batch": float(np.mean(self.batches)) if self.batches else 0.0,
+                "max_gemm_batch": max(self.batches) if self.batches else 0, "max_in_flight": self.max_inflight,
+                "peak_in_use_gb": round(self.peak_in_use / 1e9, 3),
+                "reserved_gb": round(len(self.streams) * self.slot_bytes / 1e9, 3),
+                "budget_gb": round(self.budget / 1e9, 3)}

@@ -1,8 +1,9 @@
-"""Serving loop: mixed GEMM / LU requests, continuous batching, HBM admission.
+"""Serving loop: mixed GEMM / LU requests, continuous batching, per-slot workspaces.
 
 Every request's result must be bit for bit the same served in the mix as run
 alone, the loop must overlap work (several requests in flight), batch GEMMs
-that wait together, and never exceed its memory budget while others run.
+that wait together, allocate no device memory after it starts beyond the
+results' pivot vectors, and keep each batch within its slot's workspace.
 """
 import numpy as np
 import pytest
@@ -47,12 +48,13 @@ def test_results_are_the_same_alone_and_in_the_mix():
     M = gu.mp()
     from paper_2307_06072_gb300.serve import Server
     reqs, host = _requests(M, 4000)
-    srv = Server(slots=3, hbm_budget=300 << 20)
+    srv = Server(slots=3, hbm_budget=3 << 30)
     stats = srv.run(reqs)
     torch.cuda.synchronize()
     assert stats["requests"] == len(reqs) and all(r.t_done is not None for r in reqs)
     assert stats["max_in_flight"] >= 2               # work overlapped on the device
-    assert max(stats["gemm_batches"]) >= 2           # waiting GEMMs were batched
+    assert stats["max_gemm_batch"] >= 2              # waiting GEMMs were batched
+    assert stats["rejected"] == 0
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
     for r, (kind, A, B, p) in zip(reqs, host):
         if kind == "gemm":
@@ -67,11 +69,23 @@ def test_results_are_the_same_alone_and_in_the_mix():
             assert np.array_equal(r.ipiv.cpu().numpy(), ipiv.cpu().numpy())
 
 
-def test_admission_respects_the_budget():
+def test_admission_respects_the_slot_workspaces():
+    import torch
     M = gu.mp()
     from paper_2307_06072_gb300.serve import Server
     reqs, _ = _requests(M, 5000)
-    biggest = max(Server(slots=1).footprint(r) for r in reqs)
-    srv = Server(slots=4, hbm_budget=biggest + 1)
-    srv.run(reqs)
-    assert srv.peak_in_use <= max(srv.budget, biggest)
+    probe = Server(slots=1, hbm_budget=1 << 20)
+    sizes = sorted(probe.footprint(r) for r in reqs)
+    slot = sizes[-2] + 256                       # every request fits but the largest
+    srv = Server(slots=3, hbm_budget=3 * slot)
+    ptrs = [w.ptr for w in srv.workspaces]
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    stats = srv.run(reqs)
+    torch.cuda.synchronize()
+    assert stats["rejected"] == (1 if sizes[-1] > srv.slot_bytes else 0)
+    assert stats["requests"] + stats["rejected"] == len(reqs)
+    assert [w.ptr for w in srv.workspaces] == ptrs and all(w.nbytes == srv.slot_bytes for w in srv.workspaces)
+    assert srv.peak_in_use <= srv.budget
+    lu_pivots = sum(4 * max(r.A.rows, 1) for r in reqs if r.kind == "lu" and r.ipiv is not None)
+    assert torch.cuda.memory_allocated() - before <= lu_pivots + (1 << 16)   # only the pivot vectors
