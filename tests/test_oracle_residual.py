@@ -1,0 +1,442 @@
+"""Pins of O2r, the residual split of Alg. 2 (a slice unit re-measured before every slice).
+
+The pins tie the oracle to things other than itself:
+
+* the paper's own formula: Alg. 2 takes a slice as (A + tau) - tau in S-bit arithmetic
+  with tau set by ceil(log2 mu) + beta; executed here with mpmath at a precision S
+  (beta = S - w, so a slice carries w bits) it must give the oracle's units and digits,
+  ties included (tau as the usual extraction constant 3 2^(ceil(log2 mu) + beta - 1):
+  the printed power of two rounds negative entries at half the unit, which a test
+  shows);
+* the arithmetic definition: slices and remainder reassemble the input exactly, every
+  digit is within 2^(w-1), every unit is the re-measured ceil(log2 max |R|) (checked
+  with Fractions), and units fall by at least w per slice;
+* the exact product: with every pair kept and a lossless split, the pair products
+  weighted by their units are T; the accumulator differs from the kept pairs' sum only
+  by its counted truncations; the bound holds entry by entry; the output equals O1;
+* the cases the variant exists for: a line whose residual collapses skips grid positions,
+  and an imaginary part 2^-100 below the real part keeps its full precision (the default
+  split needs the exact fallback there).
+Planted slips in the oracle (floor digits, no re-measurement, a unit one bit too fine, a
+wrong product sign, a window anchored on the smaller product) are each caught.
+"""
+from fractions import Fraction
+
+import mpmath
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import exact, ozaki, residual
+
+
+def _frac(N, x):
+    return Fraction(N) * (Fraction(2) ** x)
+
+
+def _pack(vals_re, vals_im, p):
+    return exact.pack(vals_re, vals_im, p)
+
+
+def _gap_matrix(rows, cols, p, seed, gap_at, gap_len, hi_bits, real_only=False):
+    """Row i: every element (H 2^(gap_len) + Lo) 2^x_i with H of hi_bits bits and Lo below
+    the gap, so all elements of the row have zero bits at the same absolute positions
+    [x_i + lo_bits, x_i + lo_bits + gap_len); gap_at[i] = lo_bits."""
+    rng = np.random.default_rng(seed)
+    re = [[None] * cols for _ in range(rows)]
+    im = [[None] * cols for _ in range(rows)]
+    for i in range(rows):
+        lo_bits = gap_at[i]
+        for j in range(cols):
+            for out in (re, im):
+                if out is im and real_only:
+                    out[i][j] = (0, 0)
+                    continue
+                H = int(rng.integers(1 << (hi_bits - 1), 1 << hi_bits))
+                Lo = int.from_bytes(rng.bytes((lo_bits + 7) // 8), "little") & ((1 << lo_bits) - 1)
+                N = (H << (gap_len + lo_bits)) + Lo
+                N = -N if rng.integers(0, 2) else N
+                x = -(hi_bits + gap_len + lo_bits)
+                out[i][j] = exact.round_nearest_even((N, x), p)
+    return _pack(re, im, p)
+
+
+def _line_values(mat, c, i):
+    return [exact.component(mat, c, i, l) for l in range(mat.cols)]
+
+
+# ------------------------------------------------------------------ the paper's formula
+
+def _alg2_float_slices(vals, s, w, tau_pow2=False):
+    """Alg. 2's split of one line, literally: mu, tau, slice = (R + tau) - tau at precision
+    S, R := R - slice (exact).  Returns (units, slices in units of 2^unit).
+
+    The paper prints tau = 2^(ceil(log2 mu) + beta).  Then R + tau falls into the binade
+    below tau whenever R < 0 and is rounded at half the unit, so negative entries keep one
+    bit more than positive ones (``tau_pow2=True`` shows this).  The library reads the
+    extraction as symmetric rounding at unit ulp(tau), which is what the usual extraction
+    constant tau = 3 2^(ceil(log2 mu) + beta - 1) gives: R + tau then stays in tau's binade
+    for every |R| <= mu."""
+    nz = [(N, x) for N, x in vals if N != 0]
+    c0 = max(x + (abs(N) - 1).bit_length() for N, x in nz)
+    zmin = min(x for _, x in nz)
+    b_floor = c0 - (w - 1) - w * (s - 1)
+    S = (c0 - min(zmin, b_floor)) + 2 * w + 16     # every residual and slice is exact at this precision
+    beta = S - w
+    units, digits = [], []
+    with mpmath.workprec(S):
+        R = [mpmath.ldexp(mpmath.mpf(N), x) for N, x in vals]
+        for _ in range(s):
+            mu = max(abs(r) for r in R)
+            if mu == 0:
+                units.append(None)
+                digits.append([0] * len(vals))
+                continue
+            man, e = mpmath.frexp(mu)                 # mu = man 2^e, 1/2 <= man < 1
+            c = e if man > 0.5 else e - 1             # ceil(log2 mu)
+            tau = mpmath.ldexp(1, c + beta) if tau_pow2 else mpmath.ldexp(3, c + beta - 1)
+            sl = [(r + tau) - tau for r in R]          # S-bit round to nearest, ties to even
+            u = c - (w - 1)
+            units.append(u)
+            digits.append([mpmath.ldexp(v, -u) for v in sl])
+            R = [r - v for r, v in zip(R, sl)]
+    return units, [[int(v) if v == int(v) else float(v) for v in row] for row in digits]
+
+
+def _tie_line(w):
+    """Elements that sit exactly on midpoints of the first slice's grid (both parities)."""
+    # row max 2^10 - 1 -> c = 10, unit 2^(10 - (w-1)); x = (2m+1) * unit / 2 are ties
+    u = 10 - (w - 1)
+    vals = [((1 << 10) - 1, 0)]
+    for mult in (1, 3, 5, 7, -1, -3, 9, 11):
+        vals.append((mult, u - 1))
+    return vals
+
+
+@pytest.mark.parametrize("w", [8, 9])
+@pytest.mark.parametrize("case", ["uniform", "uniform_exp", "gap", "ties"])
+def test_slices_follow_the_float_formula_of_alg2(w, case):
+    p, s = 192, 26
+    if case == "ties":
+        lines = [_tie_line(w)]
+    elif case == "gap":
+        M = _gap_matrix(4, 12, p, 5, [20, 35, 50, 70], 60, 30)
+        lines = [_line_values(M, c, i) for c in range(2) for i in range(M.rows)]
+    else:
+        M = si.random_matrix(4, 12, p, 7, case)
+        lines = [_line_values(M, c, i) for c in range(2) for i in range(M.rows)]
+    for vals in lines:
+        L = residual.split_line(vals, s, w)
+        units, digits = _alg2_float_slices(vals, s, w)
+        assert L.units == units
+        assert L.digits == digits
+
+
+def test_a_power_of_two_tau_rounds_negative_entries_at_half_the_unit():
+    """The reading above, shown: with tau = 2^(ceil(log2 mu) + beta) exactly as printed, a
+    negative entry's first slice is rounded at half the unit (a half-integer digit),
+    while the positive entry of the same magnitude is not."""
+    w = 9
+    c = 10
+    u = c - (w - 1)
+    vals = [((1 << 10) - 1, 0), (-5, u - 4), (5, u - 4)]   # -+5/16 of a unit
+    units, digits = _alg2_float_slices(vals, 2, w, tau_pow2=True)
+    assert units[0] == u
+    assert digits[0][1] == -0.5 and digits[0][2] == 0           # half unit for the negative one
+    units, digits = _alg2_float_slices(vals, 2, w)
+    assert digits[0][1] == 0 and digits[0][2] == 0              # symmetric: RNE(-+5/16) = 0
+    assert residual.split_line(vals, 2, w).digits[0][1:] == [0, 0]
+
+
+# ------------------------------------------------------------------ arithmetic definition
+
+@pytest.mark.parametrize("w", [8, 9])
+@pytest.mark.parametrize("case", ["uniform_exp", "gap", "zero_frac"])
+def test_slices_reassemble_and_units_are_remeasured(w, case):
+    p, s = 256, 30
+    if case == "gap":
+        M = _gap_matrix(5, 16, p, 9, [10, 40, 80, 5, 120], 90, 40)
+    elif case == "zero_frac":
+        M = si.random_matrix(5, 16, p, 11, "uniform_exp", zero_frac=0.5)
+    else:
+        M = si.random_matrix(5, 16, p, 13, "uniform_exp")
+    for c in range(2):
+        for i in range(M.rows):
+            vals = _line_values(M, c, i)
+            L = residual.split_line(vals, s, w)
+            if all(N == 0 for N, _ in vals):
+                assert L.units == [None] * s
+                continue
+            R = [_frac(N, x) for N, x in vals]
+            prev = None
+            for t in range(s):
+                b = L.units[t]
+                if b is None:
+                    assert all(d == 0 for d in L.digits[t])
+                    continue
+                mu = max(abs(r) for r in R)
+                # ceil(log2 mu) by comparisons, then the floor clamp
+                cmu = 0
+                while Fraction(2) ** cmu < mu:
+                    cmu += 1
+                while Fraction(2) ** (cmu - 1) >= mu:
+                    cmu -= 1
+                assert b == cmu - (w - 1)
+                if prev is not None:
+                    assert b <= prev - w
+                prev = b
+                for l, d in enumerate(L.digits[t]):
+                    assert abs(d) <= 1 << (w - 1)
+                    R[l] -= d * Fraction(2) ** b
+            for l in range(len(vals)):
+                assert R[l] == _frac(L.remainder[l], L.Z)
+                assert abs(R[l]) <= Fraction(2) ** (L.floor - 1)
+
+
+def test_regular_lines_step_by_exactly_w():
+    """Full-precision random lines (k >= 64): every residual's maximum lies above a quarter
+    unit, so every unit is the previous one minus w (the default split's grid)."""
+    p, s, w = 512, 60, 9
+    M = si.random_matrix(3, 64, p, 17, "uniform_exp")
+    for c in range(2):
+        for i in range(M.rows):
+            L = residual.split_line(_line_values(M, c, i), s, w)
+            b0 = L.units[0]
+            assert L.units == [b0 - w * t for t in range(s)]
+
+
+def test_a_collapsing_residual_skips_grid_positions():
+    """Rows whose elements share a run of 90 zero bits: the unit jumps over the run, so the
+    s slices reach below it and every row is cut without remainder, while the default split
+    with the same s (a fixed grid of ws - 1 bits below the row maximum) leaves bits behind."""
+    p, s, w = 256, 14, 9
+    M = _gap_matrix(4, 16, p, 19, [20, 30, 40, 25], 90, 40, real_only=True)
+    sp = residual.split_operand(M, s, "A", w)
+    for i in range(M.rows):
+        u = [sp.units["re"][t][i] for t in range(s) if sp.units["re"][t][i] is not None]
+        steps = [u[t] - u[t + 1] for t in range(len(u) - 1)]
+        assert max(steps) > w + 60
+    assert all(sp.lossless)
+    common = ozaki.split_operand(M, s, "A", "4m", w)
+    assert not all(common.lossless)
+
+
+# ------------------------------------------------------------------ the exact product
+
+def _pairs_sum(res, i, j, comp, keep_all=True):
+    """sum over kept pairs of sign G 2^(u_a + u_b), exactly."""
+    tot = Fraction(0)
+    for (pr, q, t, live), G in zip(res.table, res.products):
+        c, sign = residual.ENTERS[pr]
+        if c != comp or not live:
+            continue
+        pa, pb = residual.OPERANDS[pr]
+        ua, ub = res.splitA.units[pa][t][i], res.splitB.units[pb][q - t][j]
+        if ua is None or ub is None:
+            continue
+        tot += sign * int(G[i, j]) * Fraction(2) ** (ua + ub)
+    return tot
+
+
+@pytest.mark.parametrize("case", ["uniform", "im_small", "gap"])
+def test_all_pairs_of_a_lossless_split_are_the_exact_product(case):
+    p, s = 64, 20
+    if case == "gap":
+        A = _gap_matrix(3, 5, p, 23, [5, 9, 3], 40, 12)
+        B = _gap_matrix(4, 5, p, 24, [7, 2, 6, 8], 40, 12).transpose()
+    else:
+        A = si.random_matrix(3, 5, p, 25, "uniform")
+        B = si.random_matrix(5, 4, p, 26, "uniform")
+        if case == "im_small":
+            A.exp[1] = np.where(A.limb[1, -1] != 0, A.exp[1] - 100, A.exp[1])
+    res = residual.ozaki_cgemm_residual(A, B, p, s=s, Q=2 * s - 2)
+    assert all(res.splitA.lossless) and all(res.splitB.lossless)
+    re, im = exact.exact_cgemm(A, B, "4m")
+    for i in range(A.rows):
+        for j in range(B.cols):
+            for comp, T in (("re", re), ("im", im)):
+                assert _pairs_sum(res, i, j, comp) == exact.to_fraction(T[i][j])
+
+
+@pytest.mark.parametrize("case", ["uniform_exp", "im_small", "gap"])
+def test_accumulator_differs_from_the_kept_pairs_only_by_counted_truncations(case):
+    p, s = 128, 12
+    if case == "gap":
+        A = _gap_matrix(4, 6, p, 27, [5, 20, 3, 30], 50, 20)
+        B = _gap_matrix(3, 6, p, 28, [7, 2, 25], 50, 20).transpose()
+    else:
+        A = si.random_matrix(4, 6, p, 29, "uniform_exp")
+        B = si.random_matrix(6, 3, p, 30, "uniform_exp")
+        if case == "im_small":
+            B.exp[1] = np.where(B.limb[1, -1] != 0, B.exp[1] - 100, B.exp[1])
+    res = residual.ozaki_cgemm_residual(A, B, p, s=s)
+    for i in range(A.rows):
+        for j in range(B.cols):
+            for comp in ("re", "im"):
+                lo = res.lo[comp][i, j]
+                if lo is None:
+                    continue
+                acc = Fraction(int(res.acc[comp][i, j])) * Fraction(2) ** lo
+                gap = _pairs_sum(res, i, j, comp) - acc
+                n = int(res.trunc[comp][i, j])
+                assert 0 <= gap < (n if n else 1) * Fraction(2) ** lo
+                if n == 0:
+                    assert gap == 0
+
+
+@pytest.mark.parametrize("case", ["uniform_exp", "im_small", "gap"])
+def test_term_offsets_fit_the_accumulator_window(case):
+    """Every term offset is <= w Q: the window's top, so that the accumulator width of the
+    default split (w Q bits plus headroom) holds every sum."""
+    p = 128
+    if case == "gap":
+        A = _gap_matrix(4, 6, p, 41, [5, 20, 3, 30], 50, 20)
+        B = _gap_matrix(3, 6, p, 42, [7, 2, 25], 50, 20).transpose()
+    else:
+        A = si.random_matrix(4, 6, p, 43, "uniform_exp")
+        B = si.random_matrix(6, 3, p, 44, "uniform_exp")
+        if case == "im_small":
+            A.exp[1] = np.where(A.limb[1, -1] != 0, A.exp[1] - 100, A.exp[1])
+    res = residual.ozaki_cgemm_residual(A, B, p)
+    assert res.max_offset is not None and res.max_offset <= res.params.w * res.params.Q
+
+
+@pytest.mark.parametrize("case,guard", [("uniform_exp", 0), ("uniform", 4), ("im_small", 0), ("gap", 0)])
+def test_bound_holds_on_every_entry(case, guard):
+    p = 96
+    if case == "gap":
+        A = _gap_matrix(5, 7, p, 31, [5, 20, 3, 30, 12], 50, 20)
+        B = _gap_matrix(4, 7, p, 32, [7, 2, 25, 8], 50, 20).transpose()
+    else:
+        A = si.random_matrix(5, 7, p, 33, "uniform_exp" if case != "uniform" else "uniform")
+        B = si.random_matrix(7, 4, p, 34, "uniform_exp" if case != "uniform" else "uniform")
+        if case == "im_small":
+            A.exp[1] = np.where(A.limb[1, -1] != 0, A.exp[1] - 100, A.exp[1])
+    res = residual.ozaki_cgemm_residual(A, B, p, guard=guard)
+    beta = residual.bound_exponent(res.params)
+    re, im = exact.exact_cgemm(A, B, "4m")
+    for i in range(A.rows):
+        for j in range(B.cols):
+            for comp, T in (("re", re), ("im", im)):
+                lo = res.lo[comp][i, j]
+                if lo is None:
+                    assert exact.to_fraction(T[i][j]) == 0
+                    continue
+                b = residual.entry_bound(res.params, res.splitA, res.splitB, i, j, comp,
+                                         int(res.trunc[comp][i, j]))
+                err = abs(Fraction(int(res.acc[comp][i, j])) * Fraction(2) ** lo - exact.to_fraction(T[i][j]))
+                assert err <= b * Fraction(2) ** (beta + lo)
+
+
+@pytest.mark.parametrize("case", ["uniform", "uniform_exp", "im_small", "gap", "zeros", "real"])
+def test_output_equals_o1(case):
+    p = 160
+    if case == "gap":
+        A = _gap_matrix(6, 8, p, 35, [5, 20, 3, 30, 12, 40], 50, 20)
+        B = _gap_matrix(5, 8, p, 36, [7, 2, 25, 8, 4], 50, 20).transpose()
+    else:
+        dist = "uniform" if case in ("uniform", "real") else "uniform_exp"
+        zf = 0.3 if case == "zeros" else 0.0
+        A = si.random_matrix(6, 8, p, 37, dist, zero_frac=zf)
+        B = si.random_matrix(8, 5, p, 38, dist, zero_frac=zf)
+        if case == "zeros":
+            A.limb[:, :, 2, :] = 0          # an all-zero row of A
+            B.limb[:, :, :, 1] = 0          # an all-zero column of B
+        if case == "im_small":
+            A.exp[1] = np.where(A.limb[1, -1] != 0, A.exp[1] - 100, A.exp[1])
+            B.exp[1] = np.where(B.limb[1, -1] != 0, B.exp[1] - 100, B.exp[1])
+        if case == "real":
+            A.limb[1] = 0
+            B.limb[1] = 0
+    ref = exact.rounded_cgemm(A, B, p)
+    for guard in (0, 40):
+        res = residual.ozaki_cgemm_residual(A, B, p, guard=guard)
+        assert exact.equal_arrays(res.C, ref)
+
+
+def test_small_imaginary_parts_keep_their_precision():
+    """Im = 2^-100 Re in magnitude: every part of every line has its own re-measured units,
+    so every component is certified; the default split at the same s cannot certify the
+    imaginary components and recomputes them exactly."""
+    p = 128
+    A = si.random_matrix(6, 10, p, 39, "uniform")
+    B = si.random_matrix(10, 5, p, 40, "uniform")
+    A.exp[1] = np.where(A.limb[1, -1] != 0, A.exp[1] - 100, A.exp[1])
+    B.exp[1] = np.where(B.limb[1, -1] != 0, B.exp[1] - 100, B.exp[1])
+    res = residual.ozaki_cgemm_residual(A, B, p)
+    assert res.certified.all()
+    common = ozaki.ozaki_cgemm(A, B, p, "4m", s=res.params.s)
+    assert not common.certified[1].any()
+
+
+# ------------------------------------------------------------------ planted slips
+
+def _pins_pass():
+    try:
+        for w in (8, 9):
+            for case in ("uniform_exp", "gap", "ties"):
+                test_slices_follow_the_float_formula_of_alg2(w, case)
+            test_slices_reassemble_and_units_are_remeasured(w, "gap")
+        test_regular_lines_step_by_exactly_w()
+        test_a_collapsing_residual_skips_grid_positions()
+        test_accumulator_differs_from_the_kept_pairs_only_by_counted_truncations("im_small")
+        test_term_offsets_fit_the_accumulator_window("im_small")
+        test_bound_holds_on_every_entry("uniform_exp", 0)
+        test_bound_holds_on_every_entry("im_small", 0)
+        for case in ("uniform", "im_small", "gap"):
+            test_output_equals_o1(case)
+    except AssertionError:
+        return False
+    return True
+
+
+def _plant(m, name):
+    orig_split = residual.split_line
+    if name == "floor_digits":          # digits truncated (floor) instead of rounded to nearest
+        m.setattr(residual, "rne_quotient", lambda r, sh: r >> sh)
+    elif name == "no_remeasure":        # units step by w from the first one, never re-measured
+        def split(vals, s, w):
+            L = orig_split(vals, s, w)
+            if L.c0 is None:
+                return L
+            return orig_split_fixed(vals, s, w)
+
+        def orig_split_fixed(vals, s, w):
+            nz = [(N, x) for N, x in vals if N != 0]
+            c0 = max(residual.ceil_log2_abs(N, x) for N, x in nz)
+            b_floor = c0 - (w - 1) - w * (s - 1)
+            Z = min(min(x for _, x in nz), b_floor)
+            R = [N << (x - Z) if N != 0 else 0 for N, x in vals]
+            units, digits = [], []
+            for t in range(s):
+                b = c0 - (w - 1) - w * t
+                d = [residual.rne_quotient(r, b - Z) for r in R]
+                R = [r - (dd << (b - Z)) for r, dd in zip(R, d)]
+                units.append(b)
+                digits.append(d)
+            return residual.LineSplit(units, digits, R, Z, c0, b_floor)
+        m.setattr(residual, "split_line", split)
+    elif name == "log_floor":           # c_t = floor(log2 mu) instead of ceil: digits may reach 2^w
+        m.setattr(residual, "ceil_log2_int", lambda v: v.bit_length() - 1)
+    elif name == "ii_sign":             # Re = rr + ii
+        m.setattr(residual, "ENTERS", dict(residual.ENTERS, ii=("re", 1)))
+    elif name == "window_min":          # window anchored on the smaller product (min, not max)
+        def window(spA, spB, i, j, comp, prm):
+            best = None
+            for pr in residual.PRODUCTS:
+                if residual.ENTERS[pr][0] != comp:
+                    continue
+                pa, pb = residual.OPERANDS[pr]
+                ba, bb = spA.anchor(pa, i), spB.anchor(pb, j)
+                if ba is not None and bb is not None:
+                    best = ba + bb if best is None else min(best, ba + bb)
+            return None if best is None else best - prm.w * prm.Q
+        m.setattr(residual, "window_low", window)
+
+
+@pytest.mark.parametrize("name", ["floor_digits", "no_remeasure", "log_floor", "ii_sign", "window_min"])
+def test_planted_slips_are_caught(monkeypatch, name):
+    with monkeypatch.context() as m:
+        _plant(m, name)
+        assert not _pins_pass(), f"planted slip {name!r} went unnoticed"
+    assert _pins_pass()
