@@ -141,15 +141,16 @@ def shifted_part(mat, c: int, by: int):
     return out
 
 
-def run_per_part(mp, torch, dev, stream, n: int = 512, p: int = 512, shift: int = -100, steps: int = 3):
-    """The per-part split against the default one when every imaginary part is 2^shift
-    times the size of the real parts: times, stage times (the default split sends every
-    imaginary component to the exact fallback), part offsets, kept pairs, oracle check."""
+def run_split_variants(mp, torch, dev, stream, n: int = 512, p: int = 512, shift: int = -100, steps: int = 3):
+    """The per-part and the residual split (Alg. 2 with the unit re-measured before every
+    slice) against the default one when every imaginary part is 2^shift times the size of
+    the real parts: times, stage times (the default split sends every imaginary component
+    to the exact fallback), part offsets, kept pairs, oracle check."""
     A = shifted_part(si.random_matrix(n, n, p, si.SEED_BASE + 6, "uniform_exp"), 1, shift)
     B = shifted_part(si.random_matrix(n, n, p, si.SEED_BASE + 1006, "uniform_exp"), 1, shift)
     dA, dB = mp.DeviceMatrix.from_mpc(A, dev), mp.DeviceMatrix.from_mpc(B, dev)
     out = {"m": n, "n": n, "k": n, "p_bits": p, "method": "4m", "imaginary_scale": f"2^{shift}"}
-    for split in ("common", "per_part"):
+    for split in ("common", "per_part", "residual"):
         dC = mp.DeviceMatrix.empty(n, n, p, dev)
         prm = {"split": split}
         ws = mp.Workspace(dev)
@@ -179,8 +180,12 @@ def run_per_part(mp, torch, dev, stream, n: int = 512, p: int = 512, shift: int 
         if split == "per_part":
             out[split]["part_offsets_z"] = {"A_re": 2048 - int(zw[0]), "A_im": 2048 - int(zw[1]),
                                             "B_re": 2048 - int(zw[2]), "B_im": 2048 - int(zw[3])}
+        if split == "residual":
+            out[split]["pair_batch"] = pl["pair_batch"]
+            out[split]["launches"] = pl["launches"]
         del ws, dC
-    out["speedup_per_part_vs_common"] = round(out["common"]["ms_per_step"] / out["per_part"]["ms_per_step"], 1)
+    for split in ("per_part", "residual"):
+        out[f"speedup_{split}_vs_common"] = round(out["common"]["ms_per_step"] / out[split]["ms_per_step"], 1)
     return out
 
 
@@ -587,7 +592,7 @@ def run_ours(args):
                                                               known[f"plain_{mt}"]["value"], 2)
             extras["precision_sweep"] = run_sweep(mp, torch, dev, stream, ws, SWEEP, skip=args.workload, known=known)
         if not args.no_sweep and ws_ == 1:
-            extras["per_part_split"] = run_per_part(mp, torch, dev, stream)
+            extras["split_variants"] = run_split_variants(mp, torch, dev, stream)
         if not args.no_batched:
             extras["batched_c3"] = run_batched(mp, torch, dev, stream, 3, 3)
         if not args.no_lu:

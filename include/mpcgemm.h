@@ -75,7 +75,7 @@ enum { MPC_4M = 0, MPC_3M = 1 };          /* Eq. (4m_way) / Eq. (3m_way) */
 enum { MPC_PLAIN = 0, MPC_OZAKI = 1 };    /* Eq. (simple_triple_loop) / Alg. 2 */
 /* Split of the Ozaki path: one exponent per row / column for both parts (default), or
  * the per-part split of Alg. 2 (4M only; see mpc_oz_params.split). */
-enum { MPC_SPLIT_COMMON = 0, MPC_SPLIT_PER_PART = 1 };
+enum { MPC_SPLIT_COMMON = 0, MPC_SPLIT_PER_PART = 1, MPC_SPLIT_RESIDUAL = 2 };
 /* Slice-GEMM kernels (value 3 is not used and is rejected). */
 enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2, MPC_KERNEL_TCGEN05_2SM = 4,
        MPC_KERNEL_TCGEN05_N128 = 5 };
@@ -145,6 +145,24 @@ typedef struct mpc_mat {
  *               loses about D/w of them to leading zeros, and its rounding then
  *               needs the exact fallback); when no part is smaller it is the
  *               default split.  The result is the same correctly rounded product.
+ *               MPC_SPLIT_RESIDUAL (2, 4M only, else MPC_EINVAL; not in batched calls):
+ *               Alg. 2 as printed (Sec. III-C): every real part of every row of A
+ *               (column of B) is cut slice after slice, and before each slice the
+ *               largest magnitude mu left in the line is measured again; the slice is
+ *               the residual rounded to nearest (ties to even) at the unit
+ *               2^(ceil(log2 mu) - (w - 1)), so a line whose residual collapses skips
+ *               grid positions.  (The paper's tau is a power of two, which rounds
+ *               negative residuals at half that unit; the extraction is read as
+ *               symmetric, i.e. tau = 3 2^(k-1).)  The slices of one level then sit at
+ *               different units in different lines, so every kept pair (t, u),
+ *               t + u <= Q, is its own exact product (max_group is ignored), and the
+ *               accumulation adds each product at its own per-entry offset.  The pair
+ *               products are streamed through a buffer of mpc_plan.pair_batch planes
+ *               (whole levels at a time), so the workspace stays bounded; the exact
+ *               accumulators live in the workspace between batches.  Same correctly
+ *               rounded product.
+ *   pair_planes residual split: planes in the pair-product buffer (0 -> about 32 GiB
+ *               worth, at least one level, at most all pairs); other splits ignore it.
  */
 typedef struct mpc_oz_params {
     int32_t guard_bits;
@@ -156,7 +174,8 @@ typedef struct mpc_oz_params {
     int32_t wait_limit_cycles;
     int32_t dump_accumulators;
     int32_t split;
-    int32_t reserved[3];
+    int32_t pair_planes;
+    int32_t reserved[2];
 } mpc_oz_params;
 
 /*
@@ -182,13 +201,17 @@ typedef struct mpc_plan {
     uint64_t off_digits_a, off_digits_b, off_groups, off_group_table;
     uint64_t off_fallback, fallback_capacity, off_fb_scratch, fb_scratch_limbs, fb_threads;
     uint64_t off_acc_dump;        /* accumulator dump (dump_accumulators), else 0 */
-    uint64_t off_unused;          /* 0 */
+    uint64_t off_units;           /* residual split (else 0): slice units int32 [part][slice][row of A],
+                                     then [part][slice][column of B] (INT32_MIN: a zero slice); then,
+                                     256-byte aligned, the accumulator words between batches
+                                     [comp][acc_slots][m n] u32, the truncation counts [comp][m n] u32,
+                                     and B copied K-major (sign, exp, limb planes of n x k) */
     uint64_t ws_bytes;
     int32_t launches;             /* kernel launches one call makes */
     int32_t digit_bits;           /* Ozaki: bits per digit w (8 or 9); plain: 28 */
     uint64_t off_group_order;     /* groups ordered by descending level */
     int32_t split;                /* MPC_SPLIT_* */
-    int32_t reserved_plan;
+    int32_t pair_batch;           /* residual split: planes per pair-product batch (off_groups), else 0 */
 } mpc_plan;
 
 /*
@@ -198,7 +221,10 @@ typedef struct mpc_plan {
  *   ev[0] call start, ev[1] after the split (row/column exponents, digits or
  *   fixed-point operands), ev[2] after the slice products (Ozaki) or the plain
  *   GEMM, ev[3] after the accumulation (plain: combination) and rounding,
- *   ev[4] after the exact fallback.  ev[5..7] unused.
+ *   ev[4] after the exact fallback.  ev[5..7] unused.  With the residual split the
+ *   products and the accumulation alternate batch by batch: ev[2] is recorded
+ *   before the last batch's accumulation, so earlier batches' accumulations count
+ *   in the slice-product stage.
  */
 typedef struct mpc_stage_events {
     void *ev[8];

@@ -35,7 +35,7 @@ class OzParams(ctypes.Structure):
     _fields_ = [("guard_bits", ctypes.c_int32), ("slices", ctypes.c_int32),
                 ("cut_level", ctypes.c_int32), ("kernel", ctypes.c_int32), ("max_group", ctypes.c_int32),
                 ("digit_bits", ctypes.c_int32), ("wait_limit_cycles", ctypes.c_int32), ("dump_accumulators", ctypes.c_int32),
-                ("split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("split", ctypes.c_int32), ("pair_planes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class MpcProblem(ctypes.Structure):
@@ -58,9 +58,9 @@ class Plan(ctypes.Structure):
                 ("off_groups", ctypes.c_uint64), ("off_group_table", ctypes.c_uint64),
                 ("off_fallback", ctypes.c_uint64), ("fallback_capacity", ctypes.c_uint64),
                 ("off_fb_scratch", ctypes.c_uint64), ("fb_scratch_limbs", ctypes.c_uint64),
-                ("fb_threads", ctypes.c_uint64), ("off_acc_dump", ctypes.c_uint64), ("off_unused", ctypes.c_uint64),
+                ("fb_threads", ctypes.c_uint64), ("off_acc_dump", ctypes.c_uint64), ("off_units", ctypes.c_uint64),
                 ("ws_bytes", ctypes.c_uint64), ("launches", ctypes.c_int32), ("digit_bits", ctypes.c_int32),
-                ("off_group_order", ctypes.c_uint64), ("split", ctypes.c_int32), ("reserved_plan", ctypes.c_int32)]
+                ("off_group_order", ctypes.c_uint64), ("split", ctypes.c_int32), ("pair_batch", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         out = {}
@@ -142,14 +142,15 @@ def check(code: int) -> int:
     return code
 
 
-SPLITS = {"common": 0, "per_part": 1}
+SPLITS = {"common": 0, "per_part": 1, "residual": 2}
 
 
 def oz_params(guard_bits=0, slices=0, cut_level=0, kernel="auto", max_group=0, digit_bits=0,
-              wait_limit_cycles=0, dump_accumulators=0, split="common") -> OzParams:
+              wait_limit_cycles=0, dump_accumulators=0, split="common", pair_planes=0) -> OzParams:
     return OzParams(int(guard_bits), int(slices), int(cut_level), KERNELS[kernel] if isinstance(kernel, str)
                     else int(kernel), int(max_group), int(digit_bits), int(wait_limit_cycles),
-                    int(dump_accumulators), SPLITS[split] if isinstance(split, str) else int(split))
+                    int(dump_accumulators), SPLITS[split] if isinstance(split, str) else int(split),
+                    int(pair_planes))
 
 
 def exported_symbols():

@@ -31,6 +31,36 @@ struct Plan {
   long long wait_limit;   // cycles per barrier wait of the tcgen05 kernels (0: default)
 };
 
+constexpr uint64_t kPairBufferBytes = 32ull << 30;   // residual split: default pair-product buffer
+
+// Residual split: the pair products are computed and accumulated batch by batch; a batch is
+// a run of whole (product, level) groups of table entries holding at most pair_batch planes.
+// Calls f(g0, g1, first, last) for every batch [g0, g1) in table order; returns the count.
+template <class F>
+int for_each_pair_batch(const Plan &pl, F f) {
+  const mpc_plan &P = pl.pub;
+  const int total = P.n_groups_total, cap = P.pair_batch;
+  int g0 = 0, g = 0, nb = 0;
+  for (int x = 0; x < 4; ++x) {
+    const ProductDesc &d = pl.prod[x];
+    const int qhi = P.Q < 2 * P.s - 2 ? P.Q : 2 * P.s - 2;
+    for (int q = 0; q <= qhi; ++q) {
+      const int cnt = level_pairs(d.a_pos0, d.a_npos, d.b_pos0, d.b_npos, q);
+      if (g + cnt - g0 > cap && g > g0) {
+        f(g0, g, nb == 0, false);
+        ++nb;
+        g0 = g;
+      }
+      g += cnt;
+    }
+  }
+  if (g > g0 || total == 0) {
+    f(g0, g, nb == 0, true);
+    ++nb;
+  }
+  return nb;
+}
+
 // Integer bound on the pairs a product drops, in Acc units (dropped level Q + j
 // contributes <= n_{Q+j} k 2^(2w-2) 2^(-w j)): k (2^(w-2) n_{Q+1} + ceil(max_{j>=2} n / 3)).
 uint64_t drop_bound(const ProductDesc &pd, int Q, int64_t k, int w) {
@@ -63,8 +93,11 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
     return MPC_EINVAL;
   if (prm && prm->wait_limit_cycles < 0) return MPC_EINVAL;
   P.split = prm ? prm->split : MPC_SPLIT_COMMON;
-  if (P.split != MPC_SPLIT_COMMON && P.split != MPC_SPLIT_PER_PART) return MPC_EINVAL;
-  if (P.split == MPC_SPLIT_PER_PART && algo == MPC_OZAKI && method != MPC_4M) return MPC_EINVAL;
+  if (P.split != MPC_SPLIT_COMMON && P.split != MPC_SPLIT_PER_PART && P.split != MPC_SPLIT_RESIDUAL)
+    return MPC_EINVAL;
+  if (P.split != MPC_SPLIT_COMMON && algo == MPC_OZAKI && method != MPC_4M) return MPC_EINVAL;
+  if (prm && prm->pair_planes < 0) return MPC_EINVAL;
+  const bool resid = P.split == MPC_SPLIT_RESIDUAL && algo == MPC_OZAKI;
   out->wait_limit = prm ? prm->wait_limit_cycles : 0;
   uint64_t off = 0;
   P.off_status = off;
@@ -127,6 +160,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   if (gmax < 1) return MPC_EINVAL;
   if (prm && prm->max_group < 0) return MPC_EINVAL;
   if (prm && prm->max_group > 0 && prm->max_group < gmax) gmax = prm->max_group;
+  if (resid) gmax = 1;   // every pair is its own product: the units of one level differ per line
   P.s = s;
   P.Q = Q;
   P.gmax = gmax;
@@ -162,7 +196,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
     if (d.a_pos0 + d.b_pos0 < qmin) qmin = d.a_pos0 + d.b_pos0;
   }
   P.n_groups_total = total;
-  if (total > kMaxGroupsTotal) return MPC_EINVAL;   // the accumulate kernel's term table in shared memory
+  if (!resid && total > kMaxGroupsTotal) return MPC_EINVAL;   // the accumulate kernel's term table in shared memory
   P.acc_slots = (w * (Q - qmin) + 64) / 32 + 3;
   if (P.acc_slots > 88) return MPC_EINVAL;   // the accumulate kernel's word budget
   // bounds: b = bound_drop[c] + k (lossyA * bound_lossy_a[c] + lossyB * bound_lossy_b[c]), times 2^beta
@@ -189,13 +223,34 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   off = align256(off + (uint64_t)P.planes_A * m * P.kpad * 2);
   P.off_digits_b = off;
   off = align256(off + (uint64_t)P.planes_B * n * P.kpad * 2);
+  if (resid) {
+    // planes per batch: the buffer budget, at least one whole level, at most every pair
+    const uint64_t plane = (uint64_t)m * n * 4;
+    uint64_t cap = (prm && prm->pair_planes > 0) ? (uint64_t)prm->pair_planes
+                                                : (plane ? kPairBufferBytes / plane : (uint64_t)total);
+    const uint64_t maxlev = (uint64_t)(Q + 1 < s ? Q + 1 : s);
+    if (cap < maxlev) cap = maxlev;
+    if (cap > (uint64_t)total) cap = (uint64_t)total;
+    P.pair_batch = (int32_t)cap;
+  }
   P.off_groups = off;
-  off = align256(off + (uint64_t)total * m * n * 4);
+  off = align256(off + (uint64_t)(resid ? P.pair_batch : total) * m * n * 4);
   P.off_group_table = off;
   off = align256(off + (uint64_t)total * sizeof(GroupEntry));
   // accumulation order, the slice GEMM's schedule, the operands' flags, the data-dependent bounds
+  // (residual split: the flags and the bounds only)
   P.off_group_order = off;
-  off = align256(off + order_region_bytes(total, P.planes_A, P.planes_B));
+  off = align256(off + order_region_bytes(resid ? 0 : total, P.planes_A, P.planes_B));
+  if (resid) {
+    // slice units, the accumulators between batches, truncation counts, B copied K-major
+    P.off_units = off;
+    off = align256(off + (uint64_t)2 * s * (m + n) * 4);
+    off = align256(off + (uint64_t)2 * P.acc_slots * m * n * 4);
+    off = align256(off + (uint64_t)2 * m * n * 4);
+    off = align256(off + (uint64_t)2 * n * k);
+    off = align256(off + (uint64_t)2 * n * k * 4);
+    off = align256(off + (uint64_t)2 * L * n * k * 8);
+  }
   if (prm && prm->dump_accumulators) {
     P.off_acc_dump = off;
     off = align256(off + (uint64_t)2 * m * n * (P.acc_slots + 1) * 4);
@@ -203,6 +258,8 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   P.ws_bytes = off;
   // init, row max, column max, group table, 2 x digits, slice GEMM, accumulate, fallback (+ 2 part offsets)
   P.launches = P.split == MPC_SPLIT_PER_PART ? 11 : 9;
+  if (resid)   // init, 3 transposes, 2 splits, table, per batch slice GEMM + accumulate, fallback
+    P.launches = 7 + 2 * for_each_pair_batch(*out, [](int, int, bool, bool) {}) + 1;
   return MPC_OK;
 }
 
@@ -466,6 +523,123 @@ void call_fallback(Call &c, cudaStream_t st) {
   launch_fallback(fa, c.A, c.B, c.C, kFallbackBlocks, kFallbackThreads, st);
 }
 
+// The residual split (MPC_SPLIT_RESIDUAL, 4M): B copied K-major, both operands cut with a
+// unit re-measured before every slice, the single-pair table and bounds, then the pair
+// products and their accumulation batch by batch (whole levels), then the exact fallback.
+int run_residual(Call &c, const mpc_stage_events *events, cudaStream_t st) {
+  const mpc_plan &P = c.pl.pub;
+  auto mark = [&](int x) {
+    if (events && events->ev[x]) cudaEventRecord((cudaEvent_t)events->ev[x], st);
+  };
+  const int L = P.limbs, s = P.s;
+  const int64_t m = c.m, n = c.n, k = c.k, mn = m * n, nk = n * k;
+  int32_t *flags = (int32_t *)(c.ws + P.off_group_order);
+  uint64_t *bounds = (uint64_t *)(c.ws + P.off_group_order + bounds_offset(0, P.planes_A, P.planes_B));
+  mark(0);
+  launch_init(c.status, c.E, m, c.F, n, c.lossyA, c.lossyB, st, flags, (int64_t)P.planes_A + 2 + P.planes_B + 2);
+  if (k == 0) {
+    launch_zero_output(c.C, m, n, L, st);
+    for (int x = 1; x <= 4; ++x) mark(x);
+    return cuda_code(cudaGetLastError());
+  }
+  // the workspace regions of this variant (mpc_plan.off_units)
+  uint64_t o = P.off_units;
+  int32_t *uA = (int32_t *)(c.ws + o), *uB = uA + (int64_t)2 * s * m;
+  o = align256(o + (uint64_t)2 * s * (m + n) * 4);
+  uint32_t *acc = (uint32_t *)(c.ws + o);
+  o = align256(o + (uint64_t)2 * P.acc_slots * mn * 4);
+  uint32_t *trunc = (uint32_t *)(c.ws + o);
+  o = align256(o + (uint64_t)2 * mn * 4);
+  uint8_t *bt_sign = (uint8_t *)(c.ws + o);
+  o = align256(o + (uint64_t)2 * nk);
+  int32_t *bt_exp = (int32_t *)(c.ws + o);
+  o = align256(o + (uint64_t)2 * nk * 4);
+  uint64_t *bt_limb = (uint64_t *)(c.ws + o);
+  launch_transpose_operand(c.B, k, n, L, bt_sign, bt_exp, bt_limb, st);
+  MatView Bt;
+  for (int x = 0; x < 2; ++x) {
+    Bt.sign[x] = bt_sign + x * nk;
+    Bt.exp[x] = bt_exp + x * nk;
+    Bt.limb[x] = bt_limb + (int64_t)x * L * nk;
+  }
+  Bt.rows = n;
+  Bt.cols = k;
+  Bt.ld = k;
+  Bt.plane = nk;
+  __nv_bfloat16 *dA = (__nv_bfloat16 *)(c.ws + P.off_digits_a), *dB = (__nv_bfloat16 *)(c.ws + P.off_digits_b);
+  launch_resid_split(c.A, m, k, P.kpad, L, s, P.digit_bits, dA, uA, c.lossyA, flags, c.status, st);
+  launch_resid_split(Bt, n, k, P.kpad, L, s, P.digit_bits, dB, uB, c.lossyB, flags + P.planes_A + 2, c.status, st);
+  GroupEntry *table = (GroupEntry *)(c.ws + P.off_group_table);
+  ResidTableArgs ta{};
+  for (int x = 0; x < 4; ++x) ta.prod[x] = c.pl.prod[x];
+  ta.s = s;
+  ta.Q = P.Q;
+  ta.w = P.digit_bits;
+  ta.beta = P.bound_shift;
+  ta.k = k;
+  ta.planes_A = P.planes_A;
+  ta.planes_B = P.planes_B;
+  ta.flagsA = flags;
+  ta.flagsB = flags + P.planes_A + 2;
+  ta.table = table;
+  ta.bounds = bounds;
+  launch_resid_table(ta, st);
+  mark(1);
+  SliceGemmArgs sa = slice_args(c);
+  sa.sched = nullptr;   // table order
+  ResidAccumArgs aa{};
+  aa.planes = (const int32_t *)(c.ws + P.off_groups);
+  aa.m = m;
+  aa.n = n;
+  aa.k = k;
+  aa.p = c.p;
+  aa.L = L;
+  aa.Q = P.Q;
+  aa.s = s;
+  aa.w = P.digit_bits;
+  aa.nslot = P.acc_slots;
+  aa.beta = P.bound_shift;
+  aa.uA = uA;
+  aa.uB = uB;
+  aa.acc = acc;
+  aa.trunc = trunc;
+  aa.bounds = bounds;
+  aa.lossyA = c.lossyA;
+  aa.lossyB = c.lossyB;
+  aa.fallback = c.fallback;
+  aa.fallback_cap = (int64_t)P.fallback_capacity;
+  aa.status = c.status;
+  aa.acc_dump = P.off_acc_dump ? (uint32_t *)(c.ws + P.off_acc_dump) : nullptr;
+  int rc = MPC_OK;
+  for_each_pair_batch(c.pl, [&](int g0, int g1, bool first, bool last) {
+    if (rc != MPC_OK) return;
+    sa.groups = table + g0;
+    sa.n_entries = g1 - g0;
+    if (sa.n_entries > 0) {
+      if (c.pl.kernel == MPC_KERNEL_MMA_SYNC) {
+        launch_slicegemm_mma(sa, st);
+      } else {
+        cudaMemsetAsync(c.status + kStUnitCounter, 0, 4, st);   // the persistent kernel's unit counter
+        const cudaError_t e = launch_slicegemm_tc(sa, st, tile_of(c.pl.kernel), c.pl.wait_limit);
+        if (e == cudaErrorNotSupported && c.pl.kernel == MPC_KERNEL_AUTO) launch_slicegemm_mma(sa, st);
+        else if (e != cudaSuccess) rc = e == cudaErrorNotSupported ? MPC_ENOTSUP : cuda_code(e);
+      }
+    }
+    if (rc != MPC_OK) return;
+    if (last) mark(2);
+    aa.table = table + g0;
+    aa.n_entries = g1 - g0;
+    aa.first = first;
+    aa.last = last;
+    launch_resid_accum(aa, c.C, st);
+  });
+  if (rc != MPC_OK) return rc;
+  mark(3);
+  call_fallback(c, st);
+  mark(4);
+  return cuda_code(cudaGetLastError());
+}
+
 }  // namespace
 }  // namespace mpc
 
@@ -496,6 +670,7 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_
   if (rc != MPC_OK || c.empty) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   cudaGetLastError();   // clear a stale error of an earlier, unrelated call
+  if (c.pl.pub.algo == MPC_OZAKI && c.pl.pub.split == MPC_SPLIT_RESIDUAL) return run_residual(c, events, st);
   auto mark = [&](int x) {
     if (events && events->ev[x]) cudaEventRecord((cudaEvent_t)events->ev[x], st);
   };
@@ -527,6 +702,7 @@ int mpcgemm_profiled(int64_t m, int64_t n, int64_t k, int32_t p_bits, const mpc_
 int mpcgemm_batched_workspace(int count, const mpc_problem *probs, const mpc_oz_params *params, uint64_t *offsets,
                               size_t *total) {
   if (count < 0 || (count > 0 && !probs) || !total) return MPC_EINVAL;
+  if (params && params->split == MPC_SPLIT_RESIDUAL) return MPC_EINVAL;   // single calls only
   uint64_t off = 0;
   for (int x = 0; x < count; ++x) {
     Plan pl;
@@ -607,6 +783,7 @@ void side_join(SidePool *sp, cudaStream_t st) {
 int mpcgemm_batched(int count, const mpc_problem *probs, const mpc_oz_params *params, void *workspace,
                     size_t ws_bytes, void *stream) {
   if (count < 0 || (count > 0 && !probs)) return MPC_EINVAL;
+  if (params && params->split == MPC_SPLIT_RESIDUAL) return MPC_EINVAL;   // single calls only
   if (count == 0) return MPC_OK;
   thread_local std::vector<Call> calls;   // reused: no host allocation once it has grown
   if (calls.size() < (size_t)count) calls.resize((size_t)count);

@@ -34,7 +34,7 @@ constexpr int kDefaultGuard = 40;
 // status block (int32 words at the start of the workspace); words 10..13 hold the
 // per-part split's offsets as kZCap - z (A re, A im, B re, B im; maxima, so 0 = zero part)
 enum StatusWord { kStErange = 0, kStFallbackCount = 1, kStFallbackOverflow = 2, kStUncertified = 3, kStTimeout = 4,
-                  kStPartZ = 10 };
+                  kStUnitCounter = 8, kStPartZ = 10 };   // word 8: the tcgen05 slice GEMM's unit counter
 // per-part split: the offset of an all-zero part, and the cap of every offset
 constexpr int kZCap = 2048;
 

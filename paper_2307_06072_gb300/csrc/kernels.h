@@ -114,6 +114,36 @@ struct PlainCombineArgs {
   int32_t *status;
 };
 
+// Residual split (MPC_SPLIT_RESIDUAL, 4M): the single-pair group table and the call's bounds.
+struct ResidTableArgs {
+  ProductDesc prod[4];
+  int s, Q, w, beta;
+  int64_t k;
+  int planes_A, planes_B;
+  const int32_t *flagsA, *flagsB;   // per digit plane: any nonzero digit; then per part: any nonzero value
+  GroupEntry *table;
+  uint64_t *bounds;                 // out: drop[2], lossy_a[2], lossy_b[2], zero[2], Q_c[2]
+};
+
+// Residual split: one batch of pair planes folded into the exact accumulators.
+struct ResidAccumArgs {
+  const int32_t *planes;        // the batch's pair products [entry][m][n]
+  const GroupEntry *table;      // the batch's table entries
+  int32_t n_entries;
+  int64_t m, n, k;
+  int p, L, Q, s, w, nslot, beta;
+  const int32_t *uA, *uB;       // slice units [part][slice][line] (INT32_MIN: a zero slice)
+  uint32_t *acc;                // accumulator words between batches [comp][word][m n]
+  uint32_t *trunc;              // truncation counts [comp][m n]
+  int first, last;
+  const uint64_t *bounds;       // from k_resid_table
+  const int32_t *lossyA, *lossyB;
+  int64_t *fallback;
+  int64_t fallback_cap;
+  int32_t *status;
+  uint32_t *acc_dump;           // null, or per component: nslot words of |Acc| and its sign
+};
+
 // digits per operand of the plain path at precision p (an instantiated size)
 int plain_digits_for(int p);
 
@@ -146,5 +176,14 @@ void launch_fallback(const FallbackArgs &f, const MatView &A, const MatView &B, 
 void launch_plain_gemm(const PlainGemmArgs &a, cudaStream_t st);
 void launch_plain_combine(const PlainCombineArgs &a, const OutView &C, cudaStream_t st);
 void launch_zero_output(const OutView &C, int64_t m, int64_t n, int L, cudaStream_t st);
+// residual split: B's format planes copied K-major (n lines of k), the split of one operand's
+// lines, the table and bounds, and one batch of the accumulation
+void launch_transpose_operand(const MatView &B, int64_t k, int64_t n, int L, uint8_t *sign, int32_t *exp,
+                              uint64_t *limb, cudaStream_t st);
+void launch_resid_split(const MatView &X, int64_t lines, int64_t k, int64_t kpad, int L, int s, int w,
+                        __nv_bfloat16 *digits, int32_t *units, int32_t *lossy, int32_t *flags, int32_t *status,
+                        cudaStream_t st);
+void launch_resid_table(const ResidTableArgs &a, cudaStream_t st);
+void launch_resid_accum(const ResidAccumArgs &a, const OutView &C, cudaStream_t st);
 
 }  // namespace mpc

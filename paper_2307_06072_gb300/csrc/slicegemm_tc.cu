@@ -69,7 +69,6 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr long long kDefaultWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 constexpr int URING = 4;                                   // unit-index ring slots
 constexpr int kMaxBatch = 64;                              // problems per launch (kernel parameter space)
-constexpr int kStUnitCounter = 8;                          // status word used as the unit counter
 
 // One launch serves a set of up to kMaxBatch independent problems (a single
 // GEMM is a set of one): their units are numbered consecutively and each

@@ -199,6 +199,51 @@ def test_per_part_split_plan(mp):
     assert d["split"] == 1 and base["split"] == 0
     assert d["ws_bytes"] == base["ws_bytes"] and d["n_groups_total"] == base["n_groups_total"]
     assert d["launches"] == base["launches"] + 2
-    prm.split = 2
+    prm.split = 3
     rc = mp.lib().mpcgemm_plan(64, 64, 64, 256, 0, 1, ctypes.byref(prm), ctypes.byref(out))
+    assert rc == mp._native.MPC_EINVAL
+
+
+def test_residual_split_plan(mp):
+    """The residual split is a 4M option of single calls: 3M and batched calls are rejected on
+    the host.  Every kept pair is its own group (s(s+1)/2 per product at Q = s - 1); the
+    pair products go through a buffer of pair_batch planes, whole levels at a time, so the
+    launches are init, three transposes, two splits, the table, a slice GEMM and an
+    accumulation per batch, and the fallback."""
+    import ctypes
+    from oracle import ozaki
+    out = mp._native.Plan()
+    prm = mp._native.oz_params(split="residual")
+    rc = mp.lib().mpcgemm_plan(64, 64, 64, 256, 1, 1, ctypes.byref(prm), ctypes.byref(out))
+    assert rc == mp._native.MPC_EINVAL
+    m, n, k, p = 300, 200, 100, 256
+    d = mp.plan(m, n, k, p, "4m", "ozaki", dict(split="residual"))
+    s, Q = d["s"], d["Q"]
+    assert d["split"] == 2 and d["gmax"] == 1 and Q == s - 1
+    assert d["n_groups"] == [s * (s + 1) // 2] * 4 and d["n_groups_total"] == 2 * s * (s + 1)
+    assert d["pair_batch"] == d["n_groups_total"]          # everything fits the default buffer
+    assert d["launches"] == 7 + 2 + 1 and d["off_units"] > 0
+    prm0 = ozaki.make_params(p, k, "4m")
+    assert (s, Q) == (prm0.s, prm0.Q)
+    # a buffer of 50 planes: whole levels (at most s = 33 pairs), packed greedily
+    d2 = mp.plan(m, n, k, p, "4m", "ozaki", dict(split="residual", pair_planes=50))
+    batches, cur = 0, 0
+    for _ in range(4):
+        for q, lo, cnt in ozaki.level_pairs((0, s - 1), (0, s - 1), Q):
+            if cur + cnt > 50 and cur > 0:
+                batches, cur = batches + 1, 0
+            cur += cnt
+    batches += 1
+    assert d2["pair_batch"] == 50 and d2["launches"] == 7 + 2 * batches + 1
+    assert d2["ws_bytes"] < d["ws_bytes"]
+    d3 = mp.plan(m, n, k, p, "4m", "ozaki", dict(split="residual", pair_planes=5))
+    assert d3["pair_batch"] == s                             # at least one whole level
+    base = mp.plan(m, n, k, p, "4m", "ozaki")
+    assert base["off_units"] == 0 and base["pair_batch"] == 0
+    prm.pair_planes = -1
+    rc = mp.lib().mpcgemm_plan(m, n, k, p, 0, 1, ctypes.byref(prm), ctypes.byref(out))
+    assert rc == mp._native.MPC_EINVAL
+    total = ctypes.c_size_t()
+    prm.pair_planes = 0
+    rc = mp.lib().mpcgemm_batched_workspace(0, None, ctypes.byref(prm), None, ctypes.byref(total))
     assert rc == mp._native.MPC_EINVAL
