@@ -155,8 +155,11 @@ typedef struct mpc_mat {
  *               negative residuals at half that unit; the extraction is read as
  *               symmetric, i.e. tau = 3 2^(k-1).)  The slices of one level then sit at
  *               different units in different lines, so every kept pair (t, u),
- *               t + u <= Q, is its own exact product (max_group is ignored), and the
- *               accumulation adds each product at its own per-entry offset.  The pair
+ *               t + u <= Q, has its own table entry and the accumulation adds each
+ *               product at its own per-entry offset; consecutive pairs of a level whose
+ *               slices step by exactly w in every line are merged into one exact
+ *               tensor-core group of at most max_group (else the int32 limit) pairs,
+ *               so lines that never skip are grouped as in the default split.  The pair
  *               products are streamed through a buffer of mpc_plan.pair_batch planes
  *               (whole levels at a time), so the workspace stays bounded; the exact
  *               accumulators live in the workspace between batches.  Same correctly

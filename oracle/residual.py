@@ -33,7 +33,11 @@ Reading used here (the paper's S - beta bits per slice become w bits per digit):
    table lists, per real product (rr, ii, ri, ir), the pairs level by level (q = t + u
    ascending, t ascending); a pair whose A or B digit plane is zero in every line is
    skipped, as is every pair of a product that enters only components of A B that
-   vanish identically.
+   vanish identically.  Consecutive live pairs of a level whose offsets agree at every
+   entry may share one exact group sum: pair (t + 1, u - 1) joins the group of (t, u)
+   when slice t + 1 of A and slice u of B each lie exactly w below their previous slice
+   in every line where they are nonzero (``merged_table``; at most gmax pairs, the int32
+   limit).  A group's sum is the sum of its pairs' products, so no accumulator changes.
 5. Accumulation ("C := C + C_ab in L-bit arithmetic"), exact: component c of entry
    (i, j) has its own window, anchored at M = max over its products of
    b^A_(i,0) + b^B_(j,0) (lines where either part is zero do not count); its unit is
@@ -184,6 +188,37 @@ def pair_table(spA: ResidualSplit, spB: ResidualSplit, prm: oz.Params):
     return out
 
 
+def irregular_steps(sp: ResidualSplit, part: str, s: int, w: int) -> list:
+    """Per slice t: some line where slice t is nonzero has a unit other than its previous one - w."""
+    out = [False] * s
+    for t in range(1, s):
+        out[t] = any(u is not None and u != u_prev - w
+                     for u_prev, u in zip(sp.units[part][t - 1], sp.units[part][t]))
+    return out
+
+
+def merged_table(spA: ResidualSplit, spB: ResidualSplit, table, prm: oz.Params, gmax: int):
+    """The table with runs of consecutive live pairs of one level merged (module notes, step
+    4): entries (product, q, t0, count); a merged pair's own entry gets count 0."""
+    irr = {("A", p): irregular_steps(spA, p, prm.s, prm.w) for p in ("re", "im")}
+    irr.update({("B", p): irregular_steps(spB, p, prm.s, prm.w) for p in ("re", "im")})
+    out = [[pr, q, t, 1 if live else 0] for pr, q, t, live in table]
+    head = None
+    for e, (pr, q, t, live) in enumerate(table):
+        if e == 0 or (table[e - 1][0], table[e - 1][1]) != (pr, q):
+            head = None
+        if not live:
+            head = None
+            continue
+        pa, pb = OPERANDS[pr]
+        if head is not None and out[head][3] < gmax and not irr[("A", pa)][t] and not irr[("B", pb)][q - t + 1]:
+            out[head][3] += 1
+            out[e][3] = 0
+            continue
+        head = e
+    return [tuple(x) for x in out]
+
+
 def pair_products(spA: ResidualSplit, spB: ResidualSplit, table):
     """G_tu = D^A_t (D^B_u)^T per live table entry (exact: every value < 2^31 < 2^53)."""
     out = []
@@ -284,7 +319,8 @@ class ResidualResult:
     params: oz.Params
     splitA: ResidualSplit
     splitB: ResidualSplit
-    table: list
+    table: list           # one entry per kept pair: (product, q, t, live)
+    groups: list          # the merged table: (product, q, t0, count)
     products: list
     acc: dict
     lo: dict
@@ -295,13 +331,15 @@ class ResidualResult:
 
 
 def ozaki_cgemm_residual(A, B, p: int, guard: int = oz.DEFAULT_GUARD, s: int | None = None,
-                         Q: int | None = None, w: int | None = None, fallback=None) -> ResidualResult:
+                         Q: int | None = None, w: int | None = None, fallback=None,
+                         max_group: int = 0) -> ResidualResult:
     """The whole 4M Ozaki complex GEMM with the residual split; output == O1."""
     m, k, n = A.rows, A.cols, B.cols
-    prm = oz.make_params(p, k, "4m", guard, s, Q, 1, w)
+    prm = oz.make_params(p, k, "4m", guard, s, Q, max_group, w)
     spA = split_operand(A, prm.s, "A", prm.w)
     spB = split_operand(B, prm.s, "B", prm.w)
     table = pair_table(spA, spB, prm)
+    groups = merged_table(spA, spB, table, prm, prm.gmax)
     prods = pair_products(spA, spB, table)
     acc, lo, trunc, top = accumulate(spA, spB, table, prods, prm, m, n)
     beta = oz.bound_exponent(prm)
@@ -330,7 +368,7 @@ def ozaki_cgemm_residual(A, B, p: int, guard: int = oz.DEFAULT_GUARD, s: int | N
         for c, i, j in pending:
             vals[c][i][j] = o1.round_nearest_even(exact_vals[(i, j)][c], p)
     C = o1.pack(vals[0], vals[1], p)
-    return ResidualResult(prm, spA, spB, table, prods, acc, lo, trunc, top, cert, C)
+    return ResidualResult(prm, spA, spB, table, groups, prods, acc, lo, trunc, top, cert, C)
 
 
 def entry_bound(prm: oz.Params, spA, spB, i: int, j: int, comp: str, trunc: int) -> int:

@@ -160,7 +160,9 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   if (gmax < 1) return MPC_EINVAL;
   if (prm && prm->max_group < 0) return MPC_EINVAL;
   if (prm && prm->max_group > 0 && prm->max_group < gmax) gmax = prm->max_group;
-  if (resid) gmax = 1;   // every pair is its own product: the units of one level differ per line
+  // residual split: one table entry per pair (the device merges runs of up to gmax pairs
+  // whose units agree in every line)
+  const int gbuild = resid ? 1 : gmax;
   P.s = s;
   P.Q = Q;
   P.gmax = gmax;
@@ -190,7 +192,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
     d.a_plane0 = a0;
     d.b_plane0 = b0;
     d.group0 = total;
-    d.n_groups = build_groups(pr, d.a_pos0, d.a_npos, d.b_pos0, d.b_npos, Q, gmax, nullptr, 0);
+    d.n_groups = build_groups(pr, d.a_pos0, d.a_npos, d.b_pos0, d.b_npos, Q, gbuild, nullptr, 0);
     P.n_groups[pr] = d.n_groups;
     total += d.n_groups;
     if (d.a_pos0 + d.b_pos0 < qmin) qmin = d.a_pos0 + d.b_pos0;
@@ -240,7 +242,8 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   // accumulation order, the slice GEMM's schedule, the operands' flags, the data-dependent bounds
   // (residual split: the flags and the bounds only)
   P.off_group_order = off;
-  off = align256(off + order_region_bytes(resid ? 0 : total, P.planes_A, P.planes_B));
+  off = align256(off + (resid ? order_region_bytes(0, P.planes_A + 2 * s, P.planes_B + 2 * s)
+                              : order_region_bytes(total, P.planes_A, P.planes_B)));
   if (resid) {
     // slice units, the accumulators between batches, truncation counts, B copied K-major
     P.off_units = off;
@@ -533,10 +536,13 @@ int run_residual(Call &c, const mpc_stage_events *events, cudaStream_t st) {
   };
   const int L = P.limbs, s = P.s;
   const int64_t m = c.m, n = c.n, k = c.k, mn = m * n, nk = n * k;
+  // flags: A's planes, its two values, its slices' irregular steps; then the same for B
   int32_t *flags = (int32_t *)(c.ws + P.off_group_order);
-  uint64_t *bounds = (uint64_t *)(c.ws + P.off_group_order + bounds_offset(0, P.planes_A, P.planes_B));
+  const int fA = P.planes_A + 2 + 2 * s, fB = P.planes_B + 2 + 2 * s;
+  int32_t *flagsB = flags + fA, *irrA = flags + P.planes_A + 2, *irrB = flagsB + P.planes_B + 2;
+  uint64_t *bounds = (uint64_t *)(c.ws + P.off_group_order + bounds_offset(0, fA - 2, fB - 2));
   mark(0);
-  launch_init(c.status, c.E, m, c.F, n, c.lossyA, c.lossyB, st, flags, (int64_t)P.planes_A + 2 + P.planes_B + 2);
+  launch_init(c.status, c.E, m, c.F, n, c.lossyA, c.lossyB, st, flags, (int64_t)fA + fB);
   if (k == 0) {
     launch_zero_output(c.C, m, n, L, st);
     for (int x = 1; x <= 4; ++x) mark(x);
@@ -567,8 +573,8 @@ int run_residual(Call &c, const mpc_stage_events *events, cudaStream_t st) {
   Bt.ld = k;
   Bt.plane = nk;
   __nv_bfloat16 *dA = (__nv_bfloat16 *)(c.ws + P.off_digits_a), *dB = (__nv_bfloat16 *)(c.ws + P.off_digits_b);
-  launch_resid_split(c.A, m, k, P.kpad, L, s, P.digit_bits, dA, uA, c.lossyA, flags, c.status, st);
-  launch_resid_split(Bt, n, k, P.kpad, L, s, P.digit_bits, dB, uB, c.lossyB, flags + P.planes_A + 2, c.status, st);
+  launch_resid_split(c.A, m, k, P.kpad, L, s, P.digit_bits, dA, uA, c.lossyA, flags, irrA, c.status, st);
+  launch_resid_split(Bt, n, k, P.kpad, L, s, P.digit_bits, dB, uB, c.lossyB, flagsB, irrB, c.status, st);
   GroupEntry *table = (GroupEntry *)(c.ws + P.off_group_table);
   ResidTableArgs ta{};
   for (int x = 0; x < 4; ++x) ta.prod[x] = c.pl.prod[x];
@@ -579,8 +585,11 @@ int run_residual(Call &c, const mpc_stage_events *events, cudaStream_t st) {
   ta.k = k;
   ta.planes_A = P.planes_A;
   ta.planes_B = P.planes_B;
+  ta.gmax = P.gmax;
   ta.flagsA = flags;
-  ta.flagsB = flags + P.planes_A + 2;
+  ta.flagsB = flagsB;
+  ta.irregularA = irrA;
+  ta.irregularB = irrB;
   ta.table = table;
   ta.bounds = bounds;
   launch_resid_table(ta, st);

@@ -117,10 +117,11 @@ struct PlainCombineArgs {
 // Residual split (MPC_SPLIT_RESIDUAL, 4M): the single-pair group table and the call's bounds.
 struct ResidTableArgs {
   ProductDesc prod[4];
-  int s, Q, w, beta;
+  int s, Q, w, beta, gmax;
   int64_t k;
   int planes_A, planes_B;
   const int32_t *flagsA, *flagsB;   // per digit plane: any nonzero digit; then per part: any nonzero value
+  const int32_t *irregularA, *irregularB;   // per digit plane: some line's unit is not w below the last one
   GroupEntry *table;
   uint64_t *bounds;                 // out: drop[2], lossy_a[2], lossy_b[2], zero[2], Q_c[2]
 };
@@ -181,8 +182,8 @@ void launch_zero_output(const OutView &C, int64_t m, int64_t n, int L, cudaStrea
 void launch_transpose_operand(const MatView &B, int64_t k, int64_t n, int L, uint8_t *sign, int32_t *exp,
                               uint64_t *limb, cudaStream_t st);
 void launch_resid_split(const MatView &X, int64_t lines, int64_t k, int64_t kpad, int L, int s, int w,
-                        __nv_bfloat16 *digits, int32_t *units, int32_t *lossy, int32_t *flags, int32_t *status,
-                        cudaStream_t st);
+                        __nv_bfloat16 *digits, int32_t *units, int32_t *lossy, int32_t *flags, int32_t *irregular,
+                        int32_t *status, cudaStream_t st);
 void launch_resid_table(const ResidTableArgs &a, cudaStream_t st);
 void launch_resid_accum(const ResidAccumArgs &a, const OutView &C, cudaStream_t st);
 

@@ -15,10 +15,16 @@
 //    F + t_b - 2^(b'-b) t_b', F the bits of |a| in [b, b') and t_x the round-up flag of
 //    RNE(|a| / 2^x); the line's next ceil(log2 max |R|) comes from the bits of |a| below
 //    b (a block-wide maximum).  Writes the digit planes, the unit of every (part, slice,
-//    line), the plane and value flags and the lossy flags (a nonzero remainder).
-//  * k_resid_table: every kept pair (t, u), t + u <= Q, is its own group (the slice
-//    products of a level cannot share one tensor-core sum: their units differ per line);
-//    pairs with an all-zero plane are emptied; the call's error bounds.
+//    line), the plane and value flags, the lossy flags (a nonzero remainder) and, per
+//    slice, whether some line's unit is not exactly w below its previous one.
+//  * k_resid_table: one table entry per kept pair (t, u), t + u <= Q, levels in order;
+//    pairs with an all-zero plane are emptied.  The slice products of a level can share
+//    one tensor-core sum only where their units agree in every line, so consecutive
+//    pairs of a level are merged into one exact group (at most the int32 limit) where
+//    neither of the slices that changes steps by more than w in any line (the split
+//    flags such slices); the run's first entry carries the count, the others are empty.
+//    On lines that never skip (random full-precision data) this is the default split's
+//    grouping.  Also the call's error bounds.
 //  * k_resid_accum: one thread per output entry; for a batch of pair planes it adds
 //    every product at its own offset o = b^A_(i,t) + b^B_(j,u) - lo_c into the exact
 //    accumulator of its component, whose window is anchored at the largest anchor sum
@@ -137,7 +143,7 @@ __device__ __forceinline__ long long block_max(long long v, long long *red) {
 template <int W>
 __global__ void __launch_bounds__(kSplitT) k_resid_split(MatView X, int64_t lines, int64_t k, int64_t kpad, int L,
                                                          int s, __nv_bfloat16 *digits, int32_t *units, int32_t *lossy,
-                                                         int32_t *flags, int32_t *status) {
+                                                         int32_t *flags, int32_t *irregular, int32_t *status) {
   __shared__ long long red[kSplitT / 32];
   const int64_t line = blockIdx.x;
   const int tid = threadIdx.x;
@@ -202,6 +208,7 @@ __global__ void __launch_bounds__(kSplitT) k_resid_split(MatView X, int64_t line
       if (tid == 0) {
         if (b < (long long)INT32_MIN + 1 || b > (long long)INT32_MAX) status_set(status, kStErange, 1);
         units[(int64_t)plane * lines + line] = (int32_t)b;
+        if (bp != kNone && b != bp - W) irregular[plane] = 1;   // this line skipped grid positions here
       }
       bp = b;
       c = emax;
@@ -260,6 +267,38 @@ __global__ void __launch_bounds__(128) k_resid_table(ResidTableArgs a) {
       GroupEntry g = a.table[e];
       if (!live(g.t0, g.q - g.t0)) g.count = 0;
       a.table[e] = g;
+    }
+    __syncwarp();
+    // merge: within a level, pair (t + 1, u - 1) joins the run of (t, u) when both are live and
+    // their offsets agree at every entry, i.e. slice t + 1 of A and slice u of B each sit exactly
+    // w below the slice before it in every line (no irregular step); a run holds at most gmax
+    // pairs (an exact int32 sum).  The run's first entry takes the count, the others become empty.
+    const int32_t *irrA = a.irregularA + pd.a_plane0, *irrB = a.irregularB + pd.b_plane0;
+    const int qhi = a.Q < 2 * a.s - 2 ? a.Q : 2 * a.s - 2;
+    for (int q = lane; q <= qhi; q += 32) {
+      int e0 = pd.group0;
+      for (int x = 0; x < q; ++x) e0 += level_pairs(0, a.s, 0, a.s, x);
+      const int cnt = level_pairs(0, a.s, 0, a.s, q);
+      int head = -1;
+      for (int e = e0; e < e0 + cnt; ++e) {
+        GroupEntry g = a.table[e];
+        if (g.count == 0) {
+          head = -1;
+          continue;
+        }
+        if (head >= 0) {
+          GroupEntry h = a.table[head];
+          const int u_prev = g.q - g.t0 + 1;   // the B slice of the pair before this one
+          if (h.count < a.gmax && !irrA[g.t0] && !irrB[u_prev]) {
+            ++h.count;
+            a.table[head] = h;
+            g.count = 0;
+            a.table[e] = g;
+            continue;
+          }
+        }
+        head = e;
+      }
     }
     // live dropped pairs per level above the cut
     uint64_t n1 = 0, nmax = 0;
@@ -390,11 +429,13 @@ __global__ void __launch_bounds__(kAccT) k_resid_accum(ResidAccumArgs a, OutView
         if (!g.count) continue;
         const int pr = g.prod, c = comp_of(pr);
         if (lo[c] == kNone) continue;
-        const int t = g.t0, u = g.q - g.t0;
+        // the group's offset from its first A slice and its last (lowest) B slice: a line's
+        // nonzero slices are a prefix, so if either is zero here every pair of the group is
+        const int t = g.t0, ulast = g.q - g.t0 - (g.count - 1);
         const int32_t ua = a.uA[((int64_t)part_a(pr) * a.s + t) * a.m + i];
-        const int32_t ub = a.uB[((int64_t)part_b(pr) * a.s + u) * a.n + j];
-        if (ua == INT32_MIN || ub == INT32_MIN) continue;   // a zero slice of this line: G is 0 here
-        const long long off = (long long)ua + ub - lo[c];
+        const int32_t ub = a.uB[((int64_t)part_b(pr) * a.s + ulast) * a.n + j];
+        if (ua == INT32_MIN || ub == INT32_MIN) continue;
+        const long long off = (long long)ua + ub - (long long)a.w * (g.count - 1) - lo[c];
         const int key = pr * 1024 + g.q;
         if (key != run_key[c] || off != run_off[c]) {
           flush(c);
@@ -473,13 +514,15 @@ void launch_transpose_operand(const MatView &B, int64_t k, int64_t n, int L, uin
 }
 
 void launch_resid_split(const MatView &X, int64_t lines, int64_t k, int64_t kpad, int L, int s, int w,
-                        __nv_bfloat16 *digits, int32_t *units, int32_t *lossy, int32_t *flags, int32_t *status,
-                        cudaStream_t st) {
+                        __nv_bfloat16 *digits, int32_t *units, int32_t *lossy, int32_t *flags, int32_t *irregular,
+                        int32_t *status, cudaStream_t st) {
   if (lines <= 0) return;
   if (w == 9)
-    k_resid_split<9><<<(unsigned)lines, kSplitT, 0, st>>>(X, lines, k, kpad, L, s, digits, units, lossy, flags, status);
+    k_resid_split<9><<<(unsigned)lines, kSplitT, 0, st>>>(X, lines, k, kpad, L, s, digits, units, lossy, flags,
+                                                           irregular, status);
   else
-    k_resid_split<8><<<(unsigned)lines, kSplitT, 0, st>>>(X, lines, k, kpad, L, s, digits, units, lossy, flags, status);
+    k_resid_split<8><<<(unsigned)lines, kSplitT, 0, st>>>(X, lines, k, kpad, L, s, digits, units, lossy, flags,
+                                                           irregular, status);
 }
 
 void launch_resid_table(const ResidTableArgs &a, cudaStream_t st) { k_resid_table<<<1, 128, 0, st>>>(a); }

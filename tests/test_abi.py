@@ -206,7 +206,8 @@ def test_per_part_split_plan(mp):
 
 def test_residual_split_plan(mp):
     """The residual split is a 4M option of single calls: 3M and batched calls are rejected on
-    the host.  Every kept pair is its own group (s(s+1)/2 per product at Q = s - 1); the
+    the host.  The table has one entry per kept pair (s(s+1)/2 per product at Q = s - 1; the
+    device merges runs of up to gmax pairs into their first entry); the
     pair products go through a buffer of pair_batch planes, whole levels at a time, so the
     launches are init, three transposes, two splits, the table, a slice GEMM and an
     accumulation per batch, and the fallback."""
@@ -219,7 +220,7 @@ def test_residual_split_plan(mp):
     m, n, k, p = 300, 200, 100, 256
     d = mp.plan(m, n, k, p, "4m", "ozaki", dict(split="residual"))
     s, Q = d["s"], d["Q"]
-    assert d["split"] == 2 and d["gmax"] == 1 and Q == s - 1
+    assert d["split"] == 2 and d["gmax"] == ozaki.make_params(p, k, "4m").gmax and Q == s - 1
     assert d["n_groups"] == [s * (s + 1) // 2] * 4 and d["n_groups_total"] == 2 * s * (s + 1)
     assert d["pair_batch"] == d["n_groups_total"]          # everything fits the default buffer
     assert d["launches"] == 7 + 2 + 1 and d["off_units"] > 0

@@ -3,7 +3,7 @@
 Alg. 2 as printed: every real part of every line is cut slice after slice with the unit
 re-measured from the largest residual left in the line.  Every integer stage must equal
 the emulation bit for bit: the unit of every (part, slice, line), the digit planes, the
-lossy flags, the single-pair table with its emptied pairs, the exact accumulators and
+lossy flags, the pair table with its merged runs and emptied pairs, the exact accumulators and
 the number of components sent to the exact fallback; every output equals O1.  The pair
 products are streamed through a bounded buffer: a run with a small buffer (many
 batches, the accumulators kept in the workspace between them) gives the same bits.
@@ -103,9 +103,9 @@ def test_residual_stage_parity(case, kernel):
     la, lb = gu.ws_lossy(ws, pl, m, n)
     assert np.array_equal(la != 0, ~np.array(r.splitA.lossless)) and np.array_equal(lb != 0, ~np.array(r.splitB.lossless))
     table, _, _ = gu.ws_group_tables(ws, pl)
-    assert len(table) == len(r.table)
-    for e, ((pr, q, t, live), got) in enumerate(zip(r.table, table)):
-        assert tuple(int(v) for v in got) == (residual.PRODUCTS.index(pr), q, t, 1 if live else 0), e
+    assert len(table) == len(r.groups)
+    for e, ((pr, q, t, cnt), got) in enumerate(zip(r.groups, table)):
+        assert tuple(int(v) for v in got) == (residual.PRODUCTS.index(pr), q, t, cnt), e
     acc = gu.ws_accumulators(ws, pl, m, n)
     for c, comp in enumerate(("re", "im")):
         assert np.array_equal(acc[c], r.acc[comp]), comp

@@ -285,6 +285,53 @@ def test_accumulator_differs_from_the_kept_pairs_only_by_counted_truncations(cas
 
 
 @pytest.mark.parametrize("case", ["uniform_exp", "im_small", "gap"])
+def test_merged_pairs_have_equal_offsets_at_every_entry(case):
+    """Every merged group's pairs have one offset b^A_(i,t) + b^B_(j,u) at every entry where
+    both slices are nonzero (so one sum per group is exact); every live pair is in exactly
+    one group."""
+    p = 128
+    if case == "gap":
+        A = _gap_matrix(5, 7, p, 45, [5, 20, 3, 30, 12], 50, 20)
+        B = _gap_matrix(4, 7, p, 46, [7, 2, 25, 8], 50, 20).transpose()
+    else:
+        A = si.random_matrix(5, 7, p, 47, "uniform_exp")
+        B = si.random_matrix(7, 4, p, 48, "uniform_exp")
+        if case == "im_small":
+            A.exp[1] = np.where(A.limb[1, -1] != 0, A.exp[1] - 100, A.exp[1])
+    res = residual.ozaki_cgemm_residual(A, B, p, max_group=5)
+    covered = 0
+    for e, (pr, q, t0, cnt) in enumerate(res.groups):
+        assert cnt <= 5
+        covered += cnt
+        pa, pb = residual.OPERANDS[pr]
+        ulast = q - t0 - (cnt - 1)
+        for i in range(A.rows):
+            for j in range(B.cols):
+                offs = {res.splitA.units[pa][t][i] + res.splitB.units[pb][q - t][j]
+                        for t in range(t0, t0 + cnt)
+                        if res.splitA.units[pa][t][i] is not None and res.splitB.units[pb][q - t][j] is not None}
+                assert len(offs) <= 1, (e, i, j, offs)
+                if offs:   # the device's formula: first A slice, last B slice, w per extra pair
+                    ua, ub = res.splitA.units[pa][t0][i], res.splitB.units[pb][ulast][j]
+                    assert ua is not None and ub is not None and offs == {ua + ub - res.params.w * (cnt - 1)}
+    assert covered == sum(1 for x in res.table if x[3])
+
+
+def test_regular_lines_merge_like_the_default_split():
+    """Full-precision random lines of 64 elements step by exactly w, so the merged table is the
+    default split's grouping (runs of gmax pairs per level)."""
+    p = 256
+    A = si.random_matrix(3, 64, p, 49, "uniform_exp")
+    B = si.random_matrix(64, 3, p, 50, "uniform_exp")
+    res = residual.ozaki_cgemm_residual(A, B, p, guard=0, max_group=5)   # s w < p + 40: no plane is dead
+    assert all(x[3] for x in res.table)
+    default = ozaki.groups_for((0, res.params.s - 1), (0, res.params.s - 1), res.params.Q, 5)
+    for pr in residual.PRODUCTS:
+        heads = [(q, t0, cnt) for x, q, t0, cnt in res.groups if x == pr and cnt]
+        assert heads == [(g.q, g.t0, g.count) for g in default]
+
+
+@pytest.mark.parametrize("case", ["uniform_exp", "im_small", "gap"])
 def test_term_offsets_fit_the_accumulator_window(case):
     """Every term offset is <= w Q: the window's top, so that the accumulator width of the
     default split (w Q bits plus headroom) holds every sum."""
