@@ -115,6 +115,72 @@ __device__ __noinline__ void cdiv_store(const MatRW &M, int64_t r, int64_t col, 
   if (!ok) atomicOr(reinterpret_cast<int *>(status) + kStErange, 1);
 }
 
+// Component c of a - l u (Eq. 4m_way_base), rounded once, into (r, col) of M.  The two
+// components read disjoint parts of (r, col), so two threads may form them independently.
+__device__ __noinline__ void cfma_part(const MatRW &M, int64_t r, int64_t col, int c, const MPRef &a,
+                                       const MPRef &lre, const MPRef &lim, const MPRef &ure, const MPRef &uim, int p,
+                                       int L, int32_t *status) {
+  // Re: a - l_re u_re + l_im u_im;  Im: a - l_re u_im - l_im u_re (operands selected, so
+  // that the two lanes of a pair run the same instructions)
+  bool trunc = false;
+  Term t[3] = {{a, a, false, false}, {lre, c ? uim : ure, true, true}, {lim, c ? ure : uim, true, c != 0}};
+  const bool ok = sum_round(t, 3, p, L, M.out(c, r, col), &trunc);
+  if (trunc) atomicOr(reinterpret_cast<int *>(status) + kStTruncated, 1);
+  if (!ok) atomicOr(reinterpret_cast<int *>(status) + kStErange, 1);
+}
+
+// Component c of the complex quotient a / d, RN_p of its exact value, into o (the
+// register-resident form for L = 4, 8 when its windows fit, else the generic one).
+// 1: done, 0: exponent overflow, 2: d == 0 (nothing written).
+__device__ __noinline__ int cdiv_part(int c, const MPRef &are, const MPRef &aim, const MPRef &dre, const MPRef &dim,
+                                      int p, int L, MPOut o, bool *trunc) {
+  *trunc = false;
+  int rf = -1;
+  if (L == 8) rf = fastmp::cdiv_part<8>(are, aim, dre, dim, c, p, o);
+  else if (L == 4) rf = fastmp::cdiv_part<4>(are, aim, dre, dim, c, p, o);
+  if (rf >= 0) return rf;
+  uint64_t den[kWinLimbs], num[kWinLimbs];
+  int nwd, nwn;
+  int64_t lsbd, lsbn;
+  bool negd, negn, tr;
+  Term td[2] = {{dre, dre, true, false}, {dim, dim, true, false}};
+  if (!mp_sum_exact(td, 2, L, den, &nwd, &lsbd, &negd, &tr)) return 2;
+  *trunc |= tr;
+  Term t0[2] = {{are, dre, true, false}, {aim, dim, true, false}};   // a_re d_re + a_im d_im
+  Term t1[2] = {{aim, dre, true, false}, {are, dim, true, true}};    // a_im d_re - a_re d_im
+  const bool nz = mp_sum_exact(c == 0 ? t0 : t1, 2, L, num, &nwn, &lsbn, &negn, &tr);
+  *trunc |= tr;
+  if (!nz) {
+    store_zero(L, o.s, o.e, o.limb, o.stride);
+    return 1;
+  }
+  return mp_div_round(num, nwn, lsbn, negn, den, nwd, lsbd, p, L, o) ? 1 : 0;
+}
+
+// a / d into (r, col) of M by two adjacent lanes, lane parity = component; the result is
+// held in registers until both lanes have read their operands (the output may be a
+// itself).  Every lane of the warp must call it (`active`: this lane has an element).
+__device__ __forceinline__ void cdiv_pair_store(const MatRW &M, int64_t r, int64_t col, bool active, const MPRef &are,
+                                                const MPRef &aim, const MPRef &dre, const MPRef &dim, int p, int L,
+                                                int32_t *status) {
+  const int c = threadIdx.x & 1;
+  uint8_t sg = 0;
+  int32_t ex = 0;
+  uint64_t lm[kMaxLimbs];
+  MPOut tmp{&sg, &ex, lm, 1};
+  int rf = 2;
+  bool tr = false;
+  if (active) rf = cdiv_part(c, are, aim, dre, dim, p, L, tmp, &tr);
+  __syncwarp();
+  if (!active || rf == 2) return;   // d == 0: refused earlier
+  MPOut o = M.out(c, r, col);
+  *o.s = sg;
+  *o.e = ex;
+  for (int j = 0; j < L; ++j) o.limb[(int64_t)j * o.stride] = lm[j];
+  if (tr) atomicOr(reinterpret_cast<int *>(status) + kStTruncated, 1);
+  if (rf == 0) atomicOr(reinterpret_cast<int *>(status) + kStErange, 1);
+}
+
 // the pivot key RN_p(|re| + |im|) as comparable words: (zero?, exponent, limbs)
 struct Key {
   int32_t e;
@@ -133,13 +199,35 @@ __device__ __forceinline__ bool key_greater(const Key &a, const Key &b, int L) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_lu_pivot(MatRW A, int64_t n, int64_t j, int p, int L, int32_t *ipiv,
-                                                  int32_t *status) {
-  __shared__ int64_t best_row[256];
-  __shared__ Key keys[256];
+// (key, row) of the better candidate: the larger key, the first row among equal keys
+__device__ __forceinline__ void pivot_take(Key &k, int64_t &row, const Key &ok, int64_t orow, int L) {
+  if (orow < 0) return;
+  if (row < 0 || key_greater(ok, k, L) || (!key_greater(k, ok, L) && orow < row)) {
+    k = ok;
+    row = orow;
+  }
+}
+
+__device__ __forceinline__ void pivot_shfl(Key &k, int64_t &row, int off, int L) {
+  Key o;
+  o.e = __shfl_down_sync(0xffffffffu, k.e, off);
+  o.nz = __shfl_down_sync(0xffffffffu, (int)k.nz, off) != 0;
+  for (int x = 0; x < L; ++x) o.m[x] = __shfl_down_sync(0xffffffffu, k.m[x], off);
+  const int64_t orow = __shfl_down_sync(0xffffffffu, row, off);
+  pivot_take(k, row, o, orow, L);
+}
+
+constexpr int kPivotT = 512;
+static_assert(kPivotT % 32 == 0 && kPivotT / 32 <= 32, "one warp reduces the per-warp candidates");
+
+__global__ void __launch_bounds__(kPivotT) k_lu_pivot(MatRW A, int64_t n, int64_t j, int p, int L, int32_t *ipiv,
+                                                      int32_t *status) {
+  __shared__ Key keys[kPivotT / 32];
+  __shared__ int64_t rows[kPivotT / 32];
   Key best;
   best.nz = false;
   best.e = 0;
+  for (int x = 0; x < kMaxLimbs; ++x) best.m[x] = 0;
   int64_t brow = -1;
   for (int64_t i = j + threadIdx.x; i < n; i += blockDim.x) {
     MPRef re = A.ref(0, i, j), im = A.ref(1, i, j);
@@ -152,26 +240,26 @@ __global__ void __launch_bounds__(256) k_lu_pivot(MatRW A, int64_t n, int64_t j,
     bool tr;
     sum_round(t, 2, p, L, o, &tr);
     k.nz = k.m[L - 1] != 0;
-    if (brow < 0 || key_greater(k, best, L)) {
-      best = k;
-      brow = i;
-    }
+    pivot_take(best, brow, k, i, L);
   }
-  keys[threadIdx.x] = best;
-  best_row[threadIdx.x] = brow;
+  for (int off = 16; off > 0; off >>= 1) pivot_shfl(best, brow, off, L);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    keys[w] = best;
+    rows[w] = brow;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    Key kb = keys[0];
-    int64_t rb = best_row[0];
-    for (int t = 1; t < (int)blockDim.x; ++t) {
-      if (best_row[t] < 0) continue;
-      if (rb < 0 || key_greater(keys[t], kb, L) || (!key_greater(kb, keys[t], L) && best_row[t] < rb)) {
-        kb = keys[t];
-        rb = best_row[t];
-      }
+  if (w == 0) {
+    brow = -1;   // lanes beyond the block's warp count hold no candidate
+    if (lane < kPivotT / 32) {
+      best = keys[lane];
+      brow = rows[lane];
     }
-    ipiv[j] = (int32_t)rb;
-    if (!kb.nz && status[kStSingular] == 0) status[kStSingular] = (int32_t)(j + 1);
+    for (int off = 16; off > 0; off >>= 1) pivot_shfl(best, brow, off, L);
+    if (lane == 0) {
+      ipiv[j] = (int32_t)brow;
+      if (!best.nz && status[kStSingular] == 0) status[kStSingular] = (int32_t)(j + 1);
+    }
   }
 }
 
@@ -195,21 +283,24 @@ __global__ void k_lu_swap(MatRW A, int64_t ncols, int64_t j, const int32_t *ipiv
   }
 }
 
+// two lanes per element, one per component
 __global__ void k_lu_divide(MatRW A, int64_t n, int64_t j, int p, int L, int32_t *status) {
-  const int64_t i = j + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || status[kStSingular]) return;
-  cdiv_store(A, i, j, A.ref(0, i, j), A.ref(1, i, j), A.ref(0, j, j), A.ref(1, j, j), p, L, status);
+  const int64_t i = j + 1 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 2;
+  const bool active = i < n && !status[kStSingular];
+  const int64_t r = active ? i : j;
+  cdiv_pair_store(A, i, j, active, A.ref(0, r, j), A.ref(1, r, j), A.ref(0, j, j), A.ref(1, j, j), p, L, status);
 }
 
-// a_ic = RN(a_ic - a_ij a_jc) for i in [r0, r1), c in [c0, c1)
+// a_ic = RN(a_ic - a_ij a_jc) for i in [r0, r1), c in [c0, c1); two lanes per element
 __global__ void k_lu_rank1(MatRW A, int64_t j, int64_t r0, int64_t r1, int64_t c0, int64_t c1, int p, int L,
                            int32_t *status) {
   const int64_t w = c1 - c0;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 2;
+  const int c = threadIdx.x & 1;
   if (t >= (r1 - r0) * w || status[kStSingular]) return;
   const int64_t i = r0 + t / w, col = c0 + t % w;
-  cfma_store(A, i, col, A.ref(0, i, col), A.ref(1, i, col), A.ref(0, i, j), A.ref(1, i, j), A.ref(0, j, col),
-             A.ref(1, j, col), p, L, status);
+  cfma_part(A, i, col, c, A.ref(c, i, col), A.ref(0, i, j), A.ref(1, i, j), A.ref(0, j, col), A.ref(1, j, col), p, L,
+            status);
 }
 
 // the GEMM's device-side failures count for the LU as well
@@ -237,18 +328,15 @@ __global__ void k_copy_block(MatRW A, int64_t r0, int64_t c0, int64_t rows, int6
 // A[r0 + r][c0 + col] = RN(A - P[r][col]) componentwise
 __global__ void k_sub_block(MatRW A, int64_t r0, int64_t c0, int64_t rows, int64_t cols, MatRW P, int p, int L,
                             int32_t *status) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 2;   // two lanes per element
+  const int c = threadIdx.x & 1;
   if (t >= rows * cols || status[kStSingular]) return;
   const int64_t r = t / cols, col = t % cols;
-  bool trunc = false, ok = true;
-  for (int c = 0; c < 2; ++c) {
-    MPRef a = A.ref(c, r0 + r, c0 + col), q = P.ref(c, r, col);
-    Term tt[2] = {{a, a, false, false}, {q, q, false, true}};
-    bool tr;
-    ok &= sum_round(tt, 2, p, L, A.out(c, r0 + r, c0 + col), &tr);
-    trunc |= tr;
-  }
-  if (trunc) atomicOr(reinterpret_cast<int *>(status) + kStTruncated, 1);
+  MPRef a = A.ref(c, r0 + r, c0 + col), q = P.ref(c, r, col);
+  Term tt[2] = {{a, a, false, false}, {q, q, false, true}};
+  bool tr;
+  const bool ok = sum_round(tt, 2, p, L, A.out(c, r0 + r, c0 + col), &tr);
+  if (tr) atomicOr(reinterpret_cast<int *>(status) + kStTruncated, 1);
   if (!ok) atomicOr(reinterpret_cast<int *>(status) + kStErange, 1);
 }
 
@@ -323,32 +411,42 @@ __global__ void k_solve_perm(MatRW Bm, int64_t n, int64_t nrhs, const int32_t *i
   }
 }
 
-// forward step j (unit lower L): y_i = RN(y_i - l_ij y_j) for j < i < n
+// forward step j (unit lower L): y_i = RN(y_i - l_ij y_j) for j < i < n; two lanes per row
 __global__ void k_solve_fwd(MatRW LU, int64_t n, int64_t j, MatRW Bm, int64_t col0, int p, int L, int32_t *status) {
   const int64_t col = col0 + blockIdx.y;
-  const int64_t i = j + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = j + 1 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 2;
+  const int c = threadIdx.x & 1;
   if (i >= n || status[kStSingular]) return;
-  cfma_store(Bm, i, col, Bm.ref(0, i, col), Bm.ref(1, i, col), LU.ref(0, i, j), LU.ref(1, i, j), Bm.ref(0, j, col),
-             Bm.ref(1, j, col), p, L, status);
+  cfma_part(Bm, i, col, c, Bm.ref(c, i, col), LU.ref(0, i, j), LU.ref(1, i, j), Bm.ref(0, j, col), Bm.ref(1, j, col), p,
+            L, status);
 }
 
-// x_j = RN(y_j / u_jj) for the last row (the first backward step)
+// x_j = RN(y_j / u_jj) for the last row (the first backward step); two lanes per column
 __global__ void k_solve_last(MatRW LU, int64_t j, MatRW Bm, int64_t nrhs, int p, int L, int32_t *status) {
-  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= nrhs || status[kStSingular]) return;
-  cdiv_store(Bm, j, col, Bm.ref(0, j, col), Bm.ref(1, j, col), LU.ref(0, j, j), LU.ref(1, j, j), p, L, status);
+  const int64_t col = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 2;
+  const bool active = col < nrhs && !status[kStSingular];
+  const int64_t cc = active ? col : 0;
+  cdiv_pair_store(Bm, j, col, active, Bm.ref(0, j, cc), Bm.ref(1, j, cc), LU.ref(0, j, j), LU.ref(1, j, j), p, L,
+                  status);
 }
 
-// backward step j (upper U, x_j already in row j): y_i = RN(y_i - u_ij x_j) for i < j;
-// the thread of row j - 1 then forms x_{j-1} = RN(y_{j-1} / u_{j-1,j-1}) for the next step
+// backward step j (upper U, x_j already in row j): y_i = RN(y_i - u_ij x_j) for i < j,
+// two lanes per row; the lane pair of row j - 1 then forms x_{j-1} = RN(y_{j-1} / u_{j-1,j-1})
+// for the next step (after a warp barrier: each lane needs the other's component of y_{j-1})
 __global__ void k_solve_bwd(MatRW LU, int64_t j, MatRW Bm, int64_t col0, int p, int L, int32_t *status) {
   const int64_t col = col0 + blockIdx.y;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= j || status[kStSingular]) return;
-  cfma_store(Bm, i, col, Bm.ref(0, i, col), Bm.ref(1, i, col), LU.ref(0, i, j), LU.ref(1, i, j), Bm.ref(0, j, col),
-             Bm.ref(1, j, col), p, L, status);
-  if (i == j - 1)
-    cdiv_store(Bm, i, col, Bm.ref(0, i, col), Bm.ref(1, i, col), LU.ref(0, i, i), LU.ref(1, i, i), p, L, status);
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 2;
+  const int c = threadIdx.x & 1;
+  const bool live = !status[kStSingular];
+  if (i < j && live)
+    cfma_part(Bm, i, col, c, Bm.ref(c, i, col), LU.ref(0, i, j), LU.ref(1, i, j), Bm.ref(0, j, col),
+              Bm.ref(1, j, col), p, L, status);
+  if ((int64_t)blockIdx.x * blockDim.x / 2 > j - 1 || (int64_t)(blockIdx.x + 1) * blockDim.x / 2 <= j - 1) return;
+  __syncwarp();   // the warp holding row j - 1 (block-uniform test above: every lane of it is here)
+  const bool act = i == j - 1 && live;
+  const int64_t r = act ? i : j - 1;
+  cdiv_pair_store(Bm, r, col, act, Bm.ref(0, r, col), Bm.ref(1, r, col), LU.ref(0, r, r), LU.ref(1, r, r), p, L,
+                  status);
 }
 
 }  // namespace mpc
@@ -462,17 +560,17 @@ extern "C" int mpcgesv(int64_t n, int32_t p_bits, mpc_mat *A, int32_t *ipiv, mpc
   for (int64_t kb = 0; kb < n; kb += K) {
     const int64_t kend = kb + K < n ? kb + K : n;
     for (int64_t j = kb; j < kend; ++j) {
-      k_lu_pivot<<<1, 256, 0, st>>>(Am, n, j, p_bits, L, ipiv, status);
+      k_lu_pivot<<<1, kPivotT, 0, st>>>(Am, n, j, p_bits, L, ipiv, status);
       k_lu_swap<<<blocks_for(n, 128), 128, 0, st>>>(Am, n, j, ipiv, L);
-      if (j + 1 < n) k_lu_divide<<<blocks_for(n - j - 1, 64), 64, 0, st>>>(Am, n, j, p_bits, L, status);
+      if (j + 1 < n) k_lu_divide<<<blocks_for(2 * (n - j - 1), 64), 64, 0, st>>>(Am, n, j, p_bits, L, status);
       if (j + 1 < n && j + 1 < kend)   // rest of the panel
-        k_lu_rank1<<<blocks_for((n - j - 1) * (kend - j - 1), 64), 64, 0, st>>>(Am, j, j + 1, n, j + 1, kend, p_bits,
+        k_lu_rank1<<<blocks_for(2 * (n - j - 1) * (kend - j - 1), 64), 64, 0, st>>>(Am, j, j + 1, n, j + 1, kend, p_bits,
                                                                                    L, status);
     }
     // U12 = L11^-1 A12, once every interchange of the panel has been applied
     if (kend < n)
       for (int64_t j = kb; j + 1 < kend; ++j)
-        k_lu_rank1<<<blocks_for((kend - j - 1) * (n - kend), 64), 64, 0, st>>>(Am, j, j + 1, kend, kend, n, p_bits,
+        k_lu_rank1<<<blocks_for(2 * (kend - j - 1) * (n - kend), 64), 64, 0, st>>>(Am, j, j + 1, kend, kend, n, p_bits,
                                                                                    L, status);
     if (kend < n) {   // trailing update A22 -= L21 U12 through the Ozaki complex GEMM
       const int64_t rest = n - kend, w = kend - kb;
@@ -486,7 +584,7 @@ extern "C" int mpcgesv(int64_t n, int32_t p_bits, mpc_mat *A, int32_t *ipiv, mpc
                    stream);
       if (rc != MPC_OK) return rc;
       k_fold_status<<<1, 32, 0, st>>>(status, (const int32_t *)(ws + lay.off_gemm));
-      k_sub_block<<<blocks_for(rest * rest, 64), 64, 0, st>>>(Am, kend, kend, rest, rest, Pm, p_bits, L, status);
+      k_sub_block<<<blocks_for(2 * rest * rest, 64), 64, 0, st>>>(Am, kend, kend, rest, rest, Pm, p_bits, L, status);
     }
   }
   // solve: forward then backward substitution, every element's operations in the same
@@ -501,12 +599,12 @@ extern "C" int mpcgesv(int64_t n, int32_t p_bits, mpc_mat *A, int32_t *ipiv, mpc
     k_solve_perm<<<blocks_for(nrhs, kT), kT, 0, st>>>(Bm, n, nrhs, ipiv, L, status);
     for (int64_t j = 0; j + 1 < n; ++j)
       for (int64_t c0 = 0; c0 < nrhs; c0 += kMaxGridY)
-        k_solve_fwd<<<dim3(blocks_for(n - j - 1, kT), (unsigned)std::min(kMaxGridY, nrhs - c0)), kT, 0, st>>>(
+        k_solve_fwd<<<dim3(blocks_for(2 * (n - j - 1), kT), (unsigned)std::min(kMaxGridY, nrhs - c0)), kT, 0, st>>>(
             Am, n, j, Bm, c0, p_bits, L, status);
-    k_solve_last<<<blocks_for(nrhs, kT), kT, 0, st>>>(Am, n - 1, Bm, nrhs, p_bits, L, status);
+    k_solve_last<<<blocks_for(2 * nrhs, kT), kT, 0, st>>>(Am, n - 1, Bm, nrhs, p_bits, L, status);
     for (int64_t j = n - 1; j >= 1; --j)
       for (int64_t c0 = 0; c0 < nrhs; c0 += kMaxGridY)
-        k_solve_bwd<<<dim3(blocks_for(j, kT), (unsigned)std::min(kMaxGridY, nrhs - c0)), kT, 0, st>>>(
+        k_solve_bwd<<<dim3(blocks_for(2 * j, kT), (unsigned)std::min(kMaxGridY, nrhs - c0)), kT, 0, st>>>(
             Am, j, Bm, c0, p_bits, L, status);
   }
   const cudaError_t e = cudaGetLastError();

@@ -215,91 +215,93 @@ __device__ __forceinline__ int sum_round(const Term *t, int nt, int p, MPOut o) 
 
 // RN_p of num / den for exact magnitudes num 2^lsb_n, den 2^lsb_d (W words each, both
 // nonzero): Q = floor(num 2^sh / den) with p + 3 or p + 4 bits by long division on
-// 32-bit digits (Knuth, TAOCP vol. 2, Sec. 4.3.1, Algorithm D) with compile-time
-// lengths: the divisor is shifted so that its leading one is bit 64 W - 1, the dividend
-// so that it has 64 W + p + 3 bits.  The remainder gives a sticky bit below Q.
+// 64-bit digits (Knuth, TAOCP vol. 2, Sec. 4.3.1, Algorithm D; each trial digit from a
+// 128-by-64-bit division of the top two words, corrected with the divisor's second word)
+// with compile-time lengths: the divisor is shifted so that its leading one is bit
+// 64 W - 1, the dividend so that it has 64 W + p + 3 bits.  The remainder gives a sticky
+// bit below Q.
 template <int L, int W>
 __device__ __forceinline__ bool div_round(const uint64_t (&num)[W], int64_t lsb_n, bool neg,
                                           const uint64_t (&den)[W], int64_t lsb_d, int p, MPOut o) {
   constexpr int UW = W + L + 1;            // dividend words: 64 W + p + 3 < 64 UW
-  constexpr int n = 2 * W, m = 2 * UW;     // divisor and dividend digits
-  constexpr int QN = m - n + 1;            // quotient digits
+  constexpr int QN = UW - W + 1;           // quotient digits
   int nN = 0, nD = 0;
 #pragma unroll
   for (int w = W - 1; w >= 0; --w) {
     if (nN == 0 && num[w]) nN = 64 * w + 64 - __clzll((long long)num[w]);
     if (nD == 0 && den[w]) nD = 64 * w + 64 - __clzll((long long)den[w]);
   }
-  uint64_t dv[W];
+  uint64_t v[W];
 #pragma unroll
-  for (int w = 0; w < W; ++w) dv[w] = den[w];
-  shl<W>(dv, 64 * W - nD);
+  for (int w = 0; w < W; ++w) v[w] = den[w];
+  shl<W>(v, 64 * W - nD);
   const int shift_u = p + 3 + 64 * W - nN;   // > 0: no dividend bit is dropped
   uint64_t uv[UW];
 #pragma unroll
   for (int w = 0; w < UW; ++w) uv[w] = w < W ? num[w] : 0ull;
   shl<UW>(uv, shift_u);
-  uint32_t u[m + 1], v[n], q[QN];
+  uint64_t u[UW + 1];
 #pragma unroll
-  for (int i = 0; i < UW; ++i) {
-    u[2 * i] = (uint32_t)uv[i];
-    u[2 * i + 1] = (uint32_t)(uv[i] >> 32);
-  }
-  u[m] = 0;
+  for (int w = 0; w < UW; ++w) u[w] = uv[w];
+  u[UW] = 0;
+  uint64_t q[QN];
 #pragma unroll
-  for (int i = 0; i < W; ++i) {
-    v[2 * i] = (uint32_t)dv[i];
-    v[2 * i + 1] = (uint32_t)(dv[i] >> 32);
-  }
-#pragma unroll
-  for (int j = m - n; j >= 0; --j) {
-    const uint64_t num2 = ((uint64_t)u[j + n] << 32) | u[j + n - 1];
-    uint64_t qhat = num2 / v[n - 1];
-    uint64_t rhat = num2 - qhat * v[n - 1];
-    while (qhat >= (1ull << 32) || qhat * v[n - 2] > ((rhat << 32) | u[j + n - 2])) {
+  for (int j = QN - 1; j >= 0; --j) {
+    uint64_t qhat, rhat;
+    bool rbig = false;   // rhat >= 2^64: the correction test cannot fail
+    if (u[j + W] >= v[W - 1]) {   // (only equality can occur) qhat = 2^64 - 1
+      qhat = ~0ull;
+      const unsigned __int128 r = (unsigned __int128)u[j + W - 1] + v[W - 1];
+      rbig = (uint64_t)(r >> 64) != 0;
+      rhat = (uint64_t)r;
+    } else {
+      const unsigned __int128 top = ((unsigned __int128)u[j + W] << 64) | u[j + W - 1];
+      qhat = (uint64_t)(top / v[W - 1]);
+      rhat = (uint64_t)(top - (unsigned __int128)qhat * v[W - 1]);
+    }
+    while (!rbig && (unsigned __int128)qhat * v[W - 2] > (((unsigned __int128)rhat << 64) | u[j + W - 2])) {
       --qhat;
-      rhat += v[n - 1];
-      if (rhat >= (1ull << 32)) break;
+      const unsigned __int128 r = (unsigned __int128)rhat + v[W - 1];
+      rbig = (uint64_t)(r >> 64) != 0;
+      rhat = (uint64_t)r;
     }
-    int64_t borrow = 0;   // multiply and subtract
+    uint64_t borrow = 0;   // u[j .. j + W] -= qhat v
 #pragma unroll
-    for (int i = 0; i < n; ++i) {
-      const uint64_t prod = qhat * v[i];
-      const int64_t t = (int64_t)u[i + j] - borrow - (int64_t)(prod & 0xFFFFFFFFull);
-      u[i + j] = (uint32_t)t;
-      borrow = (int64_t)(prod >> 32) - (t >> 32);
+    for (int i = 0; i < W; ++i) {
+      const unsigned __int128 pr = (unsigned __int128)qhat * v[i] + borrow;
+      const uint64_t lo = (uint64_t)pr;
+      borrow = (uint64_t)(pr >> 64);
+      const uint64_t t = u[i + j] - lo;
+      borrow += u[i + j] < lo ? 1ull : 0ull;
+      u[i + j] = t;
     }
-    const int64_t t = (int64_t)u[j + n] - borrow;
-    u[j + n] = (uint32_t)t;
-    if (t < 0) {   // qhat was one too large: add the divisor back
+    const bool below = u[j + W] < borrow;
+    u[j + W] -= borrow;
+    if (below) {   // qhat was one too large: add the divisor back
       --qhat;
       uint64_t carry = 0;
 #pragma unroll
-      for (int i = 0; i < n; ++i) {
-        const uint64_t s2 = (uint64_t)u[i + j] + v[i] + carry;
-        u[i + j] = (uint32_t)s2;
-        carry = s2 >> 32;
+      for (int i = 0; i < W; ++i) {
+        const unsigned __int128 s2 = (unsigned __int128)u[i + j] + v[i] + carry;
+        u[i + j] = (uint64_t)s2;
+        carry = (uint64_t)(s2 >> 64);
       }
-      u[j + n] += (uint32_t)carry;
+      u[j + W] += carry;
     }
-    q[j] = (uint32_t)qhat;
+    q[j] = qhat;
   }
   bool sticky = false;
 #pragma unroll
-  for (int i = 0; i < n; ++i) sticky |= u[i] != 0;
+  for (int i = 0; i < W; ++i) sticky |= u[i] != 0;
   // Q' = 2 Q + sticky, value Q' 2^(lsb_n - lsb_d - (shift_u - 64 W + nD) - 1)
-  constexpr int QW = (QN + 1) / 2 + 1;
+  constexpr int QW = QN + 1;
   uint64_t Qs[QW];
-#pragma unroll
-  for (int i = 0; i < QW; ++i) Qs[i] = 0;
-#pragma unroll
-  for (int i = 0; i < QN; ++i) Qs[i >> 1] |= (uint64_t)q[i] << (32 * (i & 1));
   uint64_t c = sticky ? 1ull : 0ull;
 #pragma unroll
   for (int i = 0; i < QW; ++i) {
-    const uint64_t nc = Qs[i] >> 63;
-    Qs[i] = (Qs[i] << 1) | c;
-    c = nc;
+    const uint64_t w = i < QN ? q[i] : 0ull;
+    Qs[i] = (w << 1) | c;
+    c = w >> 63;
   }
   return round_store_w<L, QW>(Qs, lsb_n - lsb_d - (int64_t)(shift_u - 64 * W + nD) - 1, neg, p, o);
 }
@@ -351,6 +353,33 @@ __device__ __forceinline__ int cdiv(const MPRef &are, const MPRef &aim, const MP
     for (int j = 0; j < L; ++j) outs[c].limb[(int64_t)j * outs[c].stride] = lm[c][j];
   }
   return 1;
+}
+
+// Component c (0: real, 1: imaginary) of the complex quotient a / d into o: RN_p of
+// (a_re d_re + a_im d_im) / |d|^2 or (a_im d_re - a_re d_im) / |d|^2.  1 / 0 / -1 / 2 as cdiv.
+template <int L>
+__device__ __forceinline__ int cdiv_part(const MPRef &are, const MPRef &aim, const MPRef &dre, const MPRef &dim, int c,
+                                         int p, MPOut o) {
+  constexpr int W = 2 * L + 3;
+  uint64_t den[W], num[W];
+  int64_t bd, bn;
+  bool nd, nn;
+  Term td[2] = {{dre, dre, true, false}, {dim, dim, true, false}};
+  const int rd = sum_exact<L, W>(td, 2, den, bd, nd);
+  if (rd < 0) return -1;
+  if (rd == 0) return 2;
+  Term t0[2] = {{are, dre, true, false}, {aim, dim, true, false}};
+  Term t1[2] = {{aim, dre, true, false}, {are, dim, true, true}};
+  const int rn = sum_exact<L, W>(c == 0 ? t0 : t1, 2, num, bn, nn);
+  if (rn < 0) return -1;
+  bool nz = false;
+#pragma unroll
+  for (int w = 0; w < W; ++w) nz |= rn > 0 && num[w] != 0;
+  if (!nz) {
+    store_zero(L, o.s, o.e, o.limb, o.stride);
+    return 1;
+  }
+  return div_round<L, W>(num, bn, nn, den, bd, p, o) ? 1 : 0;
 }
 
 }  // namespace fastmp
