@@ -522,14 +522,16 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     method = args.method
     algo = args.algo
-    params = {"kernel": args.kernel} if algo == "ozaki" else None
+    if args.split != "common" and (method != "4m" or algo != "ozaki"):
+        raise SystemExit("--split per_part / residual is a 4M Ozaki option")
+    params = {"kernel": args.kernel, "split": args.split, "pair_planes": args.pair_planes} if algo == "ozaki" else None
     pl = mp.plan(m, n, k, p, method, algo, params)
     ws = mp.Workspace(dev)
     ws.get(pl["ws_bytes"])
 
     def timed(method_, algo_, steps, warmup, with_events=False):
         evs = []
-        prm = params if algo_ == "ozaki" else None
+        prm = dict(params, split=args.split if method_ == "4m" else "common") if algo_ == "ozaki" else None
         for _ in range(warmup):
             mp.mpcgemm(dA, dB, dC, p, method_, algo_, workspace=ws, stream=stream, params=prm)
         torch.cuda.synchronize(dev)
@@ -614,7 +616,8 @@ def run_ours(args):
     if algo == "plain":
         roofline = plain_roofline(mp, m, n, k, p, method, gemm_ms)
     else:   # the HBM-bound stages around the slice GEMM, against the measured copy bandwidth
-        extras["hbm_stages"] = hbm_stage_rooflines(pl, m, n, k, stages, float(peaks["hbm_gbs"]), peak_src)
+        if args.split != "residual":   # (the residual split interleaves its accumulation with the products)
+            extras["hbm_stages"] = hbm_stage_rooflines(pl, m, n, k, stages, float(peaks["hbm_gbs"]), peak_src)
 
     # e2e through the public API with host buffers: every step copies its inputs from
     # pinned host memory and its result back, inside the timed region.  Two device
@@ -697,7 +700,7 @@ def run_ours(args):
             "data": "synthetic (seeded)",
             "config": {"workload": f"{args.workload}: {algo} {method}, m=n=k={m}, p={p} bits, entries u*2^e, "
                                    "e in [-20,20]", "method": method, "algo": algo, "m": m, "n": n, "k": k,
-                       "p_bits": p, "kernel": args.kernel, "slices": pl["s"], "cut_level_Q": pl["Q"], "pairs": pairs,
+                       "p_bits": p, "kernel": args.kernel, "split": args.split, "slices": pl["s"], "cut_level_Q": pl["Q"], "pairs": pairs,
                        "l2": "inputs (A, B: %.2f GB) larger than L2 (126 MB)" % ((A.nbytes() + B.nbytes()) / 1e9),
                        "parallelism": f"replicas x{ws_}"},
             "stage_ms": {"split": stages[0], "slice_gemm": stages[1], "accumulate_round": stages[2],
@@ -832,6 +835,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched side measurement")
     ap.add_argument("--no-lu", action="store_true", help="skip the LU and serving side measurements")
     ap.add_argument("--method", choices=["3m", "4m"], default="3m")
+    ap.add_argument("--split", choices=["common", "per_part", "residual"], default="common",
+                    help="how the operands are cut (4M Ozaki only; default: one grid per line)")
+    ap.add_argument("--pair-planes", type=int, default=0,
+                    help="residual split: planes in the pair-product buffer (0: the library's default)")
     ap.add_argument("--algo", choices=["ozaki", "plain"], default="ozaki",
                     help="the timed step's algorithm (plain: the CUDA-core GEMM, no side measurements)")
     ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_n128", "tcgen05_2sm", "mma_sync"], default="auto",
