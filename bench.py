@@ -841,7 +841,7 @@ def main():
                     help="residual split: planes in the pair-product buffer (0: the library's default)")
     ap.add_argument("--algo", choices=["ozaki", "plain"], default="ozaki",
                     help="the timed step's algorithm (plain: the CUDA-core GEMM, no side measurements)")
-    ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_n128", "tcgen05_2sm", "mma_sync"], default="auto",
+    ap.add_argument("--kernel", choices=["auto", "tcgen05", "tcgen05_n128", "tcgen05_2sm", "tcgen05_2sm_n128", "mma_sync"], default="auto",
                     help="slice-GEMM kernel")
     ap.add_argument("--quick", action="store_true", help="skip the 4M / plain side measurements")
     ap.add_argument("--no-sweep", action="store_true", help="skip the precision sweep (n 1024/2048, p 256/512/1024)")

@@ -78,7 +78,7 @@ enum { MPC_PLAIN = 0, MPC_OZAKI = 1 };    /* Eq. (simple_triple_loop) / Alg. 2 *
 enum { MPC_SPLIT_COMMON = 0, MPC_SPLIT_PER_PART = 1, MPC_SPLIT_RESIDUAL = 2 };
 /* Slice-GEMM kernels (value 3 is not used and is rejected). */
 enum { MPC_KERNEL_AUTO = 0, MPC_KERNEL_TCGEN05 = 1, MPC_KERNEL_MMA_SYNC = 2, MPC_KERNEL_TCGEN05_2SM = 4,
-       MPC_KERNEL_TCGEN05_N128 = 5 };
+       MPC_KERNEL_TCGEN05_N128 = 5, MPC_KERNEL_TCGEN05_2SM_N128 = 6 };
 
 /* Largest supported precision and inner size. */
 #define MPC_MAX_P_BITS 1024
@@ -110,8 +110,10 @@ typedef struct mpc_mat {
  *               CTAs with 128 x 256 tiles and two TMEM accumulators; TCGEN05_N128
  *               single CTAs with 128 x 128 tiles and four; TCGEN05_2SM CTA pairs
  *               that run one 256-row MMA across both SMs, each loading its own
- *               rows of A and half of B; the mma.sync kernel is a second,
- *               independent implementation of the same sums).
+ *               rows of A and half of B, 256 columns (two accumulators per CTA);
+ *               TCGEN05_2SM_N128 the same with 128 columns (four accumulators
+ *               per CTA); the mma.sync kernel is a second, independent
+ *               implementation of the same sums).
  *   wait_limit_cycles
  *               SM clock cycles that one barrier wait of the tcgen05 kernels may
  *               last before the kernel gives up (0 -> about 4e9, some 2 s).  A

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libmpcgemm.so")
 MPC_OK, MPC_EINVAL, MPC_ENOSPC, MPC_ERANGE, MPC_ENOTSUP, MPC_ECUDA = 0, -22, -28, -34, -95, -1000
 METHODS = {"4m": 0, "3m": 1}
 ALGOS = {"plain": 0, "ozaki": 1}
-KERNELS = {"auto": 0, "tcgen05": 1, "mma_sync": 2, "tcgen05_2sm": 4, "tcgen05_n128": 5}
+KERNELS = {"auto": 0, "tcgen05": 1, "mma_sync": 2, "tcgen05_2sm": 4, "tcgen05_n128": 5, "tcgen05_2sm_n128": 6}
 
 EXPORTED = ("mpcgemm", "mpcgemm_ex", "mpcgemm_profiled", "mpcgemm_workspace_size", "mpcgemm_plan",
             "mpcgemm_read_status", "mpcgemm_noalloc", "mpcgemm_noalloc_read_status", "mpcgemm_batched", "mpcgemm_batched_workspace",

@@ -89,7 +89,8 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
   P.limbs = L;
   out->kernel = prm ? prm->kernel : MPC_KERNEL_AUTO;
   if (out->kernel != MPC_KERNEL_AUTO && out->kernel != MPC_KERNEL_TCGEN05 && out->kernel != MPC_KERNEL_MMA_SYNC &&
-      out->kernel != MPC_KERNEL_TCGEN05_2SM && out->kernel != MPC_KERNEL_TCGEN05_N128)
+      out->kernel != MPC_KERNEL_TCGEN05_2SM && out->kernel != MPC_KERNEL_TCGEN05_N128 &&
+      out->kernel != MPC_KERNEL_TCGEN05_2SM_N128)
     return MPC_EINVAL;
   if (prm && prm->wait_limit_cycles < 0) return MPC_EINVAL;
   P.split = prm ? prm->split : MPC_SPLIT_COMMON;
@@ -268,7 +269,10 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
 
 // the tcgen05 variant of a kernel choice (auto: single CTAs with 128 x 256 tiles)
 int tile_of(int kernel) {
-  return kernel == MPC_KERNEL_TCGEN05_2SM ? kTile2Sm : kernel == MPC_KERNEL_TCGEN05_N128 ? kTileNarrow : kTileSingle;
+  return kernel == MPC_KERNEL_TCGEN05_2SM        ? kTile2Sm
+         : kernel == MPC_KERNEL_TCGEN05_2SM_N128 ? kTile2SmNarrow
+         : kernel == MPC_KERNEL_TCGEN05_N128     ? kTileNarrow
+                                                 : kTileSingle;
 }
 
 int cuda_code(cudaError_t e) { return e == cudaSuccess ? MPC_OK : MPC_ECUDA - (int)e; }

@@ -164,10 +164,11 @@ void launch_plain_digits(const MatView &X, int side, int64_t lines, int64_t k, i
 void launch_group_table(const GroupTableArgs &a, cudaStream_t st);
 void launch_slicegemm_mma(const SliceGemmArgs &a, cudaStream_t st);
 // tile: kTileSingle (one CTA per 128 x 256 tile, two TMEM accumulators), kTile2Sm (CTA
-// pairs running one cta_group::2 MMA of M = 256) or kTileNarrow (one CTA per 128 x 128
-// tile, four TMEM accumulators); wait_limit: cycles a barrier wait may take (0: the
+// pairs running one cta_group::2 MMA of M = 256, N = 256), kTile2SmNarrow (the same with
+// N = 128, four TMEM accumulators per CTA) or kTileNarrow (one CTA per 128 x 128 tile,
+// four TMEM accumulators); wait_limit: cycles a barrier wait may take (0: the
 // default of about 2 s), a positive limit makes the waits poll so that it is exact
-enum { kTileSingle = 0, kTile2Sm = 1, kTileNarrow = 2 };
+enum { kTileSingle = 0, kTile2Sm = 1, kTileNarrow = 2, kTile2SmNarrow = 3 };
 cudaError_t launch_slicegemm_tc(const SliceGemmArgs &a, cudaStream_t st, int tile, long long wait_limit = 0);
 cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cudaStream_t st, int tile,
                                       long long wait_limit = 0);

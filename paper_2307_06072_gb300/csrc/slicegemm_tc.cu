@@ -741,8 +741,9 @@ cudaError_t launch_slicegemm_tc_batch(const SliceGemmArgs *list, int count, cuda
   std::lock_guard<std::mutex> lock(mu);
   for (int q0 = 0; q0 < count; q0 += kMaxBatch) {
     const int c = count - q0 < kMaxBatch ? count - q0 : kMaxBatch;
-    const cudaError_t e = tile == kTile2Sm      ? launch_set<true, 256>(list + q0, c, st, wait_limit)
-                          : tile == kTileNarrow ? launch_set<false, 128>(list + q0, c, st, wait_limit)
+    const cudaError_t e = tile == kTile2Sm         ? launch_set<true, 256>(list + q0, c, st, wait_limit)
+                          : tile == kTile2SmNarrow ? launch_set<true, 128>(list + q0, c, st, wait_limit)
+                          : tile == kTileNarrow    ? launch_set<false, 128>(list + q0, c, st, wait_limit)
                                                 : launch_set<false, 256>(list + q0, c, st, wait_limit);
     if (e != cudaSuccess) return e;
   }

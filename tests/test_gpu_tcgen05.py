@@ -36,7 +36,7 @@ def _planes(A, B, p, method, kernel, w):
     return C, gu.ws_groups(ws, pl, A.rows, B.cols), st
 
 
-@pytest.mark.parametrize("kernel", ["tcgen05", "tcgen05_2sm", "tcgen05_n128"])
+@pytest.mark.parametrize("kernel", ["tcgen05", "tcgen05_2sm", "tcgen05_n128", "tcgen05_2sm_n128"])
 @pytest.mark.parametrize("m,k,n,p,method,dist,w", CASES)
 def test_tcgen05_matches_mma_sync_and_oracle(m, k, n, p, method, dist, w, kernel):
     """(260 rows = 3 row tiles: the 2-SM kernel's second CTA of the last pair has no rows.)"""

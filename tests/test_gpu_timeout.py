@@ -19,7 +19,7 @@ from tests import gpu_util as gu
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("kernel", ["tcgen05", "tcgen05_2sm", "tcgen05_n128"])
+@pytest.mark.parametrize("kernel", ["tcgen05", "tcgen05_2sm", "tcgen05_n128", "tcgen05_2sm_n128"])
 def test_wait_limit_runs_out_then_next_call_is_exact(kernel):
     p = 256
     A = si.random_matrix(256, 512, p, 71, "uniform")
