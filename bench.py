@@ -41,7 +41,7 @@ SWEEP = [f"c2_{n}_p{p}" for n in (1024, 2048) for p in (256, 512, 1024)]
 WORKLOADS = {name: si.config_inputs(name) for name in SWEEP}
 WORKLOADS["c1_256_p256"] = si.config_inputs("c1_ozaki_256_p256")
 BATCH_WORKLOAD = "c3_batch64"
-PROFILE = os.path.join(ROOT, "profiles", "oz_slicegemm_c2_2048_p1024.md")
+PROFILE = os.path.join(ROOT, "profiles", "oz_slicegemm_c2_1024_p1024.md")
 # the slice GEMM kernel and the group table / unit schedule it runs over
 SLICEGEMM_SRC = [os.path.join(ROOT, "paper_2307_06072_gb300", "csrc", f) for f in ("slicegemm_tc.cu", "grouptable.cu")]
 
