@@ -298,9 +298,10 @@ def hbm_stage_rooflines(pl, m, n, k, stages, hbm_gbs, src):
     return out
 
 
-# Plain path roof: 64 IMAD lanes per clock per SM, two lane-operations (low and high
-# word) per 32 x 32 -> 64-bit digit product, 152 SMs at the 2070 MHz maximum SM clock.
-PLAIN_PRODUCTS_PER_CLK_SM = 32
+# Plain path roof: one mad.wide.s32 (a 32 x 32 -> 64-bit digit product added into a 64-bit
+# sum) per IMAD lane per clock, 64 lanes per SM (a register-only loop of independent
+# mad.wide.s32 ran at 60 per clock per SM on a GB300), 152 SMs at the 2070 MHz maximum clock.
+PLAIN_PRODUCTS_PER_CLK_SM = 64
 SMS, MAX_SM_GHZ = 152, 2.07
 
 
@@ -314,7 +315,7 @@ def plain_roofline(mp, m, n, k, p, method, gemm_ms):
             "peak": round(peak / 1e12, 3), "unit": "T digit-products/s (32x32->64 bit)",
             "frac": round(achieved / peak, 4), "traffic": None, "digits": pl["s"],
             "algorithmic_products_per_launch": products, "kernel_ms": round(gemm_ms, 3),
-            "peak_source": "64 IMAD lanes/clk/SM / 2 per wide product x 152 SMs x 2.07 GHz"}
+            "peak_source": "64 mad.wide.s32/clk/SM (60 measured) x 152 SMs x 2.07 GHz"}
 
 
 def pair_count(s: int, Q: int, method: str) -> int:

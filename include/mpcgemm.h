@@ -240,8 +240,10 @@ typedef struct mpc_status {
     int32_t erange;           /* nonzero: some result exponent did not fit int32 */
     int32_t fallback_entries; /* components recomputed exactly (certification failed) */
     int32_t fallback_overflow;/* nonzero: more failures than the list holds */
-    int32_t uncertified;      /* components whose exact window was too wide (rounded
-                                 from a truncated sum; see mpcgemm_read_status) */
+    int32_t uncertified;      /* components whose exact fallback window was too wide
+                                 (their terms span more than 12 288 bits) AND whose
+                                 rounding the truncated window could not certify: only
+                                 these may differ from RN_p of the exact value */
     int32_t device_timeout;   /* nonzero: a kernel's bounded wait gave up (results invalid) */
 } mpc_status;
 

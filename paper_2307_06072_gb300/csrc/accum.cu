@@ -377,7 +377,10 @@ __global__ void k_exact_fallback(FallbackArgs f, MatView A, MatView B, OutView C
     }
     LimbAcc mag{win};
     const int N = bitlen(mag, 2 * nw);
-    if (truncated) atomicAdd(reinterpret_cast<int *>(f.status) + kStUncertified, 1);
+    // A truncated window dropped every term's bits below 2^xmin: |T - window| < (terms) 2^xmin
+    // with at most 2k terms, so the rounding is still RN_p(T) when no midpoint lies that close.
+    if (truncated && (N == 0 || !certified(mag, 2 * nw, N, f.p, (uint64_t)(2 * f.k), 0)))
+      atomicAdd(reinterpret_cast<int *>(f.status) + kStUncertified, 1);
     if (N == 0) {
       store_zero(L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o, C.plane);
     } else if (!round_store(mag, 2 * nw, N, neg, xmin, f.p, L, C.sign[c] + o, C.exp[c] + o, C.limb[c] + o,

@@ -348,6 +348,20 @@ def test_huge_exponent_spread(algo, method):
 
 
 @pytest.mark.parametrize("algo", ["ozaki", "plain"])
+def test_spread_beyond_the_fallback_window(algo):
+    """Exponents over +-8000: a dot product's terms span more than the exact fallback's
+    12 288-bit window, which keeps the top of the sum and drops each term's bits below it
+    (less than one unit of the window per term); the rounding is certified against that
+    bound, so every component is RN_p of the exact value and none is uncertified."""
+    p = 128
+    A = si.random_matrix(20, 16, p, 383, "uniform_exp", emin=-8000, emax=8000)
+    B = si.random_matrix(16, 18, p, 384, "uniform_exp", emin=-8000, emax=8000)
+    C, ws, st = gu.run(A, B, p, "4m", algo)
+    assert st["fallback_entries"] > 0 and st["uncertified"] == 0
+    _check_against_o1(C, A, B, p)
+
+
+@pytest.mark.parametrize("algo", ["ozaki", "plain"])
 def test_exponent_overflow_sets_status(algo):
     p = 128
     A = si.random_matrix(3, 4, p, 391)
