@@ -74,8 +74,10 @@ constexpr int kMaxBatch = 64;                              // problems per launc
 // GEMM is a set of one): their units are numbered consecutively and each
 // problem brings its own tensor maps, group table and output planes.
 struct TcProblem {
-  int64_t m, n;
+  int64_t m, n;        // the GEMM the units tile (a transposed problem: n and m of C)
   int64_t unit0;       // first unit of this problem
+  int tr;              // nonzero: C^T = B^T A^T is computed (A-side operand: B's digits) and
+                       // stored transposed, so the output planes keep C's layout
   int kbpp;            // k-blocks per pair (kpad / 64)
   int tiles_m, tiles_n;
   int chunk_kb;        // k-blocks per exact fp32 chunk (4 for 9-bit digits, 15 for 8-bit)
@@ -464,7 +466,12 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
         for (int kb = 0; kb < x.nkb; ++kb) {
           const int pi = kb / kbpp;
           const int k0 = (kb - pi * kbpp) * BK;
-          const int t = x.g.t0 + pi, uu = x.g.q - t;
+          int t = x.g.t0 + pi, uu = x.g.q - t;   // digit positions of A and of B
+          if (P.prob[x.prob].tr) {                // the A side carries B's digits
+            const int sw = t;
+            t = uu;
+            uu = sw;
+          }
           const int planeA = x.pd.a_plane0 + t - x.pd.a_pos0;
           const int planeB = x.pd.b_plane0 + uu - x.pd.b_pos0;
           if (!mbar_wait(&empty[stage], phase ^ 1, W)) { ok = false; break; }
@@ -585,7 +592,14 @@ __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
       const int64_t pm = P.prob[x.prob].m, pn = P.prob[x.prob].n;
       const int64_t row = (int64_t)x.tm * BM + row_in_tile;
       const int64_t col0 = (int64_t)x.tn * BN + part * COLS;
-      if (row < pm) {
+      if (P.prob[x.prob].tr) {   // tile row = column `row` of C, tile columns = rows of C
+        if (row < pm) {
+          int32_t *dst = P.prob[x.prob].out + (int64_t)x.e * pm * pn + row;
+#pragma unroll
+          for (int v = 0; v < COLS; ++v)   // a warp writes 32 consecutive columns of one row
+            if (col0 + v < pn) dst[(col0 + v) * pm] = acc[v];
+        }
+      } else if (row < pm) {
         int32_t *dst = P.prob[x.prob].out + (int64_t)x.e * pm * pn + row * pn + col0;
         if (col0 + COLS <= pn && ((pn & 3) == 0)) {
 #pragma unroll
@@ -675,21 +689,40 @@ static cudaError_t launch_set(const SliceGemmArgs *list, int count, cudaStream_t
       if (a.prod[x].a_plane0 + a.prod[x].a_npos > planes_a) planes_a = a.prod[x].a_plane0 + a.prod[x].a_npos;
       if (a.prod[x].b_plane0 + a.prod[x].b_npos > planes_b) planes_b = a.prod[x].b_plane0 + a.prod[x].b_npos;
     }
-    if (!make_map(&maps.a[q], a.dA, a.m, a.kpad, planes_a, BM) ||
-        !make_map(&maps.b[q], a.dB, a.n, a.kpad, planes_b, C::B_ROWS))
+    // Orientation: the side that pads less under the 128-row tiles becomes the row side
+    // (C^T = B^T A^T computed and stored transposed).  CTA pairs keep C's orientation.
+    auto padded = [](int64_t r, int64_t c) {
+      return ((r + BM - 1) / BM) * BM * (((c + BNT - 1) / BNT) * BNT);
+    };
+    const bool tr = !TWO && padded(a.n, a.m) < padded(a.m, a.n);
+    if (tr ? (!make_map(&maps.a[q], a.dB, a.n, a.kpad, planes_b, BM) ||
+              !make_map(&maps.b[q], a.dA, a.m, a.kpad, planes_a, C::B_ROWS))
+           : (!make_map(&maps.a[q], a.dA, a.m, a.kpad, planes_a, BM) ||
+              !make_map(&maps.b[q], a.dB, a.n, a.kpad, planes_b, C::B_ROWS)))
       return cudaErrorNotSupported;
     TcProblem &t = P.prob[q];
-    t.m = a.m;
-    t.n = a.n;
+    t.tr = tr ? 1 : 0;
+    t.m = tr ? a.n : a.m;
+    t.n = tr ? a.m : a.n;
     t.kbpp = (int)(a.kpad / BK);
-    t.tiles_m = (int)((a.m + BM - 1) / BM);
-    t.tiles_n = (int)((a.n + BNT - 1) / BNT);
+    t.tiles_m = (int)((t.m + BM - 1) / BM);
+    t.tiles_n = (int)((t.n + BNT - 1) / BNT);
     t.chunk_kb = a.chunk_kb;
     t.unit0 = units;
     t.groups = a.groups;
     t.sched = a.sched;
     t.out = a.out;
-    for (int x = 0; x < 4; ++x) t.prod[x] = a.prod[x];
+    for (int x = 0; x < 4; ++x) {
+      t.prod[x] = a.prod[x];
+      if (tr) {   // the operands' roles swap
+        t.prod[x].a_plane0 = a.prod[x].b_plane0;
+        t.prod[x].a_pos0 = a.prod[x].b_pos0;
+        t.prod[x].a_npos = a.prod[x].b_npos;
+        t.prod[x].b_plane0 = a.prod[x].a_plane0;
+        t.prod[x].b_pos0 = a.prod[x].a_pos0;
+        t.prod[x].b_npos = a.prod[x].a_npos;
+      }
+    }
     units += (int64_t)a.n_entries * ((t.tiles_m + pair - 1) / pair) * t.tiles_n;
   }
   P.count = count;

@@ -7,7 +7,8 @@ units of one pair and of 15 pairs (9-bit digits: 120 chunks of 256 elements) or
 63 pairs (8-bit digits: 960-element chunks), both TMEM buffers, and more units
 than SMs (persistent loop).  Kernels: single CTAs with 128 x 256 tiles (two TMEM
 accumulators) and with 128 x 128 tiles (four), and CTA pairs running one 256-row
-cta_group::2 MMA.
+cta_group::2 MMA.  The single-CTA kernels tile C^T = B^T A^T (stored transposed) where
+that pads less; the cases below include such shapes.
 """
 import numpy as np
 import pytest
@@ -26,6 +27,11 @@ CASES = [
     (260, 2048, 520, 128, "3m", "uniform", 9),      # 15-pair groups: 120 chunks per unit
     (260, 2048, 520, 128, "3m", "uniform", 8),      # 63-pair groups of 8-bit digits: 135 chunks
     (512, 320, 768, 256, "4m", "uniform", 9),       # many units per CTA
+    # shapes the single-CTA 128 x 256 tiles cover with less padding as C^T = B^T A^T
+    # (the 200 x 300 case above is one too)
+    (300, 130, 90, 192, "4m", "uniform_exp", 9),
+    (520, 2048, 260, 128, "3m", "uniform", 9),
+    (1000, 64, 40, 128, "4m", "uniform", 8),
 ]
 
 
