@@ -7,8 +7,9 @@
 // per-part split gives component c its own cut level):
 //     4M: Re = rr - ii,        Im = ri + ir
 //     3M: Re = rr - ii,        Im = ss - rr - ii
-// Groups are visited in order of increasing shift; the groups of one level are
-// summed in int64, and each accumulator takes one level sum per step, keeping a
+// Groups are visited in order of increasing shift; the groups of kAccLevels
+// consecutive levels are summed in int64 (each scaled by its level's power of 2^w
+// within the step), and each accumulator takes one such sum per step, keeping a
 // running carry in registers and emitting finished 32-bit words.
 // Value = Acc * 2^(E_i + F_j - (2w - 2) - w Q_c).
 // The result is RN_p(Acc) when no rounding midpoint lies within the error
@@ -52,11 +53,12 @@ struct LimbAcc {   // 32-bit words of a little-endian uint64 array
   }
 };
 
-// Exact signed integer built from one term per level, at shifts 0, w, 2w, ...
-// (a skipped level counts as a zero term): after each level the low w bits of the
-// running signed carry are final, go to a bit buffer and leave the carry, so every
-// shift is by a constant w.  A level sum has at most 3 x 160 int32 groups (|h| < 2^40),
-// so |carry + h| < 2^41.
+// Exact signed integer built from one term per step, at shifts 0, W, 2W, ... with
+// W = w kAccLevels <= 27 (a skipped step counts as a zero term): after each step the low
+// W bits of the running signed carry are final, go to a bit buffer and leave the carry,
+// so every shift is by a constant W.  A level has at most 3 x 160 int32 groups (< 2^40 in
+// magnitude), a step three levels weighted 1, 2^w, 2^2w (< 2^59 for w <= 9), so
+// |carry + h| < 2^60.
 struct DigitAcc {
   int64_t c = 0;      // value not yet emitted, in units of 2^(bits emitted)
   uint64_t bb = 0;    // emitted bits not yet written to `out` (nb of them, nb < 32)
@@ -142,12 +144,13 @@ __device__ __forceinline__ void finish_component(const AccumArgs &a, const OutVi
 
 // One thread per output element (i, j); a block takes kAccT consecutive elements of
 // one row.  The term table (plane, level shift, signs per group, in accumulation
-// order, written by k_group_table) is copied into shared memory.  The group values are
+// order, written by k_group_table; a multiplier is a sign times 2^(w (l % kAccLevels)))
+// is copied into shared memory.  The group values are
 // staged through shared memory kAccBatch groups at a time in a ring of kAccStages
 // buffers filled by cp.async, so that the next batch is in flight while the block
 // folds one.  Each warp copies contiguous runs of one group plane (16-byte copies when
 // n is a multiple of 4).  The groups of one level are summed in plain int64
-// (|sum| < 2^41) and folded into the exact accumulators once per level.
+// (|sum| < 2^59) and folded into the exact accumulators once per kAccLevels levels.
 constexpr size_t kAccStageBytes = (size_t)kAccStages * kAccBatch * kAccT * 4;
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
@@ -232,11 +235,11 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
         sum1 = mad_wide(v, t.w, sum1);
         const int sh0 = (int16_t)(t.y & 0xFFFF), sh1 = t.y >> 16;   // a component's level ends here
         if (sh0 >= 0) {
-          acc[0].add(words[0], sum0, sh0, a.w);
+          acc[0].add(words[0], sum0, sh0, a.w * kAccLevels);
           sum0 = 0;
         }
         if (sh1 >= 0) {
-          acc[1].add(words[1], sum1, sh1, a.w);
+          acc[1].add(words[1], sum1, sh1, a.w * kAccLevels);
           sum1 = 0;
         }
       }

@@ -199,7 +199,7 @@ int make_plan(int64_t m, int64_t n, int64_t k, int32_t p, int method, int algo, 
     if (d.a_pos0 + d.b_pos0 < qmin) qmin = d.a_pos0 + d.b_pos0;
   }
   P.n_groups_total = total;
-  if (!resid && total > kMaxGroupsTotal) return MPC_EINVAL;   // the accumulate kernel's term table in shared memory
+  if (!resid && total > kMaxGroupsTotal) return MPC_EINVAL;   // the group-table kernel's per-group table in shared memory
   P.acc_slots = (w * (Q - qmin) + 64) / 32 + 3;
   if (P.acc_slots > 88) return MPC_EINVAL;   // the accumulate kernel's word budget
   // bounds: b = bound_drop[c] + k (lossyA * bound_lossy_a[c] + lossyB * bound_lossy_b[c]), times 2^beta

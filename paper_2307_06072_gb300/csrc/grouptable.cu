@@ -139,8 +139,9 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
   }
   __syncthreads();   // order and bounds written (global memory, visible within the block)
   // The accumulation's term table, one entry per group in the accumulation order.  For
-  // component c the groups of the products entering it form levels; the last group of
-  // each such level carries the level's shift w (Q_c - q) for c.
+  // component c the groups of the products entering it form levels l = Q_c - q, taken
+  // kAccLevels at a time: a group's multiplier is its sign times 2^(w (l % kAccLevels)),
+  // and the last group of each step carries the step's shift w kAccLevels (l / kAccLevels).
   const int G = n_groups;
   const bool z0 = a.bounds[6] != 0, z1 = a.bounds[7] != 0;   // components that vanish identically
   for (int x = threadIdx.x; x < G; x += blockDim.x) {
@@ -148,21 +149,24 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
     const int q = (s_qc[e] >> 16) - 8, count = s_qc[e] & 0xFFFF;
     const bool empty = count == 0;   // all its pairs were zero: its plane is never written
     const int prod = a.table[e].prod;
-    int shift[2];
+    int shift[2], mult[2];
     for (int c = 0; c < 2; ++c) {
       shift[c] = -1;
+      mult[c] = 0;
       if (product_sign(a.method, c, prod) == 0) continue;
+      const int l = s_qcomp[c] - q;   // >= 0: no kept group lies above its component's cut
+      mult[c] = product_sign(a.method, c, prod) << (a.w * (l % kAccLevels));
       bool last = true;
       for (int y = x + 1; y < G; ++y) {
         const int f = a.order[y];
         if (product_sign(a.method, c, a.table[f].prod) == 0) continue;
-        last = ((s_qc[f] >> 16) - 8) != q;
+        last = (s_qcomp[c] - ((s_qc[f] >> 16) - 8)) / kAccLevels != l / kAccLevels;
         break;
       }
-      if (last) shift[c] = a.w * (s_qcomp[c] - q);
+      if (last) shift[c] = a.w * kAccLevels * (l / kAccLevels);
     }
     a.terms[x] = AccTerm{empty ? -1 : e, (int32_t)(((uint32_t)shift[1] << 16) | ((uint32_t)shift[0] & 0xFFFFu)),
-                         empty || z0 ? 0 : product_sign(a.method, 0, prod), empty || z1 ? 0 : product_sign(a.method, 1, prod)};
+                         empty || z0 ? 0 : mult[0], empty || z1 ? 0 : mult[1]};
   }
   __syncthreads();   // every reader of the true levels is done
   if (a.zwords) {    // the slice GEMMs index digit planes from each operand's first position

@@ -21,14 +21,20 @@ struct SliceGemmArgs {
   int32_t *status;
 };
 
+// Levels folded into the exact accumulators per step: the level l = Q_c - q (l >= 0) of
+// component c belongs to step l / kAccLevels and enters it with weight 2^(w (l % kAccLevels)).
+constexpr int kAccLevels = 3;
+
 // One accumulation term per group, in the accumulation order (descending level):
-// group plane index (-1: an emptied group), the two signs, and per component -- on the
-// last group of a level among the groups of the products entering that component --
-// the level's shift w (Q_c - q), else -1.  Written by k_group_table, read by k_oz_accum.
+// group plane index (-1: an emptied group), the two multipliers, and per component -- on
+// the last group of a step among the groups of the products entering that component --
+// the step's shift w kAccLevels (l / kAccLevels), else -1.  Written by k_group_table, read
+// by k_oz_accum.
 struct __align__(16) AccTerm {
   int32_t plane;
   int32_t shifts;   // low 16 bits: real part's shift, high 16 bits: imaginary part's (int16, -1: none)
-  int32_t s0, s1;   // the group's sign in the real / imaginary part: -1, 0 or 1
+  int32_t s0, s1;   // the group's multiplier in the real / imaginary part: its sign (-1, 0, 1)
+                    // times 2^(w (l % kAccLevels))
 };
 static_assert(sizeof(AccTerm) == 16, "AccTerm is read as one int4");
 
