@@ -233,14 +233,16 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
         const int32_t v = stage[buf][u][tid];
         sum0 = mad_wide(v, t.z, sum0);
         sum1 = mad_wide(v, t.w, sum1);
-        const int sh0 = (int16_t)(t.y & 0xFFFF), sh1 = t.y >> 16;   // a component's level ends here
-        if (sh0 >= 0) {
-          acc[0].add(words[0], sum0, sh0, a.w * kAccLevels);
-          sum0 = 0;
-        }
-        if (sh1 >= 0) {
-          acc[1].add(words[1], sum1, sh1, a.w * kAccLevels);
-          sum1 = 0;
+        if (t.y != -1) {   // a component's step ends here (most groups: neither, both shifts -1)
+          const int sh0 = (int16_t)(t.y & 0xFFFF), sh1 = t.y >> 16;
+          if (sh0 >= 0) {
+            acc[0].add(words[0], sum0, sh0, a.w * kAccLevels);
+            sum0 = 0;
+          }
+          if (sh1 >= 0) {
+            acc[1].add(words[1], sum1, sh1, a.w * kAccLevels);
+            sum1 = 0;
+          }
         }
       }
     }
