@@ -24,16 +24,29 @@ __device__ __forceinline__ void product_kinds(int method, int prod, int &ka, int
   }
 }
 
-__device__ void serial_passes(const GroupTableArgs &a, const int32_t *s_qc, const uint64_t *s_bd, int *s_start);
+constexpr int kMaxFlagPlanes = 512;   // digit planes of an operand (3 s + 1 <= 481) and its two value flags
+constexpr int kCountBuckets = kMaxSlices + 2;   // group pair counts 0 .. kMaxSlices + 1
+
+__device__ void accumulation_order(const GroupTableArgs &a, const int32_t *s_qc, int16_t *s_order);
+__device__ void unit_schedule(const GroupTableArgs &a, const int32_t *s_qc, int *s_hist);
+__device__ void call_bounds(const GroupTableArgs &a, const uint64_t *s_bd);
+
+// product whose groups contain table entry e (the products' groups are consecutive)
+__device__ __forceinline__ int product_of(const GroupTableArgs &a, int e) {
+  int x = 0;
+  while (x + 1 < a.n_products && e >= a.prod[x + 1].group0) ++x;
+  return x;
+}
 
 // Per product (one warp each): the group table, levels ascending; then every
 // group loses the pairs at its two ends whose A or B digit plane is all zero
 // (their products are exactly zero), so it never splits and the table keeps its
 // size; a group of zero pairs only keeps its place (count 0: no unit, no term).
 // The warp also counts the dropped pairs (levels above the product's cut level)
-// whose planes are both nonzero.  Thread 0 then merges the products' groups into
-// the accumulation order (descending level, i.e. ascending shift), writes the slice
-// GEMM's unit schedule and the call's error bounds:
+// whose planes are both nonzero.  Then the block forms the accumulation order
+// (descending level, i.e. ascending shift: every group finds its own place by binary
+// searches in the other products' level-sorted lists), a warp per product sorts the
+// slice GEMM's unit schedule, and thread 0 writes the call's error bounds:
 //   drop[c]    = sum over the products of component c of ceil(B_prod / 2^beta),
 //                B_prod = k (2^(w-2) n_{Q+1} + ceil(max_{j>=2} n_{Q+j} / 3)) over live pairs;
 //   lossy_a[c] = sum of the products' truncation factors (4 for the 3M sums, else 1),
@@ -53,12 +66,16 @@ __device__ void serial_passes(const GroupTableArgs &a, const int32_t *s_qc, cons
 // digit plane (t0 - z_a, q - z_a - z_b), which is what the slice-GEMM kernels index.
 __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
   __shared__ uint64_t s_bd[4];
-  __shared__ int32_t s_qc[kMaxGroupsTotal];   // per group: (q + 8) << 16 | count, for the serial passes below
-  __shared__ int s_start[kMaxSlices + 3];
+  __shared__ int32_t s_qc[kMaxGroupsTotal];   // per group: (q + 8) << 16 | count
+  __shared__ int16_t s_order[kMaxGroupsTotal];   // the accumulation order (a copy of a.order)
+  __shared__ int s_hist[4][kCountBuckets];    // per product: unit-schedule buckets
+  __shared__ uint8_t s_fa[kMaxFlagPlanes], s_fb[kMaxFlagPlanes];   // plane / value flags of A and B
   __shared__ int s_pos[4][2];                 // per product: true first digit positions of A and B
   __shared__ int s_qp[4];                     // per product: its cut level
   __shared__ int s_qcomp[2];                  // per component: its cut level Q_c
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int x = threadIdx.x; x < a.planes_A + 2; x += blockDim.x) s_fa[x] = a.flagsA[x] != 0;
+  for (int x = threadIdx.x; x < a.planes_B + 2; x += blockDim.x) s_fb[x] = a.flagsB[x] != 0;
   if (threadIdx.x == 0) {
     int zc[2] = {1 << 30, 1 << 30};
     for (int x = 0; x < a.n_products; ++x) {
@@ -95,7 +112,7 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
     for (int c = 0; c < 2; ++c)
       if (product_sign(a.method, c, warp) != 0 && !component_zero(vA, vB, c)) needed = true;
     auto live = [&](int t, int u) {
-      return needed && a.flagsA[pd.a_plane0 + t - pd.a_pos0] != 0 && a.flagsB[pd.b_plane0 + u - pd.b_pos0] != 0;
+      return needed && s_fa[pd.a_plane0 + t - pd.a_pos0] && s_fb[pd.b_plane0 + u - pd.b_pos0];
     };
     const int ng = build_groups(warp, pd.a_pos0, pd.a_npos, pd.b_pos0, pd.b_npos, Qp, a.gmax, nullptr, 0);
     for (int e = pd.group0 + lane; e < pd.group0 + pd.n_groups; e += 32) {
@@ -133,11 +150,13 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
     s_qc[e] = ((g.q + 8) << 16) | g.count;   // q >= -2, count <= kMaxSlices + 1
   }
   __syncthreads();
+  accumulation_order(a, s_qc, s_order);
+  if (warp < a.n_products) unit_schedule(a, s_qc, s_hist[warp]);
   if (threadIdx.x == 0) {
-    serial_passes(a, s_qc, s_bd, s_start);
+    call_bounds(a, s_bd);
     for (int c = 0; c < 2; ++c) a.bounds[8 + c] = (uint64_t)(int64_t)s_qcomp[c];
   }
-  __syncthreads();   // order and bounds written (global memory, visible within the block)
+  __syncthreads();   // order (and its shared copy) and bounds written
   // The accumulation's term table, one entry per group in the accumulation order.  For
   // component c the groups of the products entering it form levels l = Q_c - q, taken
   // kAccLevels at a time: a group's multiplier is its sign times 2^(w (l % kAccLevels)),
@@ -145,10 +164,10 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
   const int G = n_groups;
   const bool z0 = a.bounds[6] != 0, z1 = a.bounds[7] != 0;   // components that vanish identically
   for (int x = threadIdx.x; x < G; x += blockDim.x) {
-    const int e = a.order[x];
+    const int e = s_order[x];
     const int q = (s_qc[e] >> 16) - 8, count = s_qc[e] & 0xFFFF;
     const bool empty = count == 0;   // all its pairs were zero: its plane is never written
-    const int prod = a.table[e].prod;
+    const int prod = product_of(a, e);
     int shift[2], mult[2];
     for (int c = 0; c < 2; ++c) {
       shift[c] = -1;
@@ -158,8 +177,8 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
       mult[c] = product_sign(a.method, c, prod) << (a.w * (l % kAccLevels));
       bool last = true;
       for (int y = x + 1; y < G; ++y) {
-        const int f = a.order[y];
-        if (product_sign(a.method, c, a.table[f].prod) == 0) continue;
+        const int f = s_order[y];
+        if (product_sign(a.method, c, product_of(a, f)) == 0) continue;
         last = (s_qcomp[c] - ((s_qc[f] >> 16) - 8)) / kAccLevels != l / kAccLevels;
         break;
       }
@@ -180,39 +199,83 @@ __global__ void __launch_bounds__(128) k_group_table(GroupTableArgs a) {
   }
 }
 
-// Thread 0's passes: accumulation order, unit schedule, bounds.
-__device__ void serial_passes(const GroupTableArgs &a, const int32_t *s_qc, const uint64_t *s_bd, int *s_start) {
+// Entries of [g0, g0 + n) (levels ascending) whose level key (s_qc >> 16) is <= key.
+__device__ __forceinline__ int count_level_le(const int32_t *s_qc, int g0, int n, int key) {
+  int lo = 0, hi = n;   // the first entry with a larger key lies in [lo, hi]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((s_qc[g0 + mid] >> 16) <= key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The accumulation order: the products' groups (each product's list ascending in level)
+// by descending level; within a level product by product, and within a product's level
+// by descending table position.  Group e of product x at level q lands at rank
+//   (its product's groups after it) + sum over x' < x of |{level >= q}| + sum over x' > x of |{level > q}|,
+// each count a binary search in x''s list.  Written to a.order and to s_order.
+__device__ void accumulation_order(const GroupTableArgs &a, const int32_t *s_qc, int16_t *s_order) {
   const ProductDesc *pds = a.prod;
+  int G = 0;
+  for (int x = 0; x < a.n_products; ++x) G = max(G, pds[x].group0 + pds[x].n_groups);
+  for (int e = threadIdx.x; e < G; e += blockDim.x) {
+    const int x = product_of(a, e);
+    const int key = s_qc[e] >> 16;
+    int r = pds[x].group0 + pds[x].n_groups - 1 - e;
+    for (int y = 0; y < a.n_products; ++y) {
+      if (y == x) continue;
+      const int n = pds[y].n_groups;
+      r += n - count_level_le(s_qc, pds[y].group0, n, y < x ? key - 1 : key);
+    }
+    a.order[r] = e;
+    s_order[r] = (int16_t)e;
+  }
+}
+
+// The slice GEMM's schedule (after the accumulation order in a.order): product by
+// product, groups by descending pair count, stable, so that consecutive units take nearly
+// equally long and the groups of adjacent levels, which share digit planes, stay next to
+// each other.  One warp per product: a counting sort whose scatter takes 32 groups at a
+// time, lanes with equal counts ranked by lane (table order).
+__device__ void unit_schedule(const GroupTableArgs &a, const int32_t *s_qc, int *hist) {
+  const ProductDesc *pds = a.prod;
+  const int x = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int G = 0, out = 0;
+  for (int y = 0; y < a.n_products; ++y) {
+    G = max(G, pds[y].group0 + pds[y].n_groups);
+    if (y < x) out += pds[y].n_groups;
+  }
+  int32_t *sched = a.order + G;
+  const int g0 = pds[x].group0, g1 = g0 + pds[x].n_groups;
+  for (int b = lane; b < kCountBuckets; b += 32) hist[b] = 0;
+  __syncwarp();
+  for (int e = g0 + lane; e < g1; e += 32) atomicAdd(&hist[kMaxSlices + 1 - (s_qc[e] & 0xFFFF)], 1);
+  __syncwarp();
+  if (lane == 0)   // bucket starts (descending count = ascending bucket)
+    for (int b = 0; b < kCountBuckets; ++b) {
+      const int c = hist[b];
+      hist[b] = out;
+      out += c;
+    }
+  __syncwarp();
+  for (int base = g0; base < g1; base += 32) {
+    const int e = base + lane;
+    const bool v = e < g1;
+    const int b = v ? kMaxSlices + 1 - (s_qc[e] & 0xFFFF) : -1 - lane;   // idle lanes: keys of their own
+    const unsigned same = __match_any_sync(0xffffffffu, b);
+    const int rank = __popc(same & ((1u << lane) - 1u));
+    const int pos = v ? hist[b] + rank : 0;
+    __syncwarp();
+    if (v && rank == 0) hist[b] += __popc(same);
+    __syncwarp();
+    if (v) sched[pos] = e;
+  }
+}
+
+// Thread 0: the call's error bounds.
+__device__ void call_bounds(const GroupTableArgs &a, const uint64_t *s_bd) {
   const int n_products = a.n_products;
-  int32_t *order = a.order;
-  // merge the per-product lists (each ascending in q) from their ends
-  int next[4];
-  for (int x = 0; x < 4; ++x) next[x] = x < n_products ? pds[x].group0 + pds[x].n_groups - 1 : -1;
-  int n = 0;
-  while (true) {
-    int best = -1;
-    for (int x = 0; x < n_products; ++x)
-      if (next[x] >= pds[x].group0 && (best < 0 || (s_qc[next[x]] >> 16) > (s_qc[next[best]] >> 16))) best = x;
-    if (best < 0) break;
-    order[n++] = next[best]--;
-  }
-  // the slice GEMM's schedule: product by product, groups by descending pair
-  // count (stable), so that consecutive units take nearly equally long and the
-  // groups of adjacent levels, which share digit planes, stay next to each other
-  // (counting sort per product; count <= kMaxSlices + 1)
-  int32_t *sched = order + n;
-  int out = 0;
-  for (int x = 0; x < n_products; ++x) {
-    const int g0 = pds[x].group0, g1 = g0 + pds[x].n_groups;
-    int *start = s_start;
-    for (int c = 0; c < kMaxSlices + 3; ++c) start[c] = 0;
-    for (int e = g0; e < g1; ++e) ++start[kMaxSlices + 1 - (s_qc[e] & 0xFFFF) + 1];
-    start[0] = out;
-    for (int c = 1; c < kMaxSlices + 3; ++c) start[c] += start[c - 1];
-    for (int e = g0; e < g1; ++e) sched[start[kMaxSlices + 1 - (s_qc[e] & 0xFFFF)]++] = e;
-    out += g1 - g0;
-  }
-  // the call's bounds
   const int32_t *valA = a.flagsA + a.planes_A, *valB = a.flagsB + a.planes_B;   // [re, im] values nonzero
   for (int c = 0; c < 2; ++c) {
     uint64_t bd = 0, la = 0, lb = 0;
