@@ -191,18 +191,25 @@ __global__ void __launch_bounds__(kAccT) k_oz_accum(AccumArgs a, OutView C) {
   const int nrun = (int)(a.n - j0 < kAccT ? a.n - j0 : kAccT);   // valid elements of this block's run
   const bool vec = (a.n & 3) == 0;
   const int nbatch = (a.n_entries + kAccBatch - 1) / kAccBatch;
+  // 16-byte copies: this thread always copies the same 4 elements (c4) of the group rows
+  // g0, g0 + 4, g0 + 8, ... of a batch, so their offset and valid count are fixed
+  constexpr int kRowsPerPass = kAccT / (kAccT / 4);   // 4 group rows per pass of the block
+  const int c4 = 4 * (tid % (kAccT / 4)), g0 = tid / (kAccT / 4);
+  const int valid4 = nrun - c4 >= 4 ? 4 : (nrun > c4 ? nrun - c4 : 0);
+  const int32_t *src4 = row + (valid4 ? c4 : 0);
   __syncthreads();   // the term table is in shared memory
   auto issue = [&](int bidx) {   // batch bidx into ring buffer bidx % kAccStages (an empty group if none)
     if (bidx < nbatch) {
       const int x0 = bidx * kAccBatch, buf = bidx % kAccStages;
       const int nb = a.n_entries - x0 < kAccBatch ? a.n_entries - x0 : kAccBatch;
       if (vec) {
-        for (int q = tid; q < nb * (kAccT / 4); q += kAccT) {
-          const int g = q / (kAccT / 4), c4 = 4 * (q % (kAccT / 4));
-          const int plane = sterm[x0 + g].x;
-          const int valid = plane < 0 ? 0 : (nrun - c4 >= 4 ? 4 : (nrun > c4 ? nrun - c4 : 0));
-          const int32_t *src = row + (plane < 0 ? 0 : (int64_t)plane * mn) + (valid ? c4 : 0);
-          cp_async16(&stage[buf][g][c4], src, 4 * valid);   // bytes beyond `valid` are zero-filled
+#pragma unroll
+        for (int g = g0; g < kAccBatch; g += kRowsPerPass) {
+          if (g < nb) {
+            const int plane = sterm[x0 + g].x;
+            const bool take = plane >= 0;   // bytes beyond the copied ones are zero-filled
+            cp_async16(&stage[buf][g][c4], src4 + (take ? (int64_t)plane * mn : 0), take ? 4 * valid4 : 0);
+          }
         }
       } else {
         for (int q = tid; q < nb * kAccT; q += kAccT) {
