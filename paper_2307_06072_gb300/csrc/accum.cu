@@ -31,7 +31,7 @@ namespace {
 constexpr int kMaxWords = 88;   // 32-bit words of the exact accumulator (Q <= 2s, s <= 160)
 
 // a block: kAccT consecutive elements of one row, one thread each
-constexpr int kAccT = 256, kAccBatch = 16, kAccStages = 2;
+constexpr int kAccT = 256, kAccBatch = 16, kAccStages = 3;
 
 // The exact accumulators' 32-bit words: a thread-local array (local memory, cached in
 // L1; the kernel leaves most of L1 to it by staging only a batch of groups in shared
